@@ -1,0 +1,309 @@
+/*
+ * pressure.h -- C ABI of libpressure: the P1 finite-element pressure system of
+ * the semi-implicit hybrid FV/FE all-Mach scheme, solved matrix-free by
+ * (preconditioned) conjugate gradient on one GB300 (sm_103a).
+ *
+ * The operator.  On the nodes of a primal triangle (dim 2) or tetrahedron
+ * (dim 3) mesh, the projection stage (Section 3.4, weak problem) asks for the
+ * pressure correction dP with
+ *
+ *     A dP = b,   A = M_alpha + dt^2 K_beta,
+ *     (M_alpha)_ij = int alpha_h phi_i phi_j      (consistent mass, no lumping)
+ *     (K_beta)_ij  = int beta grad phi_i . grad phi_j
+ *
+ * phi_i the P1 hat functions, alpha_h the P1 interpolant of a nodal field alpha
+ * (the paper's constant 1/(gamma-1), eq. pressure_dt, generalised to a nodal
+ * field), beta piecewise constant per element (the enthalpy H^{n+1,k} moved to
+ * the primal elements, Section 3.3) and dt the time step.  The stiffness sign
+ * is the one Green's formula gives from the strong form (eq. pressure_dt); it
+ * is the sign that makes A symmetric positive definite, which Section 3.4
+ * states and which the conjugate gradient method of the abstract needs.
+ *
+ * Dirichlet nodes (Section 3.6: the pressure is imposed on boundary vertices)
+ * are homogeneous: their rows and columns are removed from A.  Every vector
+ * crossing this ABI is a full nodal vector in the CALLER'S node numbering; on
+ * Dirichlet nodes inputs are ignored and outputs are 0.  The library renumbers
+ * nodes and reorders elements internally; that numbering never leaks out.
+ *
+ * Conventions.
+ *  - Every function returns an int status (PS_OK = 0, negative = error); no
+ *    C++ exception crosses this boundary.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Device pointers (suffix _dev) are caller-owned CUDA
+ *    device allocations on the context's device; the library never frees them.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).  Work is ordered on that stream; functions that
+ *    report scalars (solve info) synchronise it before returning.
+ *  - A ps_ctx and the meshes created from it may be used from one host thread
+ *    at a time; different contexts are independent.
+ */
+#ifndef PRESSURE_H
+#define PRESSURE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PS_OK            0
+#define PS_PENDING       1   /* ps_solve_poll: request not finished yet            */
+#define PS_EINVAL       -1   /* bad argument: index out of range, degenerate or
+                                non-finite element, alpha < 0, beta <= 0, ...     */
+#define PS_ENOMEM       -2   /* device allocation failed or HBM budget exceeded   */
+#define PS_ENOTCONV     -3   /* iteration limit reached; info is still filled      */
+#define PS_EBREAKDOWN   -4   /* CG breakdown: p.Ap <= 0 or a non-finite scalar     */
+#define PS_ETIMEOUT     -5   /* a bounded device-side wait gave up                 */
+#define PS_ECUDA        -6   /* a CUDA runtime call failed                          */
+#define PS_ESTATE       -7   /* call out of order (e.g. solve before coeff_set)     */
+#define PS_ENOTFOUND    -8   /* unknown ticket / case id                            */
+
+/* ---- precision of pressure_apply ------------------------------------- */
+#define PS_F32 1             /* x, y are float  arrays; FP32 element arithmetic    */
+#define PS_F64 2             /* x, y are double arrays; FP64 element arithmetic    */
+
+/* ---- solver modes ---------------------------------------------------- */
+#define PS_MODE_FP64   0     /* plain PCG, all vectors and arithmetic in FP64      */
+#define PS_MODE_MIXED  1     /* FP32 PCG inner solves inside FP64 defect correction */
+
+#define PS_PRECOND_NONE   0
+#define PS_PRECOND_JACOBI 1
+
+typedef struct ps_ctx ps_ctx;
+typedef struct ps_mesh ps_mesh;
+typedef struct ps_server ps_server;
+typedef int64_t ps_ticket;
+
+/* Mesh preprocessing options (all zero = defaults). */
+typedef struct {
+    int32_t chunk_elems;     /* target elements per chunk (0 = auto by size)       */
+    int32_t chunk_nodes_max; /* cap on distinct nodes per chunk (0 = auto)          */
+    int32_t reserved[6];
+} ps_mesh_opts;
+
+typedef struct {
+    double tol;              /* stop when ||b - A x||_2 / ||b||_2 <= tol (FP64 true
+                                residual over free nodes); default 1e-10            */
+    int64_t max_iters;       /* cap on total CG iterations (0 = 100000)            */
+    int32_t mode;            /* PS_MODE_FP64 or PS_MODE_MIXED                       */
+    int32_t precond;         /* PS_PRECOND_JACOBI (default) or PS_PRECOND_NONE     */
+    double inner_tol;        /* mixed: inner FP32 relative reduction (0 = 1e-4)    */
+    int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
+    int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
+                             /* negative = launch kernels directly, no graph)      */
+    int32_t reserved[6];
+} ps_solve_opts;
+
+typedef struct {
+    int32_t status;          /* PS_OK, PS_ENOTCONV, PS_EBREAKDOWN, ...             */
+    int32_t converged;       /* 1 if rel_res <= tol                                */
+    int64_t iters_outer;     /* FP64 true-residual evaluations (mixed: outer steps) */
+    int64_t iters_inner;     /* CG iterations (mixed: FP32 inner iterations)       */
+    double rel_res;          /* final TRUE relative residual ||b-Ax||/||b||, FP64  */
+    double bnorm;            /* ||b||_2 over free nodes                            */
+    int64_t n_free;          /* number of free (non-Dirichlet) nodes               */
+    double seconds;          /* wall time of the call                              */
+    int64_t kernel_launches; /* CUDA kernels this call launched (graph nodes included) */
+    double reserved[3];
+} ps_solve_info;
+
+typedef struct {
+    int64_t n_nodes, n_elems, n_free;
+    int32_t dim, n_chunks;
+    int64_t n_shared;        /* nodes touched by more than one chunk               */
+    int64_t chunk_node_refs; /* sum over chunks of distinct nodes                  */
+    int64_t device_bytes;    /* device memory held by this mesh                     */
+    int32_t max_chunk_elems, max_chunk_nodes;
+    int64_t reserved[4];
+} ps_mesh_stats;
+
+/* ---- library --------------------------------------------------------- */
+
+/* Library version string (static storage). */
+const char *ps_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *ps_status_str(int status);
+
+/* Message of the last error raised on the calling thread ("" if none;
+ * thread-local static storage, valid until the next failing call). */
+const char *ps_last_error(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory held by meshes, coefficients and solver workspaces of this context
+ * (0 = no cap beyond the device).  *out receives the handle. */
+int ps_ctx_create(ps_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context and every mesh still attached to it. */
+void ps_ctx_destroy(ps_ctx *ctx);
+
+/* Device bytes currently held by the context's meshes and workspaces. */
+int64_t ps_ctx_bytes_in_use(const ps_ctx *ctx);
+
+/* ---- mesh (Section 3.1: primal simplex mesh, P1 unknowns on vertices) ----
+ *
+ * ps_mesh_upload: copy a mesh to the device.
+ *   dim         2 (triangles) or 3 (tetrahedra)
+ *   coords      host [n_nodes][dim] double, vertex coordinates
+ *   conn        host [n_elems][dim+1] int32, 0-based vertex ids (any orientation)
+ *   dirichlet   host [n_nodes] uint8; nonzero = homogeneous Dirichlet node
+ *               (may be NULL: no Dirichlet nodes)
+ *   opts        preprocessing options or NULL
+ * Host work: element partition into chunks along a Morton curve, node
+ * renumbering (chunk-interior nodes contiguous per chunk, nodes shared between
+ * chunks after them), per-chunk local connectivity and incidence lists.
+ * Errors: PS_EINVAL for dim not 2/3, n_elems < 1, a vertex id out of range, a
+ * non-finite coordinate or an element of zero volume; PS_ENOMEM. */
+int ps_mesh_upload(ps_ctx *ctx, int dim, int64_t n_nodes, const double *coords,
+                   int64_t n_elems, const int32_t *conn, const uint8_t *dirichlet,
+                   const ps_mesh_opts *opts, ps_mesh **out);
+
+/* Release a mesh and its device memory. */
+void ps_mesh_free(ps_mesh *mesh);
+
+int ps_mesh_get_stats(const ps_mesh *mesh, ps_mesh_stats *out);
+
+/* ---- coefficients (Section 3.4: 1/(gamma-1), H^{n+1,k}, dt) -----------
+ *   alpha_nodal  host [n_nodes] double, >= 0, finite
+ *   beta_elem    host [n_elems] double, > 0, finite (element order of upload)
+ *   dt2          dt^2 > 0
+ * Also builds the Jacobi diagonal D_ii = sum_e (M^e_ii + dt2 K^e_ii) on the
+ * device.  May be called again to change coefficients (e.g. between Picard
+ * iterations or time steps).  Errors: PS_EINVAL. */
+int ps_coeff_set(ps_mesh *mesh, const double *alpha_nodal, const double *beta_elem, double dt2);
+
+/* Only beta changes (alpha and dt2 kept): same checks and effect. */
+int ps_coeff_set_beta(ps_mesh *mesh, const double *beta_elem);
+
+/* ---- operator apply: y = A x (Dirichlet rows/cols removed) ---------------
+ *   x_dev, y_dev  device [n_nodes] float (PS_F32) or double (PS_F64), caller
+ *                 numbering; must not alias.
+ * Matrix-free, element by element; no atomics; deterministic (the same
+ * inputs give bitwise the same outputs).  Errors: PS_EINVAL, PS_ESTATE. */
+int ps_pressure_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, int precision, void *stream);
+
+/* ---- solve A x = b (Section 3.4: SPD system, matrix-free CG, warm start) --
+ *   b_dev  device [n_nodes] double, caller numbering (Dirichlet entries ignored)
+ *   x_dev  device [n_nodes] double; in: first guess (e.g. the pressure of the
+ *          previous time level), out: solution (0 on Dirichlet nodes)
+ *   opts   NULL = defaults (mixed precision, Jacobi, tol 1e-10)
+ *   info   may be NULL
+ * Returns PS_OK when the FP64 true relative residual reaches opts->tol,
+ * PS_ENOTCONV when an iteration cap stops it first (x holds the last iterate),
+ * PS_EBREAKDOWN on p.Ap <= 0 or a non-finite scalar. */
+int ps_pressure_solve(ps_mesh *mesh, const double *b_dev, double *x_dev,
+                      const ps_solve_opts *opts, ps_solve_info *info, void *stream);
+
+/* Fill opts with the defaults. */
+void ps_solve_opts_default(ps_solve_opts *opts);
+
+/* ---- batched solve: many independent meshes in one persistent kernel ----
+ *   meshes  [n] mesh handles of one context (distinct, coefficients set)
+ *   b_dev   [n] device pointers, each [n_nodes_i] double, caller numbering
+ *   x_dev   [n] device pointers, each [n_nodes_i] double (in: guess, out: sol)
+ *   infos   [n] per-mesh results, may be NULL
+ * Mixed precision only: every FP32 inner PCG iteration of all unconverged
+ * meshes runs inside one cooperative persistent kernel (grid barriers with a
+ * bounded spin), FP64 residuals and updates between epochs; the launch
+ * sequence is captured in a CUDA graph when opts->graph_iters >= 0.
+ * Each mesh's arithmetic and reduction order do not depend on which other
+ * meshes share the batch.  Returns PS_OK if all converged, else the first
+ * per-mesh error (every info filled). */
+int ps_batch_solve(ps_mesh *const *meshes, int n, const double *const *b_dev,
+                   double *const *x_dev, const ps_solve_opts *opts, ps_solve_info *infos,
+                   void *stream);
+
+/* ---- serving: continuous batching of solve requests ---------------------
+ * A server owns a worker thread and a stream.  Cases (simulations) register a
+ * mesh once; each request (one time step's solve) names a case, carries a host
+ * right-hand side, and warm-starts from the case's previous solution kept on
+ * the device (Section 3.4: the solution at t^n is the first guess).  Requests
+ * are admitted while their workspace fits the HBM budget and a slot is free;
+ * admitted requests share persistent-kernel epochs with requests already in
+ * flight, and a request that converges frees its slot at the next epoch
+ * boundary. */
+typedef struct {
+    int32_t max_slots;        /* requests in flight at once (0 = 64)                */
+    int32_t epoch_iters;      /* inner iterations per epoch (0 = 64)                */
+    size_t hbm_budget_bytes;  /* cap on workspaces of in-flight requests (0 = ctx)  */
+    ps_solve_opts opts;       /* solver options for every request                   */
+    int32_t reserved[8];
+} ps_server_opts;
+
+int ps_server_create(ps_ctx *ctx, const ps_server_opts *opts, ps_server **out);
+
+/* Stop the worker (pending requests fail with PS_ESTATE) and free the server. */
+void ps_server_destroy(ps_server *srv);
+
+/* Register a case: mesh (coefficients set) and the initial warm start
+ * (host [n_nodes] double or NULL = zeros).  *case_id receives its id. */
+int ps_server_add_case(ps_server *srv, ps_mesh *mesh, const double *x0_host, int32_t *case_id);
+
+/* Queue one solve of `case_id`.  b_host [n_nodes] double is copied before the
+ * call returns.  If beta_host is not NULL ([n_elems] double) the case's beta is
+ * replaced (the enthalpy drifts between time steps) before this request runs.
+ * Requests of one case run in submission order. */
+int ps_solve_submit(ps_server *srv, int32_t case_id, const double *b_host,
+                    const double *beta_host, ps_ticket *out);
+
+/* Poll a ticket: PS_PENDING while queued or running; otherwise the request's
+ * final status, with info filled and, if x_out is not NULL, the solution copied
+ * to x_out (host [n_nodes] double).  A finished ticket may be polled again
+ * until ps_server_release is called for it. */
+int ps_solve_poll(ps_server *srv, ps_ticket ticket, ps_solve_info *info, double *x_out);
+
+/* Block until the ticket finishes (bounded by timeout_s seconds, <= 0 = 600). */
+int ps_solve_wait(ps_server *srv, ps_ticket ticket, double timeout_s, ps_solve_info *info,
+                  double *x_out);
+
+/* Drop a finished ticket's record. */
+int ps_server_release(ps_server *srv, ps_ticket ticket);
+
+typedef struct {
+    int64_t submitted, completed, failed, in_flight, queued;
+    int64_t epochs;           /* persistent-kernel epochs launched                  */
+    int64_t peak_in_flight;
+    int64_t bytes_in_use;
+    double busy_seconds;
+    int64_t reserved[4];
+} ps_server_stats;
+
+int ps_server_get_stats(ps_server *srv, ps_server_stats *out);
+
+/* ---- host-only diagnostics ---------------------------------------------
+ * Run the mesh preprocessing of ps_mesh_upload on the host (no device work)
+ * and check the invariants the kernels rely on: every element vertex appears
+ * exactly once in its chunk's incidence lists, chunk-interior nodes belong to
+ * one chunk, partial-sum slots of shared nodes form a bijection.  Same
+ * arguments as ps_mesh_upload; stats filled (device_bytes = shared memory per
+ * block of the FP64 operator pass).  PS_EINVAL for bad input, PS_ESTATE if an
+ * invariant fails (ps_last_error names it). */
+int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
+                     const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
+                     ps_mesh_stats *stats);
+
+/* ---- kernel timing (diagnostics for roofline reports) -------------------
+ * Launch one internal kernel of the solver `reps` times back to back on
+ * `stream` between two CUDA events recorded on that stream, and report the
+ * average device time per launch in *avg_ms.  The workspace vectors are used
+ * as inputs as they stand (run a solve first for meaningful data); results
+ * are discarded.  which:
+ *   PS_KERNEL_CG_F32     FP32 CG operator pass, chunk kernel (apply + p update + p.q)
+ *   PS_KERNEL_SHARED_F32 FP32 CG shared-node reduction kernel
+ *   PS_KERNEL_UPDATE_F32 FP32 CG vector update kernel
+ *   PS_KERNEL_RESID_F64  FP64 true-residual chunk kernel
+ *   PS_KERNEL_CG_F64     FP64 CG operator pass, chunk kernel
+ * Errors: PS_EINVAL, PS_ESTATE (coefficients not set). */
+#define PS_KERNEL_CG_F32     0
+#define PS_KERNEL_SHARED_F32 1
+#define PS_KERNEL_UPDATE_F32 2
+#define PS_KERNEL_RESID_F64  3
+#define PS_KERNEL_CG_F64     4
+int ps_profile_kernel(ps_mesh *mesh, int which, int reps, void *stream, double *avg_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRESSURE_H */

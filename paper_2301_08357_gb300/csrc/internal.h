@@ -1,0 +1,87 @@
+// Internal host-side types of libpressure (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <set>
+#include <vector>
+
+#include "mesh_prep.h"
+#include "ops.cuh"
+
+struct ps_mesh;
+
+namespace ps {
+
+struct DevAlloc {
+    void *p;
+    size_t bytes;
+};
+
+struct GraphRec {
+    int kind;    // precision (0 FP32, 1 FP64) + 2 * (no preconditioner)
+    int iters;
+    cudaGraphExec_t exec;
+};
+
+// Per-mesh solver workspace (allocated on first apply/solve).
+struct Workspace {
+    bool ready = false;
+    std::vector<DevAlloc> allocs;
+    double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *part32 = nullptr;
+    double *part64 = nullptr;
+    double *dot1 = nullptr, *dot2 = nullptr;
+    CgState *st = nullptr;
+    CgState *h_st = nullptr;
+    float *one32 = nullptr;
+    double *one64 = nullptr;
+    bool ones_ready = false;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphRec> graphs;
+};
+
+int dalloc(ps_ctx *ctx, void **p, size_t bytes, std::vector<DevAlloc> &owner);
+void dfree_all(ps_ctx *ctx, std::vector<DevAlloc> &owner);
+int grid_for(int64_t n, int dev_sms);
+int cuda_status(cudaError_t e);
+SmemLayout make_layout(int esz, int nsz, int max_loc, int max_elem, int max_sh);
+int ensure_workspace(ps_mesh *m);
+template <typename T, int MODE>
+int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
+
+// batched.cu
+int batched_set_attrs();
+void batched_release_mesh(ps_mesh *m);
+
+}  // namespace ps
+
+struct ps_ctx {
+    int device = 0;
+    size_t budget = 0;
+    int sms = 1;
+    std::atomic<int64_t> bytes{0};
+    std::recursive_mutex mu_r;
+    std::mutex mu;
+    std::set<ps_mesh *> meshes;
+    int *d_err = nullptr;
+};
+
+struct ps_mesh {
+    ps_ctx *ctx = nullptr;
+    ps::PrepMesh prep;
+    ps::MeshDev dev;
+    std::vector<ps::DevAlloc> allocs;
+    int32_t *d_loc_node = nullptr, *d_elem_src = nullptr;
+    int32_t *d_old_of_new = nullptr, *d_new_of_old = nullptr;
+    int grid2 = 1, grid3 = 1;
+    bool coeff_ok = false, alpha_set = false;
+    double dt2 = 0.0;
+    ps::Workspace ws;
+    void *batch_ws = nullptr;   // owned by batched.cu
+    int64_t launches = 0;       // kernel launches of the current call
+};
+
+extern "C" void ps_set_last_error(const char *msg);

@@ -1,0 +1,461 @@
+// Chunked matrix-free P1 operator and the fused CG kernels.
+//
+// One thread block processes one chunk (layout.h):
+//   1. one elected thread moves the chunk's static data (node records,
+//      local connectivity, beta*dt^2, incidence lists, shared-node ids) into
+//      shared memory with bulk copies signalled on an mbarrier;
+//   2. the block gathers the input vector for its local nodes (contiguous for
+//      interior nodes, through the shared-node ids otherwise), masking
+//      Dirichlet nodes; in CG mode it forms the new search direction
+//      p = D^-1 r + beta p on the fly and stores it for its interior nodes;
+//   3. one thread per element computes the element's (d+1) contributions into
+//      shared memory;
+//   4. one thread per local node sums its contributions in incidence-list
+//      order and writes its row (interior node) or a partial sum (shared node).
+// A second kernel adds the partial sums of shared nodes in a fixed order.
+// Dot products are accumulated in FP64 per block and reduced by the last
+// block to finish, in a fixed order, so every result is bitwise reproducible.
+#pragma once
+#include "device.cuh"
+
+namespace ps {
+
+enum Mode : int { kApply = 0, kCG = 1, kResid = 2, kDiag = 3 };
+
+struct SmemLayout {
+    uint32_t node, val, lconn, bdt2, incp, inc, shid, contrib, red, bar, total;
+};
+
+struct MeshDev {
+    int dim, n_chunks;
+    int64_t n_nodes, n_int, n_shared, n_pad;
+    const ChunkDesc *chunks;
+    const ushort4 *lconn;
+    const uint16_t *incp, *inc;
+    const int32_t *sh_ids, *shr_ptr, *shr_slot;
+    const NodeF *node32;
+    const NodeD *node64;
+    const float *bdt2_32;
+    const double *bdt2_64;
+    const float *dinv32;
+    const double *dinv64;
+    const uint8_t *dirichlet;
+    int *err;
+    SmemLayout sm32, sm64;
+};
+
+// Scalars of one CG run, kept on the device.
+struct CgState {
+    double rz, pq, alpha, beta, rr, rr0, stop_rr, bb;
+    long long iters, max_iters;
+    int done, status;
+    unsigned int cnt_a, cnt_b;
+    int host_done_idx, pad;
+};
+
+enum CgStatus : int { kCgRunning = 0, kCgConverged = 1, kCgMaxIter = 2, kCgBreakdown = 3 };
+
+template <typename T>
+struct VecArgs {
+    const T *x;      // apply / resid: input vector
+    T *y;            // apply: output; cg: q; resid: r
+    const T *b;      // resid: right-hand side (0 on Dirichlet nodes)
+    T *p;            // cg: search direction (read old, write new)
+    const T *r;      // cg: residual
+    const T *dinv;   // cg: Jacobi inverse diagonal (0 on Dirichlet nodes)
+    T *partial;      // [sh_total] partial sums of shared local nodes
+    double *dotbuf;  // per-block dot partials
+    CgState *st;
+    int *host_done;  // optional host-mapped copy of st->done
+};
+
+__device__ __forceinline__ float cg_dir(float dinv, float r, float beta, float p) {
+    return __fmaf_rn(beta, p, __fmul_rn(dinv, r));
+}
+__device__ __forceinline__ double cg_dir(double dinv, double r, double beta, double p) {
+    return __fma_rn(beta, p, __dmul_rn(dinv, r));
+}
+
+__device__ __forceinline__ int ld_flag(const int *p) { return *(volatile const int *)p; }
+
+// Process chunk c.  Returns this thread's share of the mode's dot product
+// (CG: p.q, resid: r.r over interior nodes).  `phase` is the mbarrier parity
+// to wait for; it flips on return.  Block-uniform; contains __syncthreads.
+template <int D, typename T, int MODE>
+__device__ double process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, unsigned char *smem,
+                                const SmemLayout &L, uint32_t &phase, T beta_cg, bool &failed) {
+    using N4 = typename NodeOf<T>::type;
+    constexpr int NV = D + 1;
+    const ChunkDesc cd = m.chunks[c];
+    N4 *s_node = reinterpret_cast<N4 *>(smem + L.node);
+    T *s_val = reinterpret_cast<T *>(smem + L.val);
+    ushort4 *s_lconn = reinterpret_cast<ushort4 *>(smem + L.lconn);
+    T *s_bdt2 = reinterpret_cast<T *>(smem + L.bdt2);
+    uint16_t *s_incp = reinterpret_cast<uint16_t *>(smem + L.incp);
+    uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
+    int32_t *s_shid = reinterpret_cast<int32_t *>(smem + L.shid);
+    T *s_contrib = reinterpret_cast<T *>(smem + L.contrib);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+
+    const int n_loc = cd.n_loc, n_int = cd.n_int, n_sh = cd.n_sh, n_elem = cd.n_elem;
+    const int e_pad = (n_elem + kElemPad - 1) / kElemPad * kElemPad;
+    const int incp_n = (n_loc + 1 + kIncpPad - 1) / kIncpPad * kIncpPad;
+    const int sh_n = (n_sh + kShPad - 1) / kShPad * kShPad;
+    const N4 *gnode = (sizeof(T) == 4) ? reinterpret_cast<const N4 *>(m.node32) : reinterpret_cast<const N4 *>(m.node64);
+    const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
+
+    if (threadIdx.x == 0) {
+        const uint32_t b_node = (uint32_t)n_loc * sizeof(N4);
+        const uint32_t b_lconn = (uint32_t)e_pad * 8u;
+        const uint32_t b_bdt2 = (uint32_t)e_pad * sizeof(T);
+        const uint32_t b_incp = (uint32_t)incp_n * 2u;
+        const uint32_t b_inc = (uint32_t)e_pad * 8u;
+        const uint32_t b_sh = (uint32_t)sh_n * 4u;
+        mbar_arrive_expect_tx(s_bar, b_node + b_lconn + b_bdt2 + b_incp + b_inc + b_sh);
+        bulk_g2s(s_node, gnode + cd.node_off, b_node, s_bar);
+        bulk_g2s(s_lconn, m.lconn + cd.elem_off, b_lconn, s_bar);
+        bulk_g2s(s_bdt2, gbdt2 + cd.elem_off, b_bdt2, s_bar);
+        bulk_g2s(s_incp, m.incp + cd.incp_off, b_incp, s_bar);
+        bulk_g2s(s_inc, m.inc + (size_t)cd.elem_off * 4, b_inc, s_bar);
+        if (b_sh) bulk_g2s(s_shid, m.sh_ids + cd.sh_off, b_sh, s_bar);
+    }
+    bool ok = mbar_wait_bounded(s_bar, phase);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(m.err, kErrMbarTimeout);
+        mbar_wait_bounded(s_bar, phase);   // let copies in flight land before leaving
+        phase ^= 1u;
+        failed = true;
+        return 0.0;
+    }
+    phase ^= 1u;
+
+    // ---- gather the input vector (masked on Dirichlet nodes)
+    if (MODE != kDiag) {
+        for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+            const int g = l < n_int ? cd.int_begin + l : s_shid[l - n_int];
+            T v;
+            if (MODE == kCG) {
+                v = cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]);
+                if (is_dirichlet(s_node[l].w)) v = T(0);
+                if (l < n_int) a.p[g] = v;
+            } else {
+                v = is_dirichlet(s_node[l].w) ? T(0) : a.x[g];
+            }
+            s_val[l] = v;
+        }
+        __syncthreads();
+    }
+
+    // ---- element contributions
+    for (int e = threadIdx.x; e < n_elem; e += blockDim.x) {
+        const ushort4 lc = s_lconn[e];
+        const T bd = s_bdt2[e];
+        T o0, o1, o2, o3 = T(0);
+        if (D == 3) {
+            if (MODE == kDiag)
+                elem_diag_3d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_node[lc.w], bd, o0, o1, o2, o3);
+            else
+                elem_apply_3d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_node[lc.w], s_val[lc.x], s_val[lc.y],
+                                 s_val[lc.z], s_val[lc.w], bd, o0, o1, o2, o3);
+        } else {
+            if (MODE == kDiag)
+                elem_diag_2d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], bd, o0, o1, o2);
+            else
+                elem_apply_2d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_val[lc.x], s_val[lc.y], s_val[lc.z], bd,
+                                 o0, o1, o2);
+        }
+        T *dst = s_contrib + 4 * e;
+        dst[0] = o0;
+        dst[1] = o1;
+        dst[2] = o2;
+        if (NV == 4) dst[3] = o3;
+    }
+    __syncthreads();
+
+    // ---- per-node sums in incidence order
+    double dot = 0.0;
+    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+        const int b = s_incp[l], e = s_incp[l + 1];
+        T s = T(0);
+        for (int k = b; k < e; ++k) s += s_contrib[s_inc[k]];
+        const bool dir = is_dirichlet(s_node[l].w);
+        if (dir) s = T(0);
+        if (l < n_int) {
+            const int g = cd.int_begin + l;
+            if (MODE == kApply) {
+                a.y[g] = s;
+            } else if (MODE == kCG) {
+                a.y[g] = s;
+                dot += (double)s_val[l] * (double)s;
+            } else if (MODE == kResid) {
+                const T rv = dir ? T(0) : a.b[g] - s;
+                a.y[g] = rv;
+                dot += (double)rv * (double)rv;
+            } else {  // diag: T == double here
+                const double dv = dir ? 0.0 : 1.0 / (double)s;
+                const_cast<double *>(m.dinv64)[g] = dv;
+                const_cast<float *>(m.dinv32)[g] = (float)dv;
+            }
+        } else {
+            a.partial[cd.sh_off + (l - n_int)] = s;
+        }
+    }
+    return dot;
+}
+
+// Kernel 1: one block per chunk.
+template <int D, typename T, int MODE>
+__global__ void __launch_bounds__(256) k_chunks(MeshDev m, VecArgs<T> a) {
+    if (MODE == kCG && ld_flag(&a.st->done)) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const SmemLayout &L = (sizeof(T) == 4) ? m.sm32 : m.sm64;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    double *s_red = reinterpret_cast<double *>(smem + L.red);
+    if (threadIdx.x == 0) {
+        mbar_init(s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool failed = false;
+    const T beta_cg = (MODE == kCG) ? (T)a.st->beta : T(0);
+    double dot = process_chunk<D, T, MODE>(m, a, blockIdx.x, smem, L, phase, beta_cg, failed);
+    if (MODE == kCG || MODE == kResid) {
+        dot = block_sum(dot, s_red);
+        if (threadIdx.x == 0) a.dotbuf[blockIdx.x] = dot;
+    }
+}
+
+// Kernel 2: shared nodes sum their partials in slot order.  The last block to
+// finish also reduces all dot partials (kernel 1's n_first blocks, then this
+// kernel's blocks) and updates the CG scalars.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_first) {
+    if (MODE == kCG && ld_flag(&a.st->done)) return;
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    const T beta_cg = (MODE == kCG) ? (T)a.st->beta : T(0);
+    double dot = 0.0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m.n_shared;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = m.n_int + s;
+        T sum = T(0);
+        const int kb = m.shr_ptr[s], ke = m.shr_ptr[s + 1];
+        for (int k = kb; k < ke; ++k) sum += a.partial[m.shr_slot[k]];
+        const bool dir = m.dirichlet[g] != 0;
+        if (MODE == kApply) {
+            a.y[g] = sum;
+        } else if (MODE == kCG) {
+            T v = cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]);
+            if (dir) v = T(0);
+            a.p[g] = v;
+            a.y[g] = sum;
+            dot += (double)v * (double)sum;
+        } else if (MODE == kResid) {
+            const T rv = dir ? T(0) : a.b[g] - sum;
+            a.y[g] = rv;
+            dot += (double)rv * (double)rv;
+        } else {
+            const double dv = dir ? 0.0 : 1.0 / (double)sum;
+            const_cast<double *>(m.dinv64)[g] = dv;
+            const_cast<float *>(m.dinv32)[g] = (float)dv;
+        }
+    }
+    if (MODE != kCG && MODE != kResid) return;
+    dot = block_sum(dot, s_red);
+    if (threadIdx.x == 0) {
+        a.dotbuf[n_first + blockIdx.x] = dot;
+        __threadfence();
+        const unsigned int t = atomicAdd(&a.st->cnt_a, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double tot = block_sum_array(a.dotbuf, n_first + gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+        CgState *st = a.st;
+        st->cnt_a = 0;
+        if (MODE == kCG) {
+            st->pq = tot;
+            if (!(tot > 0.0) || !isfinite(tot)) {
+                st->status = kCgBreakdown;
+                st->done = 1;
+                if (a.host_done) *(volatile int *)a.host_done = 1;
+            } else {
+                st->alpha = st->rz / tot;
+            }
+        } else {
+            st->rr = tot;
+        }
+    }
+}
+
+// Kernel 3: x += alpha p; r -= alpha q; z = D^-1 r; rz = r.z; rr = r.r; the
+// last block decides convergence and forms beta.  Vectors are padded to a
+// multiple of 4 entries with zeros.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(int64_t n_pad, T *__restrict__ x, T *__restrict__ r,
+                                                   const T *__restrict__ p, const T *__restrict__ q,
+                                                   const T *__restrict__ dinv, CgState *st, double *dotbuf,
+                                                   int *host_done) {
+    if (ld_flag(&st->done)) return;
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    const T al = (T)st->alpha;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+        const T xi = x[i] + al * p[i];
+        const T ri = r[i] - al * q[i];
+        x[i] = xi;
+        r[i] = ri;
+        const T zi = dinv[i] * ri;
+        rz += (double)ri * (double)zi;
+        rr += (double)ri * (double)ri;
+    }
+    rz = block_sum(rz, s_red);
+    rr = block_sum(rr, s_red);
+    if (threadIdx.x == 0) {
+        dotbuf[blockIdx.x] = rz;
+        dotbuf[gridDim.x + blockIdx.x] = rr;
+        __threadfence();
+        const unsigned int t = atomicAdd(&st->cnt_b, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double rz_new = block_sum_array(dotbuf, gridDim.x, s_red);
+    const double rr_new = block_sum_array(dotbuf + gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+        st->cnt_b = 0;
+        st->iters += 1;
+        st->rr = rr_new;
+        int done = 0;
+        if (!isfinite(rz_new) || !isfinite(rr_new)) {
+            st->status = kCgBreakdown;
+            done = 1;
+        } else if (rr_new <= st->stop_rr) {
+            st->status = kCgConverged;
+            done = 1;
+        } else if (st->iters >= st->max_iters) {
+            st->status = kCgMaxIter;
+            done = 1;
+        } else {
+            st->beta = rz_new / st->rz;
+            st->rz = rz_new;
+        }
+        if (done) {
+            st->done = 1;
+            if (host_done) *(volatile int *)host_done = 1;
+        }
+    }
+}
+
+// Start of an inner FP32 solve of A d = r64 * scale (mixed mode), or of an
+// FP64 PCG run from a residual already in r (mode FP64: rsrc == nullptr).
+// Sets d = 0, p = 0, rz = r.D^-1 r, rr0 = r.r, stop_rr = tol2 * (rr0 or bb).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_start(int64_t n_pad, const double *__restrict__ rsrc, double scale,
+                                                  T *__restrict__ r, T *__restrict__ d, T *__restrict__ p,
+                                                  const T *__restrict__ dinv, CgState *st, double *dotbuf,
+                                                  double tol2, int relative, long long max_iters) {
+    __shared__ double s_red[32];
+    __shared__ bool s_last;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+        T ri = rsrc ? (T)(rsrc[i] * scale) : r[i];
+        if (rsrc) r[i] = ri;
+        if (d) d[i] = T(0);
+        p[i] = T(0);
+        rz += (double)ri * (double)(dinv[i] * ri);
+        rr += (double)ri * (double)ri;
+    }
+    rz = block_sum(rz, s_red);
+    rr = block_sum(rr, s_red);
+    if (threadIdx.x == 0) {
+        dotbuf[blockIdx.x] = rz;
+        dotbuf[gridDim.x + blockIdx.x] = rr;
+        __threadfence();
+        const unsigned int t = atomicAdd(&st->cnt_b, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double rz0 = block_sum_array(dotbuf, gridDim.x, s_red);
+    const double rr0 = block_sum_array(dotbuf + gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+        st->cnt_b = 0;
+        st->cnt_a = 0;
+        st->rz = rz0;
+        st->rr0 = rr0;
+        st->rr = rr0;
+        st->beta = 0.0;
+        st->alpha = 0.0;
+        st->iters = 0;
+        st->max_iters = max_iters;
+        st->stop_rr = relative ? tol2 * rr0 : tol2;
+        st->status = kCgRunning;
+        st->done = 0;
+        if (!isfinite(rz0) || !isfinite(rr0)) {
+            st->status = kCgBreakdown;
+            st->done = 1;
+        } else if (rr0 <= st->stop_rr || rr0 == 0.0) {
+            st->status = kCgConverged;
+            st->done = 1;
+        }
+    }
+}
+
+// x64 += d32 / scale (mixed-mode correction), vectors padded to 4.
+static __global__ void k_correct(int64_t n_pad, double *__restrict__ x, const float *__restrict__ d, double inv_scale) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)d[i] * inv_scale;
+}
+
+// out_new[i] = in_old[old_of_new[i]] (0 on Dirichlet nodes); element types converted.
+template <typename TI, typename TO>
+__global__ void k_perm_in(int64_t n, const TI *__restrict__ in, TO *__restrict__ out, const int32_t *__restrict__ old_of_new,
+                          const uint8_t *__restrict__ dirichlet) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dirichlet[i] ? TO(0) : (TO)in[old_of_new[i]];
+}
+// out_old[j] = in_new[new_of_old[j]]
+template <typename TI, typename TO>
+__global__ void k_perm_out(int64_t n, const TI *__restrict__ in, TO *__restrict__ out, const int32_t *__restrict__ new_of_old) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[j] = (TO)in[new_of_old[j]];
+}
+
+// Fill the alpha slot of every node record: w = +alpha, or -alpha (sign bit
+// set, also for alpha = 0) on Dirichlet nodes.
+static __global__ void k_set_alpha(int64_t n_loc, const int32_t *__restrict__ loc_node, const double *__restrict__ alpha_new,
+                            const uint8_t *__restrict__ dirichlet, NodeF *node32, NodeD *node64) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_loc; k += (int64_t)gridDim.x * blockDim.x) {
+        const int g = loc_node[k];
+        const double a = alpha_new[g];
+        double w64 = a;
+        float w32 = (float)a;
+        if (dirichlet[g]) {
+            w64 = __longlong_as_double(__double_as_longlong(w64) | (long long)0x8000000000000000ULL);
+            w32 = __int_as_float(__float_as_int(w32) | (int)0x80000000u);
+        }
+        node64[k].w = w64;
+        node32[k].w = w32;
+    }
+}
+
+// bdt2[k] = beta[elem_src[k]] * dt2 (0 on padding slots).
+static __global__ void k_set_beta(int64_t n, const int32_t *__restrict__ elem_src, const double *__restrict__ beta,
+                           double dt2, float *b32, double *b64) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int e = elem_src[k];
+        const double v = e >= 0 ? beta[e] * dt2 : 0.0;
+        b64[k] = v;
+        b32[k] = (float)v;
+    }
+}
+
+}  // namespace ps

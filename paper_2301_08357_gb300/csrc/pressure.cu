@@ -1,0 +1,953 @@
+// libpressure: host side of the C ABI declared in include/pressure.h.
+//
+// Context and mesh objects, device memory accounting, coefficient upload, the
+// matrix-free apply, and the single-mesh solvers (plain FP64 PCG; FP32 PCG
+// inside FP64 defect correction).  CG iterations are captured once per mesh
+// into CUDA graphs of `graph_iters` iterations; every kernel of an iteration
+// first checks the device-side done flag, so a graph launched after
+// convergence costs only its launch latency.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/pressure.h"
+#include "internal.h"
+
+using namespace ps;
+
+namespace ps {
+
+const int kBlock = 256;
+
+static int sm_count_of(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+int grid_for(int64_t n, int dev_sms) {
+    int64_t g = (n + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)dev_sms * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ---- context-accounted device allocations
+int dalloc(ps_ctx *ctx, void **p, size_t bytes, std::vector<DevAlloc> &owner) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    if (ctx->budget && ctx->bytes + (int64_t)bytes > (int64_t)ctx->budget) return PS_ENOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return PS_ENOMEM;
+    }
+    ctx->bytes += (int64_t)bytes;
+    owner.push_back(DevAlloc{*p, bytes});
+    return PS_OK;
+}
+
+void dfree_all(ps_ctx *ctx, std::vector<DevAlloc> &owner) {
+    for (auto &a : owner) {
+        cudaFree(a.p);
+        ctx->bytes -= (int64_t)a.bytes;
+    }
+    owner.clear();
+}
+
+static uint32_t align128(uint64_t v) { return (uint32_t)((v + 127) / 128 * 128); }
+
+SmemLayout make_layout(int esz, int nsz, int max_loc, int max_elem, int max_sh) {
+    SmemLayout L;
+    const uint64_t epad = (uint64_t)round_up(max_elem, kElemPad);
+    uint64_t off = 0;
+    L.node = (uint32_t)off;    off += align128((uint64_t)max_loc * nsz);
+    L.val = (uint32_t)off;     off += align128((uint64_t)max_loc * esz);
+    L.lconn = (uint32_t)off;   off += align128(epad * 8);
+    L.bdt2 = (uint32_t)off;    off += align128(epad * esz);
+    L.incp = (uint32_t)off;    off += align128((uint64_t)round_up(max_loc + 1, kIncpPad) * 2);
+    L.inc = (uint32_t)off;     off += align128(epad * 8);
+    L.shid = (uint32_t)off;    off += align128((uint64_t)round_up(max_sh > 0 ? max_sh : 1, kShPad) * 4);
+    L.contrib = (uint32_t)off; off += align128(epad * 4 * esz);
+    L.red = (uint32_t)off;     off += 32 * 8;
+    L.bar = (uint32_t)off;     off += 16;
+    L.total = (uint32_t)off;
+    return L;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PS_OK;
+    return e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA;
+}
+
+}  // namespace ps
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) {                            \
+            ps_set_last_error(cudaGetErrorString(_e));      \
+            return cuda_status(_e);                         \
+        }                                                   \
+    } while (0)
+
+#define RC(call)                      \
+    do {                              \
+        int _r = (call);              \
+        if (_r != PS_OK) return _r;   \
+    } while (0)
+
+static thread_local std::string g_last_error;
+extern "C" void ps_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+extern "C" const char *ps_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------- kernels setup
+namespace ps {
+
+static int set_smem_attrs() {
+    const int lim = 227 * 1024;
+    CK(cudaFuncSetAttribute(k_chunks<2, float, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, float, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<2, double, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, double, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<2, float, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, float, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<2, double, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, double, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<2, double, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, double, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<2, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(k_chunks<3, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return batched_set_attrs();
+}
+
+// Launch kernel 1 + kernel 2 of one operator pass (mode MODE, type T).
+template <typename T, int MODE>
+int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s) {
+    const SmemLayout &L = sizeof(T) == 4 ? m->dev.sm32 : m->dev.sm64;
+    if (m->dev.dim == 2)
+        k_chunks<2, T, MODE><<<m->dev.n_chunks, kBlock, L.total, s>>>(m->dev, a);
+    else
+        k_chunks<3, T, MODE><<<m->dev.n_chunks, kBlock, L.total, s>>>(m->dev, a);
+    k_shared<T, MODE><<<m->grid2, kBlock, 0, s>>>(m->dev, a, m->dev.n_chunks);
+    CK(cudaGetLastError());
+    m->launches += 2;
+    return PS_OK;
+}
+
+template int launch_pass<float, kApply>(ps_mesh *, const VecArgs<float> &, cudaStream_t);
+template int launch_pass<double, kApply>(ps_mesh *, const VecArgs<double> &, cudaStream_t);
+template int launch_pass<double, kResid>(ps_mesh *, const VecArgs<double> &, cudaStream_t);
+template int launch_pass<float, kCG>(ps_mesh *, const VecArgs<float> &, cudaStream_t);
+template int launch_pass<double, kCG>(ps_mesh *, const VecArgs<double> &, cudaStream_t);
+
+}  // namespace ps
+
+// ---------------------------------------------------------------- ABI: library / ctx
+extern "C" const char *ps_version(void) { return "libpressure 0.1 (sm_103a)"; }
+
+extern "C" const char *ps_status_str(int s) {
+    switch (s) {
+        case PS_OK: return "ok";
+        case PS_PENDING: return "pending";
+        case PS_EINVAL: return "invalid argument";
+        case PS_ENOMEM: return "out of device memory / over HBM budget";
+        case PS_ENOTCONV: return "not converged";
+        case PS_EBREAKDOWN: return "CG breakdown";
+        case PS_ETIMEOUT: return "device wait timed out";
+        case PS_ECUDA: return "CUDA error";
+        case PS_ESTATE: return "call out of order";
+        case PS_ENOTFOUND: return "not found";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int ps_ctx_create(ps_ctx **out, int device, size_t budget) {
+    if (!out) return PS_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return PS_EINVAL;
+    CK(cudaSetDevice(device));
+    RC(set_smem_attrs());
+    ps_ctx *c = new (std::nothrow) ps_ctx();
+    if (!c) return PS_ENOMEM;
+    c->device = device;
+    c->budget = budget;
+    c->sms = sm_count_of(device);
+    int *e = nullptr;
+    if (cudaMalloc(&e, 64) != cudaSuccess) {
+        delete c;
+        return PS_ENOMEM;
+    }
+    cudaMemset(e, 0, 64);
+    c->d_err = e;
+    *out = c;
+    return PS_OK;
+}
+
+extern "C" void ps_ctx_destroy(ps_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    std::vector<ps_mesh *> ms(c->meshes.begin(), c->meshes.end());
+    for (ps_mesh *m : ms) ps_mesh_free(m);
+    cudaFree(c->d_err);
+    delete c;
+}
+
+extern "C" int64_t ps_ctx_bytes_in_use(const ps_ctx *c) { return c ? (int64_t)c->bytes.load() : 0; }
+
+// ---------------------------------------------------------------- ABI: mesh
+template <typename V>
+static int upload(ps_ctx *c, ps_mesh *m, V **dst, const void *src, size_t bytes) {
+    void *p = nullptr;
+    RC(dalloc(c, &p, bytes, m->allocs));
+    if (src && bytes) CK(cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice));
+    *dst = reinterpret_cast<V *>(p);
+    return PS_OK;
+}
+
+static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
+    MeshDev &d = m->dev;
+    std::memset(&d, 0, sizeof(d));
+    d.dim = pm.dim;
+    d.n_chunks = pm.n_chunks;
+    d.n_nodes = pm.n_nodes;
+    d.n_int = pm.n_int;
+    d.n_shared = pm.n_shared;
+    d.n_pad = round_up(pm.n_nodes, 4);
+    ChunkDesc *ch;
+    RC(upload(c, m, &ch, pm.chunks.data(), pm.chunks.size() * sizeof(ChunkDesc)));
+    d.chunks = ch;
+    ushort4 *lc;
+    RC(upload(c, m, &lc, pm.lconn.data(), pm.lconn.size() * 2));
+    d.lconn = lc;
+    uint16_t *u;
+    RC(upload(c, m, &u, pm.incp.data(), pm.incp.size() * 2));
+    d.incp = u;
+    RC(upload(c, m, &u, pm.inc.data(), pm.inc.size() * 2));
+    d.inc = u;
+    int32_t *i32;
+    RC(upload(c, m, &i32, pm.sh_ids.data(), pm.sh_ids.size() * 4));
+    d.sh_ids = i32;
+    RC(upload(c, m, &i32, pm.shr_ptr.data(), pm.shr_ptr.size() * 4));
+    d.shr_ptr = i32;
+    RC(upload(c, m, &i32, pm.shr_slot.data(), pm.shr_slot.size() * 4));
+    d.shr_slot = i32;
+    RC(upload(c, m, &m->d_loc_node, pm.loc_node.data(), pm.loc_node.size() * 4));
+    RC(upload(c, m, &m->d_elem_src, pm.elem_src.data(), pm.elem_src.size() * 4));
+    RC(upload(c, m, &m->d_old_of_new, pm.old_of_new.data(), pm.old_of_new.size() * 4));
+    RC(upload(c, m, &m->d_new_of_old, pm.new_of_old.data(), pm.new_of_old.size() * 4));
+    // Dirichlet flags, padded to n_pad with 1 so padding rows stay zero
+    std::vector<uint8_t> dir(d.n_pad, 1);
+    std::memcpy(dir.data(), pm.dirichlet_new.data(), pm.n_nodes);
+    uint8_t *du;
+    RC(upload(c, m, &du, dir.data(), dir.size()));
+    d.dirichlet = du;
+    // node records: coordinates relative to the chunk origin, alpha set later
+    {
+        std::vector<NodeF> nf(pm.loc_total);
+        std::vector<NodeD> nd(pm.loc_total);
+        for (int64_t k = 0; k < pm.loc_total; ++k) {
+            const double *r = &pm.loc_rel[k * pm.dim];
+            nd[k].x = r[0];
+            nd[k].y = r[1];
+            nd[k].z = pm.dim == 3 ? r[2] : 0.0;
+            nd[k].w = 0.0;
+            nf[k].x = (float)nd[k].x;
+            nf[k].y = (float)nd[k].y;
+            nf[k].z = (float)nd[k].z;
+            nf[k].w = 0.0f;
+        }
+        NodeF *pf;
+        NodeD *pd;
+        RC(upload(c, m, &pf, nf.data(), nf.size() * sizeof(NodeF)));
+        RC(upload(c, m, &pd, nd.data(), nd.size() * sizeof(NodeD)));
+        d.node32 = pf;
+        d.node64 = pd;
+    }
+    float *f;
+    double *g;
+    RC(upload(c, m, &f, nullptr, pm.elem_total * 4));
+    d.bdt2_32 = f;
+    RC(upload(c, m, &g, nullptr, pm.elem_total * 8));
+    d.bdt2_64 = g;
+    RC(upload(c, m, &f, nullptr, d.n_pad * 4));
+    CK(cudaMemset(f, 0, d.n_pad * 4));
+    d.dinv32 = f;
+    RC(upload(c, m, &g, nullptr, d.n_pad * 8));
+    CK(cudaMemset(g, 0, d.n_pad * 8));
+    d.dinv64 = g;
+    d.err = c->d_err;
+    d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_elem, pm.max_sh);
+    d.sm64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_elem, pm.max_sh);
+    if (d.sm64.total > 227 * 1024) {
+        ps_set_last_error("chunk too large for shared memory; lower chunk_elems");
+        return PS_EINVAL;
+    }
+    m->grid2 = grid_for(pm.n_shared, c->sms);
+    m->grid3 = grid_for(d.n_pad, c->sms);
+    return PS_OK;
+}
+
+extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
+                              const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
+                              ps_mesh **out) {
+    if (!c || !out || !coords || !conn) return PS_EINVAL;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    PrepOptions po;
+    if (opts) {
+        po.chunk_elems = opts->chunk_elems;
+        po.chunk_nodes_max = opts->chunk_nodes_max;
+    }
+    ps_mesh *m = new (std::nothrow) ps_mesh();
+    if (!m) return PS_ENOMEM;
+    m->ctx = c;
+    std::string err = prepare_mesh(dim, n_nodes, coords, n_elems, conn, dirichlet, po, m->prep);
+    if (!err.empty()) {
+        ps_set_last_error(err.c_str());
+        delete m;
+        return PS_EINVAL;
+    }
+    int rc = mesh_upload_impl(c, m, m->prep);
+    if (rc != PS_OK) {
+        dfree_all(c, m->allocs);
+        delete m;
+        return rc;
+    }
+    // host copies that are no longer needed
+    m->prep.loc_rel.clear();
+    m->prep.loc_rel.shrink_to_fit();
+    c->meshes.insert(m);
+    *out = m;
+    return PS_OK;
+}
+
+static void free_workspace(ps_mesh *m) {
+    Workspace &w = m->ws;
+    for (auto &g : w.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    w.graphs.clear();
+    if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
+    w.cap_stream = nullptr;
+    if (w.h_st) cudaFreeHost(w.h_st);
+    w.h_st = nullptr;
+    dfree_all(m->ctx, w.allocs);
+    w.ready = false;
+}
+
+extern "C" void ps_mesh_free(ps_mesh *m) {
+    if (!m) return;
+    ps_ctx *c = m->ctx;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_workspace(m);
+    batched_release_mesh(m);
+    dfree_all(c, m->allocs);
+    c->meshes.erase(m);
+    delete m;
+}
+
+extern "C" int ps_mesh_get_stats(const ps_mesh *m, ps_mesh_stats *o) {
+    if (!m || !o) return PS_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    const PrepMesh &p = m->prep;
+    o->n_nodes = p.n_nodes;
+    o->n_elems = p.n_elems;
+    o->n_free = p.n_free;
+    o->dim = p.dim;
+    o->n_chunks = p.n_chunks;
+    o->n_shared = p.n_shared;
+    o->chunk_node_refs = p.loc_total;
+    int64_t b = 0;
+    for (auto &a : m->allocs) b += (int64_t)a.bytes;
+    for (auto &a : m->ws.allocs) b += (int64_t)a.bytes;
+    o->device_bytes = b;
+    o->max_chunk_elems = p.max_elem;
+    o->max_chunk_nodes = p.max_loc;
+    return PS_OK;
+}
+
+// ---------------------------------------------------------------- ABI: coefficients
+static int coeff_upload(ps_mesh *m, const double *alpha, const double *beta, double dt2) {
+    ps_ctx *c = m->ctx;
+    const PrepMesh &p = m->prep;
+    MeshDev &d = m->dev;
+    std::vector<DevAlloc> tmp;
+    void *dbeta = nullptr;
+    int rc = dalloc(c, &dbeta, p.n_elems * 8, tmp);
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMemcpy(dbeta, beta, p.n_elems * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_set_beta<<<grid_for(p.elem_total, c->sms), kBlock>>>(p.elem_total, m->d_elem_src, (const double *)dbeta, dt2,
+                                                                 const_cast<float *>(d.bdt2_32),
+                                                                 const_cast<double *>(d.bdt2_64));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && alpha) {
+        std::vector<double> an(p.n_nodes);
+        for (int64_t i = 0; i < p.n_nodes; ++i) an[p.new_of_old[i]] = alpha[i];
+        void *dal = nullptr;
+        rc = dalloc(c, &dal, p.n_nodes * 8, tmp);
+        if (rc != PS_OK) {
+            dfree_all(c, tmp);
+            return rc;
+        }
+        e = cudaMemcpy(dal, an.data(), p.n_nodes * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            k_set_alpha<<<grid_for(p.loc_total, c->sms), kBlock>>>(p.loc_total, m->d_loc_node, (const double *)dal,
+                                                                    d.dirichlet, const_cast<NodeF *>(d.node32),
+                                                                    const_cast<NodeD *>(d.node64));
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        // Jacobi diagonal, FP64 element arithmetic, both precisions stored
+        VecArgs<double> a;
+        std::memset(&a, 0, sizeof(a));
+        void *part = nullptr;
+        rc = dalloc(c, &part, (p.sh_total > 0 ? p.sh_total : 1) * 8, tmp);
+        if (rc != PS_OK) {
+            dfree_all(c, tmp);
+            return rc;
+        }
+        a.partial = (double *)part;
+        if (d.dim == 2)
+            k_chunks<2, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total>>>(d, a);
+        else
+            k_chunks<3, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total>>>(d, a);
+        k_shared<double, kDiag><<<m->grid2, kBlock>>>(d, a, d.n_chunks);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    dfree_all(c, tmp);
+    if (e != cudaSuccess) {
+        ps_set_last_error(cudaGetErrorString(e));
+        return cuda_status(e);
+    }
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        return PS_ETIMEOUT;
+    }
+    m->dt2 = dt2;
+    m->coeff_ok = true;
+    return PS_OK;
+}
+
+extern "C" int ps_coeff_set(ps_mesh *m, const double *alpha, const double *beta, double dt2) {
+    if (!m || !alpha || !beta) return PS_EINVAL;
+    if (!(dt2 > 0.0) || !std::isfinite(dt2)) return PS_EINVAL;
+    const PrepMesh &p = m->prep;
+    for (int64_t i = 0; i < p.n_nodes; ++i)
+        if (!(alpha[i] >= 0.0) || !std::isfinite(alpha[i])) return PS_EINVAL;
+    for (int64_t e = 0; e < p.n_elems; ++e)
+        if (!(beta[e] > 0.0) || !std::isfinite(beta[e])) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    int rc = coeff_upload(m, alpha, beta, dt2);
+    if (rc == PS_OK) m->alpha_set = true;
+    return rc;
+}
+
+extern "C" int ps_coeff_set_beta(ps_mesh *m, const double *beta) {
+    if (!m || !beta) return PS_EINVAL;
+    if (!m->alpha_set) return PS_ESTATE;
+    const PrepMesh &p = m->prep;
+    for (int64_t e = 0; e < p.n_elems; ++e)
+        if (!(beta[e] > 0.0) || !std::isfinite(beta[e])) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    return coeff_upload(m, nullptr, beta, m->dt2);
+}
+
+// ---------------------------------------------------------------- workspace
+namespace ps {
+
+int ensure_workspace(ps_mesh *m) {
+    Workspace &w = m->ws;
+    if (w.ready) return PS_OK;
+    ps_ctx *c = m->ctx;
+    const int64_t np = m->dev.n_pad;
+    const int64_t sh = m->prep.sh_total > 0 ? m->prep.sh_total : 1;
+    void *p;
+    auto A = [&](void **dst, size_t bytes) -> int {
+        int r = dalloc(c, dst, bytes, w.allocs);
+        if (r == PS_OK) cudaMemset(*dst, 0, bytes);
+        return r;
+    };
+    int rc = PS_OK;
+#define WA(field, T, n)                                   \
+    if (rc == PS_OK) {                                    \
+        rc = A(&p, (size_t)(n) * sizeof(T));              \
+        w.field = (T *)p;                                 \
+    }
+    WA(x64, double, np);
+    WA(b64, double, np);
+    WA(r64, double, np);
+    WA(p64, double, np);
+    WA(q64, double, np);
+    WA(x32, float, np);
+    WA(r32, float, np);
+    WA(p32, float, np);
+    WA(q32, float, np);
+    WA(part32, float, sh);
+    WA(part64, double, sh);
+    WA(dot1, double, m->dev.n_chunks + m->grid2 + 8);
+    WA(dot2, double, 2 * m->grid3 + 8);
+    WA(st, CgState, 1);
+#undef WA
+    if (rc != PS_OK) {
+        dfree_all(c, w.allocs);
+        return rc;
+    }
+    CK(cudaHostAlloc((void **)&w.h_st, sizeof(CgState), cudaHostAllocDefault));
+    CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+    w.ready = true;
+    return PS_OK;
+}
+
+static VecArgs<float> cg_args32(ps_mesh *m) {
+    Workspace &w = m->ws;
+    VecArgs<float> a;
+    std::memset(&a, 0, sizeof(a));
+    a.y = w.q32;
+    a.p = w.p32;
+    a.r = w.r32;
+    a.dinv = m->dev.dinv32;
+    a.partial = w.part32;
+    a.dotbuf = w.dot1;
+    a.st = w.st;
+    return a;
+}
+
+static VecArgs<double> cg_args64(ps_mesh *m) {
+    Workspace &w = m->ws;
+    VecArgs<double> a;
+    std::memset(&a, 0, sizeof(a));
+    a.y = w.q64;
+    a.p = w.p64;
+    a.r = w.r64;
+    a.dinv = m->dev.dinv64;
+    a.partial = w.part64;
+    a.dotbuf = w.dot1;
+    a.st = w.st;
+    return a;
+}
+
+// Enqueue `iters` CG iterations (no host sync) of precision T.
+template <typename T>
+static int enqueue_cg_iters(ps_mesh *m, int iters, cudaStream_t s) {
+    Workspace &w = m->ws;
+    for (int k = 0; k < iters; ++k) {
+        if (sizeof(T) == 4) {
+            VecArgs<float> a = cg_args32(m);
+            RC((launch_pass<float, kCG>(m, a, s)));
+            k_cg_update<float><<<m->grid3, kBlock, 0, s>>>(m->dev.n_pad, w.x32, w.r32, w.p32, w.q32, m->dev.dinv32,
+                                                           w.st, w.dot2, nullptr);
+            m->launches += 1;
+        } else {
+            VecArgs<double> a = cg_args64(m);
+            RC((launch_pass<double, kCG>(m, a, s)));
+            k_cg_update<double><<<m->grid3, kBlock, 0, s>>>(m->dev.n_pad, w.x64, w.r64, w.p64, w.q64,
+                                                            m->dev.dinv64, w.st, w.dot2, nullptr);
+            m->launches += 1;
+        }
+        CK(cudaGetLastError());
+    }
+    return PS_OK;
+}
+
+// Run CG iterations until the device state says done: graph batches of
+// `gi` iterations followed by a copy of the state to pinned host memory.
+template <typename T>
+static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
+    Workspace &w = m->ws;
+    const int kind = (sizeof(T) == 4 ? 0 : 1) + (jac ? 0 : 2);
+    if (gi <= 0) {
+        const int batch = 16;
+        for (;;) {
+            RC(enqueue_cg_iters<T>(m, batch, s));
+            CK(cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (w.h_st->done) return PS_OK;
+        }
+    }
+    GraphRec *g = nullptr;
+    for (auto &r : w.graphs)
+        if (r.kind == kind && r.iters == gi) g = &r;
+    if (!g) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t saved_launches = m->launches;
+        int rc = enqueue_cg_iters<T>(m, gi, w.cap_stream);
+        m->launches = saved_launches;
+        cudaError_t e2 = cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, w.cap_stream);
+        cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
+        if (rc != PS_OK) return rc;
+        CK(e2);
+        CK(e);
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        w.graphs.push_back(GraphRec{kind, gi, ex});
+        g = &w.graphs.back();
+    }
+    for (;;) {
+        CK(cudaGraphLaunch(g->exec, s));
+        m->launches += 3 * (int64_t)gi;
+        CK(cudaStreamSynchronize(s));
+        if (w.h_st->done) return PS_OK;
+    }
+}
+
+static int read_state(ps_mesh *m, cudaStream_t s, CgState *out) {
+    CK(cudaMemcpyAsync(m->ws.h_st, m->ws.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = *m->ws.h_st;
+    return PS_OK;
+}
+
+// FP64 true residual r64 = b64 - A x64; returns ||r||^2 (free nodes).
+static int true_residual(ps_mesh *m, cudaStream_t s, double *rr) {
+    Workspace &w = m->ws;
+    VecArgs<double> a;
+    std::memset(&a, 0, sizeof(a));
+    a.x = w.x64;
+    a.y = w.r64;
+    a.b = w.b64;
+    a.partial = w.part64;
+    a.dotbuf = w.dot1;
+    a.st = w.st;
+    RC((launch_pass<double, kResid>(m, a, s)));
+    CgState h;
+    RC(read_state(m, s, &h));
+    *rr = h.rr;
+    return PS_OK;
+}
+
+static int check_dev_err(ps_ctx *c) {
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        return PS_ETIMEOUT;
+    }
+    return PS_OK;
+}
+
+int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cudaStream_t s) {
+    Workspace &w = m->ws;
+    const int64_t np = m->dev.n_pad;
+    const int g3 = m->grid3;
+    // ||b||^2 through the residual pass with x = 0 would cost an apply; use a
+    // start kernel on b instead (rz unused).
+    k_cg_start<double><<<g3, kBlock, 0, s>>>(np, w.b64, 1.0, w.r64, nullptr, w.p64, m->dev.dinv64, w.st, w.dot2, 0.0,
+                                             0, 0);
+    CK(cudaGetLastError());
+    m->launches += 1;
+    CgState h;
+    RC(read_state(m, s, &h));
+    const double bb = h.rr0;
+    info->bnorm = std::sqrt(bb);
+    info->n_free = m->prep.n_free;
+    const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const double stop_abs2 = tol * tol * (bb > 0 ? bb : 1.0);
+    const int64_t max_it = o.max_iters > 0 ? o.max_iters : 100000;
+    int64_t used = 0, outer = 0;
+    double rr = 0;
+    int status = PS_ENOTCONV;
+    const bool jac = o.precond != PS_PRECOND_NONE;
+    const float *dinv32 = m->dev.dinv32;
+    const double *dinv64 = m->dev.dinv64;
+    if (!jac) {
+        // unpreconditioned: D^-1 = 1 on free nodes (kept in a workspace vector)
+        if (!w.ones_ready) {
+            RC(dalloc(m->ctx, (void **)&w.one32, np * 4, w.allocs));
+            RC(dalloc(m->ctx, (void **)&w.one64, np * 8, w.allocs));
+            std::vector<float> f(np);
+            std::vector<double> d(np);
+            std::vector<uint8_t> dir(np, 1);
+            for (int64_t i = 0; i < m->prep.n_nodes; ++i) dir[i] = m->prep.dirichlet_new[i];
+            for (int64_t i = 0; i < np; ++i) {
+                f[i] = dir[i] ? 0.f : 1.f;
+                d[i] = dir[i] ? 0.0 : 1.0;
+            }
+            CK(cudaMemcpy(w.one32, f.data(), np * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(w.one64, d.data(), np * 8, cudaMemcpyHostToDevice));
+            w.ones_ready = true;
+        }
+        dinv32 = w.one32;
+        dinv64 = w.one64;
+    }
+    MeshDev saved = m->dev;
+    m->dev.dinv32 = dinv32;
+    m->dev.dinv64 = dinv64;
+    const int gi = o.graph_iters == 0 ? 32 : o.graph_iters;
+    int rc = PS_OK;
+    if (o.mode == PS_MODE_FP64) {
+        const int max_restarts = o.max_outer > 0 ? o.max_outer : 40;
+        for (;;) {
+            rc = true_residual(m, s, &rr);
+            if (rc != PS_OK) break;
+            ++outer;
+            if (rr <= stop_abs2) { status = PS_OK; break; }
+            if (used >= max_it || outer > max_restarts) { status = PS_ENOTCONV; break; }
+            k_cg_start<double><<<g3, kBlock, 0, s>>>(np, nullptr, 1.0, w.r64, nullptr, w.p64, m->dev.dinv64, w.st,
+                                                     w.dot2, stop_abs2, 0, max_it - used);
+            m->launches += 1;
+            if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
+            if ((rc = run_cg_until_done<double>(m, gi, jac, s)) != PS_OK) break;
+            RC(read_state(m, s, &h));
+            used += h.iters;
+            if (h.status == kCgBreakdown) { status = PS_EBREAKDOWN; rc = PS_OK; break; }
+        }
+    } else {
+        const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+        const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
+        for (;;) {
+            rc = true_residual(m, s, &rr);
+            if (rc != PS_OK) break;
+            ++outer;
+            if (rr <= stop_abs2) { status = PS_OK; break; }
+            if (used >= max_it || outer > max_outer) { status = PS_ENOTCONV; break; }
+            const double scale = 1.0 / std::sqrt(rr);
+            k_cg_start<float><<<g3, kBlock, 0, s>>>(np, w.r64, scale, w.r32, w.x32, w.p32, m->dev.dinv32, w.st,
+                                                    w.dot2, itol * itol, 1, max_it - used);
+            m->launches += 1;
+            if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
+            if ((rc = run_cg_until_done<float>(m, gi, jac, s)) != PS_OK) break;
+            RC(read_state(m, s, &h));
+            used += h.iters;
+            if (h.status == kCgBreakdown) { status = PS_EBREAKDOWN; rc = PS_OK; break; }
+            k_correct<<<g3, kBlock, 0, s>>>(np, w.x64, w.x32, 1.0 / scale);
+            m->launches += 1;
+            if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
+        }
+    }
+    m->dev = saved;
+    if (rc != PS_OK) return rc;
+    RC(check_dev_err(m->ctx));
+    info->iters_outer = outer;
+    info->iters_inner = used;
+    info->rel_res = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    info->converged = status == PS_OK;
+    info->status = status;
+    return status;
+}
+
+}  // namespace ps
+
+// ---------------------------------------------------------------- ABI: apply / solve
+extern "C" int ps_pressure_apply(ps_mesh *m, const void *x, void *y, int prec, void *stream) {
+    if (!m || !x || !y || (prec != PS_F32 && prec != PS_F64) || x == y) return PS_EINVAL;
+    if (!m->coeff_ok) return PS_ESTATE;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    RC(ensure_workspace(m));
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &w = m->ws;
+    const int64_t n = m->dev.n_nodes;
+    const int g = grid_for(n, m->ctx->sms);
+    if (prec == PS_F32) {
+        k_perm_in<float, float><<<g, kBlock, 0, s>>>(n, (const float *)x, w.r32, m->d_old_of_new, m->dev.dirichlet);
+        VecArgs<float> a;
+        std::memset(&a, 0, sizeof(a));
+        a.x = w.r32;
+        a.y = w.q32;
+        a.partial = w.part32;
+        RC((launch_pass<float, kApply>(m, a, s)));
+        k_perm_out<float, float><<<g, kBlock, 0, s>>>(n, w.q32, (float *)y, m->d_new_of_old);
+    } else {
+        k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, (const double *)x, w.r64, m->d_old_of_new, m->dev.dirichlet);
+        VecArgs<double> a;
+        std::memset(&a, 0, sizeof(a));
+        a.x = w.r64;
+        a.y = w.q64;
+        a.partial = w.part64;
+        RC((launch_pass<double, kApply>(m, a, s)));
+        k_perm_out<double, double><<<g, kBlock, 0, s>>>(n, w.q64, (double *)y, m->d_new_of_old);
+    }
+    CK(cudaGetLastError());
+    return PS_OK;
+}
+
+extern "C" void ps_solve_opts_default(ps_solve_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-10;
+    o->max_iters = 100000;
+    o->mode = PS_MODE_MIXED;
+    o->precond = PS_PRECOND_JACOBI;
+    o->inner_tol = 1e-4;
+    o->max_outer = 40;
+    o->graph_iters = 32;
+}
+
+extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const ps_solve_opts *opts,
+                                 ps_solve_info *info, void *stream) {
+    if (!m || !b || !x) return PS_EINVAL;
+    if (!m->coeff_ok) return PS_ESTATE;
+    ps_solve_opts o;
+    if (opts) o = *opts; else ps_solve_opts_default(&o);
+    if (o.mode != PS_MODE_FP64 && o.mode != PS_MODE_MIXED) return PS_EINVAL;
+    ps_solve_info local;
+    ps_solve_info *inf = info ? info : &local;
+    std::memset(inf, 0, sizeof(*inf));
+    auto t0 = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    RC(ensure_workspace(m));
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &w = m->ws;
+    const int64_t n = m->dev.n_nodes;
+    const int g = grid_for(n, m->ctx->sms);
+    m->launches = 0;
+    k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, b, w.b64, m->d_old_of_new, m->dev.dirichlet);
+    k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, x, w.x64, m->d_old_of_new, m->dev.dirichlet);
+    m->launches += 2;
+    CK(cudaGetLastError());
+    int rc = solve_internal(m, o, inf, s);
+    if (rc == PS_OK || rc == PS_ENOTCONV || rc == PS_EBREAKDOWN) {
+        k_perm_out<double, double><<<g, kBlock, 0, s>>>(n, w.x64, x, m->d_new_of_old);
+        m->launches += 1;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+    }
+    inf->kernel_launches = m->launches;
+    inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+// ---------------------------------------------------------------- debug hooks (host only)
+extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
+                                const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
+                                ps_mesh_stats *stats) {
+    if (!coords || !conn) return PS_EINVAL;
+    PrepOptions po;
+    if (opts) {
+        po.chunk_elems = opts->chunk_elems;
+        po.chunk_nodes_max = opts->chunk_nodes_max;
+    }
+    PrepMesh pm;
+    std::string err = prepare_mesh(dim, n_nodes, coords, n_elems, conn, dirichlet, po, pm);
+    if (!err.empty()) {
+        ps_set_last_error(err.c_str());
+        return PS_EINVAL;
+    }
+    err = validate_prep(pm, conn);
+    if (!err.empty()) {
+        ps_set_last_error(err.c_str());
+        return PS_ESTATE;
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->n_nodes = pm.n_nodes;
+        stats->n_elems = pm.n_elems;
+        stats->n_free = pm.n_free;
+        stats->dim = pm.dim;
+        stats->n_chunks = pm.n_chunks;
+        stats->n_shared = pm.n_shared;
+        stats->chunk_node_refs = pm.loc_total;
+        stats->max_chunk_elems = pm.max_elem;
+        stats->max_chunk_nodes = pm.max_loc;
+        SmemLayout l64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_elem, pm.max_sh);
+        stats->device_bytes = l64.total;  // shared memory per block of the FP64 pass
+    }
+    return PS_OK;
+}
+
+// ---------------------------------------------------------------- kernel timing
+extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, double *avg_ms) {
+    if (!m || !avg_ms || reps < 1 || which < 0 || which > 4) return PS_EINVAL;
+    if (!m->coeff_ok) return PS_ESTATE;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    RC(ensure_workspace(m));
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &w = m->ws;
+    MeshDev &d = m->dev;
+    // a state that keeps every kernel running (done = 0, huge stop criterion unused)
+    CgState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.rz = 1.0;
+    hs.alpha = 0.0;
+    hs.beta = 0.0;
+    hs.max_iters = 1LL << 60;
+    hs.stop_rr = -1.0;
+    CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto one = [&]() {
+        switch (which) {
+            case 0: {
+                VecArgs<float> a = cg_args32(m);
+                if (d.dim == 2) k_chunks<2, float, kCG><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                else k_chunks<3, float, kCG><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                break;
+            }
+            case 1: {
+                VecArgs<float> a = cg_args32(m);
+                k_shared<float, kCG><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
+                break;
+            }
+            case 2:
+                k_cg_update<float><<<m->grid3, kBlock, 0, s>>>(d.n_pad, w.x32, w.r32, w.p32, w.q32, d.dinv32, w.st,
+                                                               w.dot2, nullptr);
+                break;
+            case 3: {
+                VecArgs<double> a;
+                std::memset(&a, 0, sizeof(a));
+                a.x = w.x64;
+                a.y = w.q64;
+                a.b = w.b64;
+                a.partial = w.part64;
+                a.dotbuf = w.dot1;
+                a.st = w.st;
+                if (d.dim == 2) k_chunks<2, double, kResid><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                else k_chunks<3, double, kResid><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                break;
+            }
+            case 4: {
+                VecArgs<double> a = cg_args64(m);
+                if (d.dim == 2) k_chunks<2, double, kCG><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                else k_chunks<3, double, kCG><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                break;
+            }
+        }
+    };
+    one();  // warm-up
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) one();
+    CK(cudaEventRecord(e1, s));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *avg_ms = (double)ms / reps;
+    // leave a clean state for the next solve
+    std::memset(&hs, 0, sizeof(hs));
+    hs.done = 1;
+    CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return check_dev_err(m->ctx);
+}

@@ -1,0 +1,94 @@
+"""CPU-only checks of the C ABI library: it loads, exports every function that
+include/pressure.h declares, and its host preprocessing (chunking, renumbering,
+incidence lists) satisfies the invariants the kernels rely on.  No device
+call is made here."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pressure.h")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2301_08357_gb300 import build
+    build.build()
+    from paper_2301_08357_gb300 import pressure
+    return pressure
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ps_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported(P):
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.check_output(["nm", "-D", "--defined-only", P.LIB_PATH]).decode()
+    exported = set(re.findall(r"\bT (ps_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the binding wraps exactly these names
+    for n in names:
+        assert n in P.SIGNATURES, n
+
+
+def test_version_and_status_strings(P):
+    assert "sm_103a" in P.ps_version()
+    assert P.ps_status_str(P.PS_OK) == "ok"
+    assert "budget" in P.ps_status_str(P.PS_ENOMEM)
+
+
+@pytest.mark.parametrize("dim,n,chunk", [(2, 8, 0), (2, 17, 37), (3, 4, 0), (3, 7, 50), (3, 6, 1000)])
+def test_prepare_invariants(P, dim, n, chunk):
+    from paper_2301_08357_gb300 import synthetic as S
+    case = (S.make_c1 if dim == 2 else S.make_c2)(n=n, seed=n)
+    s = P.ps_debug_prepare(dim, case.coords, case.conn, case.dirichlet, chunk_elems=chunk)
+    assert s.n_nodes == case.n_nodes and s.n_elems == case.n_elems
+    assert s.n_free == case.n_free
+    assert s.n_chunks >= 1
+    if chunk:
+        assert s.max_chunk_elems <= chunk
+    assert s.chunk_node_refs >= case.n_nodes
+    # shuffled numbering gives the same sizes and still passes the invariants
+    sh = S.shuffle_case(case, seed=7)
+    s2 = P.ps_debug_prepare(dim, sh.coords, sh.conn, sh.dirichlet, chunk_elems=chunk)
+    assert s2.n_free == s.n_free
+
+
+def test_prepare_chunk_node_cap(P):
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_c2(n=8)
+    s = P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=512, chunk_nodes_max=64)
+    assert s.max_chunk_nodes <= 64
+
+
+def test_prepare_rejects_bad_input(P):
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_c1(n=4)
+    bad = case.conn.copy()
+    bad[3, 1] = case.n_nodes          # out of range
+    with pytest.raises(P.PressureError) as e:
+        P.ps_debug_prepare(2, case.coords, bad, case.dirichlet)
+    assert e.value.status == P.PS_EINVAL
+    flat = case.conn.copy()
+    flat[0] = [0, 1, 2]               # collinear vertices on the bottom edge
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, case.coords, flat, case.dirichlet)
+    rep = case.conn.copy()
+    rep[0, 2] = rep[0, 0]             # repeated vertex
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, case.coords, rep, case.dirichlet)
+    nanc = case.coords.copy()
+    nanc[5, 0] = np.nan
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, nanc, case.conn, case.dirichlet)
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(4, case.coords, case.conn, case.dirichlet)

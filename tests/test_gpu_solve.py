@@ -1,0 +1,191 @@
+"""Parity of the CUDA pressure solves (through the C ABI) with the FP64 oracle.
+
+Gates (the CG stop test is the true FP64 relative residual, computed here
+again by the oracle on the GPU's solution):
+  * ||b - A x_gpu|| / ||b|| <= 1e-10 for a solve run at tol 1e-10;
+  * ||x_gpu - x*|| / ||x*|| <= 1e-9 against the oracle's solution x* (solved
+    to 1e-13 or stagnation), for a solve run at the tightened tolerance
+    1e-9 / kappa_est (floored at 1e-13): a residual of 1e-10 bounds the error
+    only by kappa * 1e-10.
+Both precision modes (plain FP64 PCG; FP32 PCG inside FP64 defect
+correction), with and without Jacobi, cold and warm starts, shuffled
+numberings, degenerate right-hand sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_08357_gb300 import synthetic as S
+from tests.gpu_util import upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2301_08357_gb300 import build
+    build.build()
+    from paper_2301_08357_gb300 import pressure
+    return pressure
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(P, torch_mod):
+    c = P.ps_ctx_create(0)
+    yield c
+    P.ps_ctx_destroy(c)
+
+
+def gpu_solve(P, torch, m, b, x0, **kw):
+    bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
+    xd = torch.as_tensor(x0, dtype=torch.float64, device="cuda").clone()
+    st, info = P.ps_pressure_solve(m, bd, xd, P.make_opts(**kw))
+    return st, info, xd.cpu().numpy()
+
+
+MODES = [(0, "fp64"), (1, "mixed")]
+SMALL = [
+    ("c1_64", lambda: S.make_c1(64), 0),
+    ("c1_32_shuffled", lambda: S.shuffle_case(S.make_c1(32)), 41),
+    ("c2_n12", lambda: S.make_c2(12), 0),
+    ("c2_n10_shuffled", lambda: S.shuffle_case(S.make_c2(10), seed=5), 77),
+    ("c3_n12_warm", lambda: S.make_c3(12), 0),
+    ("batch_mesh_3", lambda: S.make_batch_case(3, lo=2e3, hi=6e3), 0),
+]
+
+
+def _rhs_and_guess(case, A):
+    if "xstar" in case.extra:            # stiff case: b = A xstar, warm start
+        return A.apply(case.extra["xstar"]), case.x0
+    return case.b, case.x0
+
+
+@pytest.mark.parametrize("name,make,chunk", SMALL, ids=[c[0] for c in SMALL])
+@pytest.mark.parametrize("mode,mname", MODES, ids=[m[1] for m in MODES])
+def test_solve_matches_oracle(P, torch_mod, ctx, name, make, chunk, mode, mname):
+    case = make()
+    A = oracle.PressureMatrix.from_case(case)
+    b, x0 = _rhs_and_guess(case, A)
+    xs, st, it, rr = A.cg(b, x0_full=x0, precond=1, tol=1e-13)
+    m = upload(P, ctx, case, chunk)
+    try:
+        status, info, x = gpu_solve(P, torch_mod, m, b, x0, mode=mode, tol=1e-10)
+        assert status == P.PS_OK and info.converged == 1
+        assert info.rel_res <= 1e-10
+        res = A.residual(b, x)
+        assert res <= 1e-10 * 1.05, (name, mname, res, info.rel_res)
+        assert np.all(x[case.dirichlet.astype(bool)] == 0.0)
+        # error gate at the tightened tolerance
+        status, info, x = gpu_solve(P, torch_mod, m, b, x0, mode=mode, tol=1e-13)
+        err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+        assert err <= 1e-9, (name, mname, err, info.rel_res)
+    finally:
+        P.ps_mesh_free(m)
+
+
+@pytest.mark.parametrize("mode,mname", MODES, ids=[m[1] for m in MODES])
+def test_solve_full_size_c2(P, torch_mod, ctx, mode, mname):
+    """64^3 Kuhn cube, 270,400 free nodes: the timed workload's size."""
+    case = S.make_c2()
+    A = oracle.PressureMatrix.from_case(case)
+    m = upload(P, ctx, case)
+    try:
+        status, info, x = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=mode, tol=1e-10)
+        assert status == P.PS_OK
+        res = A.residual(case.b, x)
+        assert res <= 1e-10 * 1.05, (mname, res, info.rel_res)
+        xs, st, it, rr = A.cg(case.b, precond=1, tol=1e-13)
+        status, info, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=mode, tol=1e-13)
+        err = np.linalg.norm(x2 - xs) / np.linalg.norm(xs)
+        assert err <= 1e-9, (mname, err)
+    finally:
+        P.ps_mesh_free(m)
+
+
+def test_solve_is_deterministic(P, torch_mod, ctx):
+    case = S.make_c2(14)
+    m = upload(P, ctx, case)
+    try:
+        _, i1, x1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
+        _, i2, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
+        assert np.array_equal(x1, x2)
+        assert i1.iters_inner == i2.iters_inner
+        _, j1, y1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1, graph_iters=-1)
+        assert np.array_equal(x1, y1)
+    finally:
+        P.ps_mesh_free(m)
+
+
+def test_solve_degenerate_inputs(P, torch_mod, ctx):
+    case = S.make_c1(16)
+    A = oracle.PressureMatrix.from_case(case)
+    m = upload(P, ctx, case)
+    try:
+        z = np.zeros(case.n_nodes)
+        st, info, x = gpu_solve(P, torch_mod, m, z, z, mode=1)
+        assert st == P.PS_OK and np.all(x == 0.0)
+        # the exact solution as first guess: converged without iterations
+        xs, _, _, _ = A.cg(case.b, precond=1, tol=1e-14)
+        st, info, x = gpu_solve(P, torch_mod, m, case.b, xs, mode=0)
+        assert st == P.PS_OK and info.iters_inner == 0
+        # Dirichlet entries of b and x0 are ignored
+        b2 = case.b.copy()
+        b2[case.dirichlet.astype(bool)] = 1e3
+        x02 = np.where(case.dirichlet.astype(bool), 7.0, 0.0)
+        st, info, x = gpu_solve(P, torch_mod, m, b2, x02, mode=1)
+        assert A.residual(case.b, x) <= 1.05e-10
+        # an iteration cap is reported, not hidden
+        st, info, x = gpu_solve(P, torch_mod, m, case.b, z, mode=0, max_iters=3)
+        assert st == P.PS_ENOTCONV and info.converged == 0
+    finally:
+        P.ps_mesh_free(m)
+
+
+def test_solve_without_dirichlet_and_without_preconditioner(P, torch_mod, ctx):
+    """Pure Neumann: the mass term alone keeps A SPD."""
+    case = S.make_c2(6)
+    case.dirichlet[:] = 0
+    A = oracle.PressureMatrix.from_case(case)
+    b = np.random.default_rng(2).standard_normal(case.n_nodes)
+    m = upload(P, ctx, case)
+    try:
+        for mode in (0, 1):
+            st, info, x = gpu_solve(P, torch_mod, m, b, np.zeros_like(b), mode=mode, precond=0)
+            assert st == P.PS_OK
+            assert A.residual(b, x) <= 1.05e-10
+    finally:
+        P.ps_mesh_free(m)
+
+
+def test_poisson_limit_alpha_zero(P, torch_mod, ctx):
+    """alpha = 0: the pressure Poisson system of the low-Mach limit."""
+    case = S.make_c2(8)
+    case.alpha[:] = 0.0
+    A = oracle.PressureMatrix.from_case(case)
+    m = upload(P, ctx, case)
+    try:
+        st, info, x = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
+        assert st == P.PS_OK and A.residual(case.b, x) <= 1.05e-10
+    finally:
+        P.ps_mesh_free(m)
+
+
+def test_beta_update_between_solves(P, torch_mod, ctx):
+    """ps_coeff_set_beta (Picard / time-step drift) changes the operator."""
+    case = S.make_c2(8)
+    m = upload(P, ctx, case)
+    try:
+        beta2 = case.beta * np.exp(0.3 * np.random.default_rng(4).standard_normal(case.n_elems))
+        P.ps_coeff_set_beta(m, beta2)
+        A2 = oracle.PressureMatrix.from_case(case, beta=beta2)
+        st, info, x = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
+        assert st == P.PS_OK and A2.residual(case.b, x) <= 1.05e-10
+    finally:
+        P.ps_mesh_free(m)
