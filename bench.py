@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     return ap.parse_args()
 
 
@@ -172,9 +173,11 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    import contextlib
     from __graft_entry__ import build
     if rank == 0 or ws == 1:
-        build()
+        with contextlib.redirect_stdout(sys.stderr):   # keep stdout to the one JSON line
+            build()
     if ws > 1:
         torch.distributed.barrier()
     from paper_2301_08357_gb300 import pressure as P
@@ -182,7 +185,7 @@ def run_ours(args):
 
     case = S.make_c2(args.n)
     ctx = P.ps_ctx_create(local)
-    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet)
+    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk)
     P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()
@@ -259,6 +262,9 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: the FP32 CG operator pass (chunk kernel)
     which = P.PS_KERNEL_CG_F32 if mode == P.PS_MODE_MIXED else P.PS_KERNEL_CG_F64
     kern_ms = P.ps_profile_kernel(m, which, reps=50, stream=stream)
+    kern_other = {name: P.ps_profile_kernel(m, k, reps=50, stream=stream)
+                  for name, k in (("shared_f32", P.PS_KERNEL_SHARED_F32), ("update_f32", P.PS_KERNEL_UPDATE_F32),
+                                  ("resid_f64", P.PS_KERNEL_RESID_F64))}
     E, N = stats.n_elems, stats.n_nodes
     if mode == P.PS_MODE_MIXED:
         # per element: 4 x u16 local vertex ids + 4 x u16 incidence entries + f32 beta*dt^2 = 20 B
@@ -271,6 +277,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "kernel": "k_chunks<3,%s,kCG>" % ("float" if mode == P.PS_MODE_MIXED else "double"),
             "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+            "other_kernels_ms": kern_other, "chunks": stats.n_chunks,
+            "shared_node_frac": stats.n_shared / stats.n_nodes,
             "note": "64^3 working set (~%.0f MB/launch) is L2-resident" % (alg_bytes / 1e6)}
 
     cpu = None

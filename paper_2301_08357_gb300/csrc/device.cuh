@@ -72,6 +72,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// ---------------------------------------------------------------- completion counter
+// "Last block" detection: every block publishes its partial result with a
+// plain store, then increments a device-scope counter with acquire-release
+// semantics (no sequentially consistent fence); the block that sees
+// count == gridDim - 1 has acquired every other block's partial.
+__device__ __forceinline__ unsigned int atomic_add_acq_rel(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -100,6 +111,81 @@ __device__ __forceinline__ double block_sum_array(const double *a, int n, double
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(a + i);
     return block_sum(s, red);
 }
+
+// ---------------------------------------------------------------- double-float dot accumulation
+// FP64 instructions are scarce on this part (2 DFMA/clk/SM), so dot products
+// of FP32 vectors are accumulated in "double-float" form: an unevaluated sum
+// hi + lo of two floats, updated with Knuth's error-free TwoSum and the
+// FMA-based exact product (Dekker / Ogita-Rump-Oishi "Dot2").  The result is
+// as accurate as a sum carried in twice the FP32 precision; it is converted to
+// FP64 once per warp and the per-warp values are summed in FP64 in a fixed
+// order.  The intrinsics below are never contracted or reassociated.
+struct DotF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ void merge(float h2, float l2) {
+        const float s = __fadd_rn(hi, h2);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, l2), e);
+    }
+};
+// FP64 accumulator with the same interface (FP64 vectors).
+struct DotD {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+};
+template <typename T> struct DotOf;
+template <> struct DotOf<float> { using type = DotF; };
+template <> struct DotOf<double> { using type = DotD; };
+
+// Block-wide sum of accumulators in a fixed order; all threads get the FP64
+// result.  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(const DotF &a, double *red) {
+    float hi = a.hi, lo = a.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        DotF t;
+        t.hi = hi;
+        t.lo = lo;
+        t.merge(h2, l2);
+        hi = t.hi;
+        lo = t.lo;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = (double)hi + (double)lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        red[32] = t;
+    }
+    __syncthreads();
+    const double r = red[32];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_sum(const DotD &a, double *red) { return block_sum(a.v, red); }
 
 // ---------------------------------------------------------------- P1 element kernels
 // Notation: vertices p0..pd with coordinates (x,y[,z]) and nodal alpha in w;
@@ -204,6 +290,137 @@ __device__ __forceinline__ void elem_diag_2d(const N4 &p0, const N4 &p1, const N
     o0 = cm * (T(2) * S + T(4) * a0) + kc * (c0x * c0x + c0y * c0y);
     o1 = cm * (T(2) * S + T(4) * a1) + kc * (c1x * c1x + c1y * c1y);
     o2 = cm * (T(2) * S + T(4) * a2) + kc * (c2x * c2x + c2y * c2y);
+}
+
+// ---------------------------------------------------------------- star patches
+// One thread evaluates a whole patch (layout.h): element j is (a, b, r_j,
+// r_{j+1}) in 3D and (a, r_j, r_{j+1}) in 2D.  With e1 = b - a and
+// d_j = r_j - a, the cofactor vectors of element j are
+//   c1 = d_j x d_{j+1},  c2 = -(e1 x d_{j+1}),  c3 = e1 x d_j   (3D)
+//   c1 = perp(d_{j+1}),  c2 = -perp(d_j), perp(v) = (v.y, -v.x)  (2D)
+// so e1 x d_j and the node data of r_j carry over from element j-1 to j.
+// The per-element arithmetic is the one of elem_apply_3d / elem_diag_3d.
+// out[slot]: 0 -> a, 1 -> b, 2 + j -> r_j (j = 0..m); other slots untouched.
+__device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }
+
+template <int D, typename T, typename N4, bool DIAG>
+__device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const T *__restrict__ s_val,
+                                           const uint16_t *__restrict__ rec, const T *__restrict__ bdt2,
+                                           T *__restrict__ out) {
+    const int pm = rec[0];
+    const int ia = rec[1];
+    const N4 A = s_node[ia];
+    const T va = DIAG ? T(0) : s_val[ia];
+    const T aa = fabs(A.w);
+    T acc_a = T(0), acc_b = T(0);
+    if (D == 3) {
+        const int ib = rec[2];
+        const N4 B = s_node[ib];
+        const T vb = DIAG ? T(0) : s_val[ib];
+        const T ab = fabs(B.w);
+        const T e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
+        int i0 = rec[3];
+        N4 R0 = s_node[i0];
+        T v0 = DIAG ? T(0) : s_val[i0];
+        T d0x = R0.x - A.x, d0y = R0.y - A.y, d0z = R0.z - A.z;
+        T w0x = e1y * d0z - e1z * d0y, w0y = e1z * d0x - e1x * d0z, w0z = e1x * d0y - e1y * d0x;
+        T acc_c = T(0);
+        for (int j = 0; j < pm; ++j) {
+            const int i1 = rec[4 + j];
+            const N4 R1 = s_node[i1];
+            const T v1 = DIAG ? T(0) : s_val[i1];
+            const T d1x = R1.x - A.x, d1y = R1.y - A.y, d1z = R1.z - A.z;
+            const T w1x = e1y * d1z - e1z * d1y, w1y = e1z * d1x - e1x * d1z, w1z = e1x * d1y - e1y * d1x;
+            const T c1x = d0y * d1z - d0z * d1y, c1y = d0z * d1x - d0x * d1z, c1z = d0x * d1y - d0y * d1x;
+            const T ad = fabs(e1x * c1x + e1y * c1y + e1z * c1z);
+            const T kc = fdiv_fast(bdt2[j], T(6) * ad);
+            const T a2 = fabs(R0.w), a3 = fabs(R1.w);
+            const T S = (aa + ab) + (a2 + a3);
+            const T cm = ad * T(1.0 / 720.0);
+            T o0, o1, o2, o3;
+            if (DIAG) {
+                const T c0x = -(c1x - w1x + w0x), c0y = -(c1y - w1y + w0y), c0z = -(c1z - w1z + w0z);
+                o0 = cm * (T(2) * S + T(4) * aa) + kc * (c0x * c0x + c0y * c0y + c0z * c0z);
+                o1 = cm * (T(2) * S + T(4) * ab) + kc * (c1x * c1x + c1y * c1y + c1z * c1z);
+                o2 = cm * (T(2) * S + T(4) * a2) + kc * (w1x * w1x + w1y * w1y + w1z * w1z);
+                o3 = cm * (T(2) * S + T(4) * a3) + kc * (w0x * w0x + w0y * w0y + w0z * w0z);
+            } else {
+                // g = (vb - va) c1 + (v0 - va) c2 + (v1 - va) c3, c2 = -w1, c3 = w0
+                const T t1 = vb - va, t2 = v0 - va, t3 = v1 - va;
+                const T gx = t1 * c1x - t2 * w1x + t3 * w0x;
+                const T gy = t1 * c1y - t2 * w1y + t3 * w0y;
+                const T gz = t1 * c1z - t2 * w1z + t3 * w0z;
+                const T k1 = kc * (c1x * gx + c1y * gy + c1z * gz);
+                const T k2 = -kc * (w1x * gx + w1y * gy + w1z * gz);
+                const T k3 = kc * (w0x * gx + w0y * gy + w0z * gz);
+                const T k0 = -(k1 + k2 + k3);
+                const T X = (va + vb) + (v0 + v1);
+                const T Q = (aa * va + ab * vb) + (a2 * v0 + a3 * v1);
+                const T base = S * X + Q;
+                o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
+                o1 = cm * (base + S * vb + ab * (X + T(2) * vb)) + k1;
+                o2 = cm * (base + S * v0 + a2 * (X + T(2) * v0)) + k2;
+                o3 = cm * (base + S * v1 + a3 * (X + T(2) * v1)) + k3;
+            }
+            acc_a += o0;
+            acc_b += o1;
+            out[2 + j] = acc_c + o2;
+            acc_c = o3;
+            d0x = d1x; d0y = d1y; d0z = d1z;
+            w0x = w1x; w0y = w1y; w0z = w1z;
+            R0 = R1;
+            v0 = v1;
+        }
+        out[2 + pm] = acc_c;
+        out[0] = acc_a;
+        out[1] = acc_b;
+    } else {
+        int i0 = rec[3];
+        N4 R0 = s_node[i0];
+        T v0 = DIAG ? T(0) : s_val[i0];
+        T d0x = R0.x - A.x, d0y = R0.y - A.y;
+        T acc_c = T(0);
+        for (int j = 0; j < pm; ++j) {
+            const int i1 = rec[4 + j];
+            const N4 R1 = s_node[i1];
+            const T v1 = DIAG ? T(0) : s_val[i1];
+            const T d1x = R1.x - A.x, d1y = R1.y - A.y;
+            // c1 = perp(d1) = (d1y, -d1x), c2 = -perp(d0) = (-d0y, d0x)
+            const T c1x = d1y, c1y = -d1x, c2x = -d0y, c2y = d0x;
+            const T ad = fabs(d0x * d1y - d0y * d1x);
+            const T kc = fdiv_fast(bdt2[j], T(2) * ad);
+            const T a1 = fabs(R0.w), a2 = fabs(R1.w);
+            const T S = aa + a1 + a2;
+            const T cm = ad * T(1.0 / 120.0);
+            T o0, o1, o2;
+            if (DIAG) {
+                const T c0x = -(c1x + c2x), c0y = -(c1y + c2y);
+                o0 = cm * (T(2) * S + T(4) * aa) + kc * (c0x * c0x + c0y * c0y);
+                o1 = cm * (T(2) * S + T(4) * a1) + kc * (c1x * c1x + c1y * c1y);
+                o2 = cm * (T(2) * S + T(4) * a2) + kc * (c2x * c2x + c2y * c2y);
+            } else {
+                const T t1 = v0 - va, t2 = v1 - va;
+                const T gx = t1 * c1x + t2 * c2x, gy = t1 * c1y + t2 * c2y;
+                const T k1 = kc * (c1x * gx + c1y * gy);
+                const T k2 = kc * (c2x * gx + c2y * gy);
+                const T k0 = -(k1 + k2);
+                const T X = va + v0 + v1, Q = aa * va + a1 * v0 + a2 * v1;
+                const T base = S * X + Q;
+                o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
+                o1 = cm * (base + S * v0 + a1 * (X + T(2) * v0)) + k1;
+                o2 = cm * (base + S * v1 + a2 * (X + T(2) * v1)) + k2;
+            }
+            acc_a += o0;
+            out[2 + j] = acc_c + o1;
+            acc_c = o2;
+            d0x = d1x; d0y = d1y;
+            R0 = R1;
+            v0 = v1;
+        }
+        out[2 + pm] = acc_c;
+        out[0] = acc_a;
+    }
 }
 
 }  // namespace ps

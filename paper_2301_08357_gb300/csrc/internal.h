@@ -47,7 +47,7 @@ int dalloc(ps_ctx *ctx, void **p, size_t bytes, std::vector<DevAlloc> &owner);
 void dfree_all(ps_ctx *ctx, std::vector<DevAlloc> &owner);
 int grid_for(int64_t n, int dev_sms);
 int cuda_status(cudaError_t e);
-SmemLayout make_layout(int esz, int nsz, int max_loc, int max_elem, int max_sh);
+SmemLayout make_layout(int esz, int nsz, int max_loc, int max_patch, int max_inc, int max_sh);
 int ensure_workspace(ps_mesh *m);
 template <typename T, int MODE>
 int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);

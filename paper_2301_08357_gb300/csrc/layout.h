@@ -2,7 +2,7 @@
 // preprocessing (mesh_prep.cpp) and the CUDA kernels.
 //
 // Elements are partitioned into "chunks" of consecutive elements along a Morton
-// curve of their centroids.  Nodes touched by exactly one chunk are that
+// curve of their centroids, and inside a chunk into star-shaped patches.  Nodes touched by exactly one chunk are that
 // chunk's interior nodes; they are numbered contiguously per chunk, so the
 // chunk owns their rows outright.  Nodes touched by several chunks ("shared")
 // are numbered after all interior nodes.  A chunk computes its element
@@ -18,14 +18,26 @@
 
 namespace ps {
 
-constexpr int kElemPad = 8;     // element segments padded to 8 elements
-constexpr int kIncpPad = 8;     // incidence-pointer segments padded to 8 u16
-constexpr int kShPad = 4;       // shared-id segments padded to 4 int32
-constexpr int kMaxChunkElems = 16383;  // slot = 4 * e + v must fit in u16
+constexpr int kPatchMax = 6;     // elements per patch (star) at most
+constexpr int kPatchIds = 12;    // u16 per patch record: m, a, b, ring[0..m], padding
+constexpr int kPatchSlots = 9;   // contribution slots per patch: a, b, ring[0..6]
+constexpr int kPatchPad = 4;     // patch segments padded to 4 patches (96 B)
+constexpr int kIncPad = 8;       // incidence segments padded to 8 u16
+constexpr int kIncpPad = 8;      // incidence-pointer segments padded to 8 u16
+constexpr int kShPad = 4;        // shared-id segments padded to 4 int32
+constexpr int kMaxChunkPatches = 65535 / kPatchSlots;  // slot ids fit in u16
+
+// Elements of a chunk are grouped into "patches": the elements around one
+// pivot (an edge (a, b) in 3D, a vertex a in 2D), ordered so that element j of
+// the patch is (a, b, ring[j], ring[j+1]) in 3D and (a, ring[j], ring[j+1]) in
+// 2D, j = 0..m-1.  A closed star repeats ring[0] as ring[m].  An element that
+// joins no star is a patch of one (m = 1).  Patch record (u16): [0] = m,
+// [1] = a, [2] = b (3D), [3 + j] = ring[j], j = 0..m; all local node ids.
+// Contribution slots: 0 -> a, 1 -> b, 2 + j -> ring[j].
 
 struct ChunkDesc {
-    int32_t elem_off;   // first (padded) element of the chunk
-    int32_t n_elem;
+    int32_t patch_off;  // first (padded) patch of the chunk
+    int32_t n_patch;
     int32_t node_off;   // first entry of the chunk's node block
     int32_t n_loc;      // local nodes = n_int + n_sh
     int32_t n_int;      // interior nodes: local 0..n_int-1 = new ids int_begin + l
@@ -33,7 +45,9 @@ struct ChunkDesc {
     int32_t sh_off;     // first entry in sh_ids / partial slots (padded)
     int32_t n_sh;       // shared local nodes: local n_int + j -> sh_ids[sh_off + j]
     int32_t incp_off;   // first entry of the chunk's incidence pointers (padded)
-    int32_t pad0, pad1, pad2;
+    int32_t inc_off;    // first entry of the chunk's incidence list (padded)
+    int32_t n_inc;      // incidence entries (patch * kPatchSlots + slot)
+    int32_t n_elem;
 };
 static_assert(sizeof(ChunkDesc) == 48, "ChunkDesc layout");
 

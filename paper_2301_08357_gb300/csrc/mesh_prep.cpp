@@ -3,6 +3,7 @@
 #include "mesh_prep.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 
@@ -72,6 +73,133 @@ double simplex_det(int dim, const double *coords, const int32_t *v) {
            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
 }
 
+// One star patch under construction (chunk-local ids).
+struct PatchRec {
+    int m = 0;
+    int a = 0, b = 0;
+    int ring[kPatchMax + 1];
+    int elem[kPatchMax];   // chunk-local element index
+};
+
+// Group the elements of one chunk into star patches.  lc: [n][4] local vertex
+// ids.  Pivots are edges (3D) or vertices (2D); pivots are taken greedily by
+// the number of still unassigned elements around them (more first, ties by
+// pivot key), and the unassigned elements around a pivot are linked into
+// chains through their shared ring vertices, at most kPatchMax per chain.
+// Whatever is left becomes patches of one element.
+void build_patches(int dim, int n, const std::vector<std::array<int, 4>> &lc, std::vector<PatchRec> &out) {
+    const int nv = dim + 1;
+    out.clear();
+    std::vector<char> used(n, 0);
+    std::vector<std::pair<uint64_t, int>> inc;   // (pivot key, element)
+    inc.reserve((size_t)n * (dim == 3 ? 6 : 3));
+    for (int e = 0; e < n; ++e) {
+        if (dim == 3) {
+            for (int i = 0; i < 4; ++i)
+                for (int j = i + 1; j < 4; ++j) {
+                    uint64_t u = (uint64_t)std::min(lc[e][i], lc[e][j]);
+                    uint64_t v = (uint64_t)std::max(lc[e][i], lc[e][j]);
+                    inc.push_back({(u << 20) | v, e});
+                }
+        } else {
+            for (int i = 0; i < 3; ++i) inc.push_back({(uint64_t)lc[e][i], e});
+        }
+    }
+    std::sort(inc.begin(), inc.end());
+    std::vector<size_t> gstart;
+    for (size_t k = 0; k < inc.size(); ++k)
+        if (k == 0 || inc[k].first != inc[k - 1].first) gstart.push_back(k);
+    gstart.push_back(inc.size());
+    const size_t ng = gstart.size() - 1;
+    int maxc = 0;
+    for (size_t g = 0; g < ng; ++g) maxc = std::max(maxc, (int)(gstart[g + 1] - gstart[g]));
+    std::vector<int> cand;
+    std::vector<std::array<int, 2>> rp;   // ring pair of each candidate
+    for (int c = maxc; c >= 2; --c) {
+        for (size_t g = 0; g < ng; ++g) {
+            cand.clear();
+            for (size_t k = gstart[g]; k < gstart[g + 1]; ++k)
+                if (!used[inc[k].second]) cand.push_back(inc[k].second);
+            if ((int)cand.size() < c) continue;
+            const uint64_t key = inc[gstart[g]].first;
+            int pa, pb = 0;
+            if (dim == 3) {
+                pa = (int)(key >> 20);
+                pb = (int)(key & 0xfffff);
+            } else {
+                pa = (int)key;
+            }
+            rp.clear();
+            for (int e : cand) {
+                std::array<int, 2> r{-1, -1};
+                int t = 0;
+                for (int i = 0; i < nv; ++i) {
+                    int v = lc[e][i];
+                    if (v == pa || (dim == 3 && v == pb)) continue;
+                    if (t < 2) r[t++] = v;
+                }
+                rp.push_back(r);
+            }
+            std::vector<char> taken(cand.size(), 0);
+            size_t left = cand.size();
+            while (left > 0) {
+                // start from a ring vertex of degree 1 among the remaining, if any
+                int start = -1;
+                for (size_t i = 0; i < cand.size() && start < 0; ++i) {
+                    if (taken[i]) continue;
+                    for (int s2 = 0; s2 < 2 && start < 0; ++s2) {
+                        int v = rp[i][s2], deg = 0;
+                        for (size_t k = 0; k < cand.size(); ++k)
+                            if (!taken[k] && (rp[k][0] == v || rp[k][1] == v)) ++deg;
+                        if (deg == 1) start = v;
+                    }
+                }
+                if (start < 0)
+                    for (size_t i = 0; i < cand.size(); ++i)
+                        if (!taken[i]) { start = rp[i][0]; break; }
+                PatchRec P;
+                P.a = pa;
+                P.b = pb;
+                P.ring[0] = start;
+                int cur = start;
+                while (P.m < kPatchMax) {
+                    int pick = -1;
+                    for (size_t k = 0; k < cand.size(); ++k)
+                        if (!taken[k] && (rp[k][0] == cur || rp[k][1] == cur)) { pick = (int)k; break; }
+                    if (pick < 0) break;
+                    taken[pick] = 1;
+                    --left;
+                    int nxt = rp[pick][0] == cur ? rp[pick][1] : rp[pick][0];
+                    P.elem[P.m] = cand[pick];
+                    P.ring[P.m + 1] = nxt;
+                    ++P.m;
+                    cur = nxt;
+                }
+                if (P.m == 0) break;   // cannot happen: start has an element
+                for (int j = 0; j < P.m; ++j) used[P.elem[j]] = 1;
+                out.push_back(P);
+            }
+        }
+    }
+    for (int e = 0; e < n; ++e) {
+        if (used[e]) continue;
+        PatchRec P;
+        P.m = 1;
+        P.a = lc[e][0];
+        if (dim == 3) {
+            P.b = lc[e][1];
+            P.ring[0] = lc[e][2];
+            P.ring[1] = lc[e][3];
+        } else {
+            P.b = 0;
+            P.ring[0] = lc[e][1];
+            P.ring[1] = lc[e][2];
+        }
+        P.elem[0] = e;
+        out.push_back(P);
+    }
+}
+
 }  // namespace
 
 std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
@@ -137,12 +265,12 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     // ---- chunk sizes
     int ec = opt.chunk_elems;
     if (ec <= 0) {
-        // aim for ~8 chunks per SM of a 152-SM part, 128..1024 elements each
-        int64_t t = n_elems / 1216;
-        t = std::max<int64_t>(128, std::min<int64_t>(1024, t));
+        // aim for >= 4 chunks per SM of a 152-SM part, 96..3072 elements each
+        int64_t t = n_elems / 608;
+        t = std::max<int64_t>(96, std::min<int64_t>(3072, t));
         ec = (int)round_up(t, 32);
     }
-    ec = std::max(1, std::min(ec, kMaxChunkElems));
+    ec = std::max(1, std::min(ec, kMaxChunkPatches));
     int nmax = opt.chunk_nodes_max > 0 ? opt.chunk_nodes_max : std::max(ec, nv * 64);
     nmax = std::max(nmax, nv);
     nmax = std::min(nmax, 65535);
@@ -224,23 +352,16 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     for (int64_t i = 0; i < n_nodes; ++i) m.n_free += m.dirichlet_new[i] == 0;
 
     // ---- per-chunk local structure
-    int64_t elem_off = 0, node_off = 0, sh_off = 0, incp_off = 0;
-    for (int c = 0; c < nc; ++c) {
-        ChunkDesc &cd = m.chunks[c];
-        cd.n_elem = (int32_t)(chunk_begin[c + 1] - chunk_begin[c]);
-        cd.elem_off = (int32_t)elem_off;
-        elem_off += round_up(cd.n_elem, kElemPad);
-    }
-    m.elem_total = elem_off;
-    m.elem_src.assign(m.elem_total, -1);
-    m.lconn.assign(m.elem_total * 4, 0);
-    m.inc.assign(m.elem_total * 4, 0);
+    int64_t patch_off = 0, node_off = 0, sh_off = 0, incp_off = 0, inc_off = 0;
     std::vector<int32_t> loc_of_new(n_nodes, -1);
     std::vector<int32_t> shl;
-    std::vector<std::vector<int32_t>> node_slots;   // unused placeholder to keep code plain
     std::vector<int32_t> shr_cnt(m.n_shared + 1, 0);
+    std::vector<std::array<int, 4>> lc;
+    std::vector<PatchRec> patches;
     for (int c = 0; c < nc; ++c) {
         ChunkDesc &cd = m.chunks[c];
+        const int n_el = (int)(chunk_begin[c + 1] - chunk_begin[c]);
+        cd.n_elem = n_el;
         // shared local nodes, ascending new id
         shl.clear();
         for (int64_t k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) {
@@ -265,46 +386,74 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         for (int64_t j = cd.n_sh; j < round_up(cd.n_sh, kShPad); ++j) m.sh_ids.push_back(-1);
         sh_off += round_up(cd.n_sh, kShPad);
         node_off += cd.n_loc;
-        // local connectivity
-        for (int32_t e = 0; e < cd.n_elem; ++e) {
+        // local connectivity and star patches
+        lc.assign(n_el, std::array<int, 4>{0, 0, 0, 0});
+        for (int e = 0; e < n_el; ++e) {
             int32_t src = order[chunk_begin[c] + e];
-            m.elem_src[cd.elem_off + e] = src;
-            for (int a = 0; a < nv; ++a) {
-                int32_t l = loc_of_new[m.new_of_old[conn[(int64_t)src * nv + a]]];
-                m.lconn[(int64_t)(cd.elem_off + e) * 4 + a] = (uint16_t)l;
-            }
+            for (int a = 0; a < nv; ++a) lc[e][a] = loc_of_new[m.new_of_old[conn[(int64_t)src * nv + a]]];
         }
-        // incidence lists: counting sort of slots 4e+a by local node
+        build_patches(dim, n_el, lc, patches);
+        const int np = (int)patches.size();
+        if (np > kMaxChunkPatches) return "internal: too many patches in a chunk";
+        cd.patch_off = (int32_t)patch_off;
+        cd.n_patch = np;
+        const int64_t np_pad = round_up(np, kPatchPad);
+        m.pids.resize((patch_off + np_pad) * kPatchIds, 0);
+        m.elem_src.resize((patch_off + np_pad) * kPatchMax, -1);
         std::vector<int32_t> cnt(cd.n_loc + 1, 0);
-        for (int32_t e = 0; e < cd.n_elem; ++e)
-            for (int a = 0; a < nv; ++a) cnt[m.lconn[(int64_t)(cd.elem_off + e) * 4 + a] + 1]++;
+        auto each_slot = [&](const PatchRec &P, auto &&fn) {
+            fn(P.a, 0);
+            if (dim == 3) fn(P.b, 1);
+            for (int j = 0; j <= P.m; ++j) fn(P.ring[j], 2 + j);
+        };
+        for (int q = 0; q < np; ++q) {
+            const PatchRec &P = patches[q];
+            uint16_t *rec = &m.pids[(patch_off + q) * kPatchIds];
+            rec[0] = (uint16_t)P.m;
+            rec[1] = (uint16_t)P.a;
+            rec[2] = (uint16_t)(dim == 3 ? P.b : P.a);
+            for (int j = 0; j <= P.m; ++j) rec[3 + j] = (uint16_t)P.ring[j];
+            for (int j = 0; j < P.m; ++j)
+                m.elem_src[(patch_off + q) * kPatchMax + j] = order[chunk_begin[c] + P.elem[j]];
+            each_slot(P, [&](int node, int) { cnt[node + 1]++; });
+        }
         for (int32_t l = 0; l < cd.n_loc; ++l) cnt[l + 1] += cnt[l];
+        const int n_inc = cnt[cd.n_loc];
         for (int32_t l = 0; l <= cd.n_loc; ++l) m.incp.push_back((uint16_t)cnt[l]);
-        for (int64_t j = cd.n_loc + 1; j < round_up(cd.n_loc + 1, kIncpPad); ++j)
-            m.incp.push_back((uint16_t)cnt[cd.n_loc]);
+        for (int64_t j = cd.n_loc + 1; j < round_up(cd.n_loc + 1, kIncpPad); ++j) m.incp.push_back((uint16_t)n_inc);
         incp_off += round_up(cd.n_loc + 1, kIncpPad);
-        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-        for (int32_t e = 0; e < cd.n_elem; ++e)
-            for (int a = 0; a < nv; ++a) {
-                int l = m.lconn[(int64_t)(cd.elem_off + e) * 4 + a];
-                m.inc[(int64_t)cd.elem_off * 4 + fill[l]++] = (uint16_t)(4 * e + a);
-            }
+        cd.inc_off = (int32_t)inc_off;
+        cd.n_inc = n_inc;
+        m.inc.resize(inc_off + round_up(n_inc, kIncPad), 0);
+        {
+            std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+            for (int q = 0; q < np; ++q)
+                each_slot(patches[q], [&](int node, int slot) {
+                    m.inc[inc_off + fill[node]++] = (uint16_t)(q * kPatchSlots + slot);
+                });
+        }
+        inc_off += round_up(n_inc, kIncPad);
+        patch_off += np_pad;
+        m.n_patches += np;
         // node block bookkeeping (coordinates relative to the chunk origin)
-        int32_t origin_new = cd.n_loc > 0 ? (cd.n_int > 0 ? cd.int_begin : shl[0]) : 0;
+        int32_t origin_new = cd.n_int > 0 ? cd.int_begin : shl[0];
         const double *o = coords + (int64_t)m.old_of_new[origin_new] * dim;
         for (int32_t l = 0; l < cd.n_loc; ++l) {
             int32_t g = l < cd.n_int ? cd.int_begin + l : shl[l - cd.n_int];
             m.loc_node.push_back(g);
-            m.loc_chunk.push_back(c);
             const double *p = coords + (int64_t)m.old_of_new[g] * dim;
             for (int k = 0; k < dim; ++k) m.loc_rel.push_back(p[k] - o[k]);
         }
         for (int32_t l = 0; l < cd.n_int; ++l) loc_of_new[cd.int_begin + l] = -1;
         for (int32_t j = 0; j < cd.n_sh; ++j) loc_of_new[shl[j]] = -1;
-        m.max_elem = std::max(m.max_elem, cd.n_elem);
+        m.max_patch = std::max(m.max_patch, np);
+        m.max_elem = std::max(m.max_elem, n_el);
         m.max_loc = std::max(m.max_loc, cd.n_loc);
         m.max_sh = std::max(m.max_sh, cd.n_sh);
+        m.max_inc = std::max(m.max_inc, n_inc);
     }
+    m.patch_total = patch_off;
+    m.inc_total = inc_off;
     m.sh_total = sh_off;
     m.loc_total = node_off;
     m.incp_total = incp_off;
@@ -332,35 +481,58 @@ std::string validate_prep(const PrepMesh &m, const int32_t *conn) {
     std::vector<int32_t> owner(m.n_nodes, -1);
     for (int c = 0; c < m.n_chunks; ++c) {
         const ChunkDesc &cd = m.chunks[c];
-        if (cd.elem_off % kElemPad || cd.sh_off % kShPad || cd.incp_off % kIncpPad)
+        if (cd.patch_off % kPatchPad || cd.sh_off % kShPad || cd.incp_off % kIncpPad || cd.inc_off % kIncPad)
             return "segment not aligned";
-        std::vector<int> hits((size_t)cd.n_elem * 4, 0);
+        auto global_of = [&](int l) -> int32_t {
+            return l < cd.n_int ? cd.int_begin + l : m.sh_ids[cd.sh_off + l - cd.n_int];
+        };
+        std::vector<int> hits((size_t)cd.n_patch * kPatchSlots, 0);
+        std::vector<int> slot_node((size_t)cd.n_patch * kPatchSlots, -1);
+        int n_el = 0;
+        for (int q = 0; q < cd.n_patch; ++q) {
+            const uint16_t *rec = &m.pids[(int64_t)(cd.patch_off + q) * kPatchIds];
+            const int pm = rec[0];
+            if (pm < 1 || pm > kPatchMax) return "bad patch size";
+            slot_node[q * kPatchSlots + 0] = rec[1];
+            if (m.dim == 3) slot_node[q * kPatchSlots + 1] = rec[2];
+            for (int j = 0; j <= pm; ++j) slot_node[q * kPatchSlots + 2 + j] = rec[3 + j];
+            for (int j = 0; j < pm; ++j) {
+                int32_t src = m.elem_src[(int64_t)(cd.patch_off + q) * kPatchMax + j];
+                if (src < 0 || src >= m.n_elems) return "bad element source";
+                seen_elem[src]++;
+                ++n_el;
+                std::vector<int32_t> want, have;
+                for (int a = 0; a < nv; ++a) want.push_back(conn[(int64_t)src * nv + a]);
+                have.push_back(m.old_of_new[global_of(rec[1])]);
+                if (m.dim == 3) have.push_back(m.old_of_new[global_of(rec[2])]);
+                have.push_back(m.old_of_new[global_of(rec[3 + j])]);
+                have.push_back(m.old_of_new[global_of(rec[3 + j + 1])]);
+                std::sort(want.begin(), want.end());
+                std::sort(have.begin(), have.end());
+                if (want != have) return "patch element does not match the mesh";
+                for (int a = 0; a < nv; ++a) {
+                    int32_t g = m.new_of_old[want[a]];
+                    if (g < m.n_int) {
+                        if (owner[g] != -1 && owner[g] != c) return "interior node in two chunks";
+                        owner[g] = c;
+                    }
+                }
+            }
+            for (int j = pm; j < kPatchMax; ++j)
+                if (m.elem_src[(int64_t)(cd.patch_off + q) * kPatchMax + j] != -1) return "stray element slot";
+        }
+        if (n_el != cd.n_elem) return "chunk element count mismatch";
         for (int32_t l = 0; l < cd.n_loc; ++l) {
             int b = m.incp[cd.incp_off + l], e = m.incp[cd.incp_off + l + 1];
             for (int k = b; k < e; ++k) {
-                int slot = m.inc[(int64_t)cd.elem_off * 4 + k];
-                int el = slot / 4, a = slot % 4;
-                if (el >= cd.n_elem || a >= nv) return "bad slot";
-                if (m.lconn[(int64_t)(cd.elem_off + el) * 4 + a] != l) return "slot/local mismatch";
-                hits[slot]++;
+                int idx = m.inc[cd.inc_off + k];
+                if (idx >= cd.n_patch * kPatchSlots) return "bad incidence entry";
+                if (slot_node[idx] != l) return "incidence/slot mismatch";
+                hits[idx]++;
             }
         }
-        for (int32_t e = 0; e < cd.n_elem; ++e) {
-            for (int a = 0; a < nv; ++a)
-                if (hits[4 * e + a] != 1) return "slot not covered once";
-            int32_t src = m.elem_src[cd.elem_off + e];
-            if (src < 0 || src >= m.n_elems) return "bad element source";
-            seen_elem[src]++;
-            for (int a = 0; a < nv; ++a) {
-                int l = m.lconn[(int64_t)(cd.elem_off + e) * 4 + a];
-                int32_t g = l < cd.n_int ? cd.int_begin + l : m.sh_ids[cd.sh_off + l - cd.n_int];
-                if (m.old_of_new[g] != conn[(int64_t)src * nv + a]) return "connectivity mismatch";
-                if (g < m.n_int) {
-                    if (owner[g] != -1 && owner[g] != c) return "interior node in two chunks";
-                    owner[g] = c;
-                }
-            }
-        }
+        for (size_t k = 0; k < hits.size(); ++k)
+            if ((slot_node[k] >= 0) != (hits[k] == 1)) return "slot not covered exactly once";
     }
     for (int64_t e = 0; e < m.n_elems; ++e)
         if (seen_elem[e] != 1) return "element not placed exactly once";

@@ -21,22 +21,23 @@ struct PrepMesh {
     int n_chunks = 0;
     int64_t n_int = 0;        // interior nodes (new ids 0..n_int-1)
     int64_t n_shared = 0;     // shared nodes (new ids n_int..n_nodes-1)
-    int64_t elem_total = 0;   // padded element slots
+    int64_t patch_total = 0;  // padded patch records
+    int64_t n_patches = 0;    // real patches
+    int64_t inc_total = 0;    // padded incidence entries
     int64_t loc_total = 0;    // sum of n_loc
     int64_t incp_total = 0;
     int64_t sh_total = 0;     // padded shared-id slots (= partial slots)
-    int max_elem = 0, max_loc = 0, max_sh = 0;
+    int max_patch = 0, max_loc = 0, max_sh = 0, max_inc = 0, max_elem = 0;
 
     std::vector<int32_t> new_of_old, old_of_new;   // [n_nodes]
     std::vector<uint8_t> dirichlet_new;            // [n_nodes]
     std::vector<ChunkDesc> chunks;                 // [n_chunks]
-    std::vector<int32_t> elem_src;                 // [elem_total] original element id, -1 pad
-    std::vector<uint16_t> lconn;                   // [elem_total * 4]
+    std::vector<uint16_t> pids;                    // [patch_total * kPatchIds]
+    std::vector<int32_t> elem_src;                 // [patch_total * kPatchMax] original element, -1 unused
     std::vector<uint16_t> incp;                    // [incp_total]
-    std::vector<uint16_t> inc;                     // [elem_total * 4]
+    std::vector<uint16_t> inc;                     // [inc_total] patch * kPatchSlots + slot
     std::vector<int32_t> sh_ids;                   // [sh_total], -1 pad
     std::vector<int32_t> loc_node;                 // [loc_total] new id of each local node
-    std::vector<int32_t> loc_chunk;                // [loc_total] chunk of each local node
     std::vector<double> loc_rel;                   // [loc_total * dim] coords - chunk origin
     std::vector<int32_t> shr_ptr;                  // [n_shared + 1]
     std::vector<int32_t> shr_slot;                 // partial slots of each shared node
@@ -48,8 +49,10 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
                          PrepMesh &out);
 
 // Checks the invariants the kernels rely on (used by the tests through the ABI
-// debug hook): every element slot appears once in its chunk's incidence lists,
-// interior nodes are touched by one chunk only, partial slots are a bijection.
+// debug hook): every element sits in exactly one patch slot with the patch's
+// vertex pattern, every used contribution slot appears once in the incidence
+// list of its node, interior nodes are touched by one chunk only, partial
+// slots are a bijection.
 std::string validate_prep(const PrepMesh &m, const int32_t *conn_original);
 
 }  // namespace ps

@@ -23,14 +23,14 @@ namespace ps {
 enum Mode : int { kApply = 0, kCG = 1, kResid = 2, kDiag = 3 };
 
 struct SmemLayout {
-    uint32_t node, val, lconn, bdt2, incp, inc, shid, contrib, red, bar, total;
+    uint32_t node, val, pids, incp, inc, shid, contrib, red, bar, total;
 };
 
 struct MeshDev {
     int dim, n_chunks;
     int64_t n_nodes, n_int, n_shared, n_pad;
     const ChunkDesc *chunks;
-    const ushort4 *lconn;
+    const uint16_t *pids;    // [patch_total * kPatchIds]
     const uint16_t *incp, *inc;
     const int32_t *sh_ids, *shr_ptr, *shr_slot;
     const NodeF *node32;
@@ -82,42 +82,52 @@ __device__ __forceinline__ int ld_flag(const int *p) { return *(volatile const i
 // (CG: p.q, resid: r.r over interior nodes).  `phase` is the mbarrier parity
 // to wait for; it flips on return.  Block-uniform; contains __syncthreads.
 template <int D, typename T, int MODE>
-__device__ double process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, unsigned char *smem,
-                                const SmemLayout &L, uint32_t &phase, T beta_cg, bool &failed) {
+__device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, unsigned char *smem,
+                                                 const SmemLayout &L, uint32_t &phase, T beta_cg, bool &failed) {
+    using Acc = typename DotOf<T>::type;
     using N4 = typename NodeOf<T>::type;
-    constexpr int NV = D + 1;
     const ChunkDesc cd = m.chunks[c];
     N4 *s_node = reinterpret_cast<N4 *>(smem + L.node);
     T *s_val = reinterpret_cast<T *>(smem + L.val);
-    ushort4 *s_lconn = reinterpret_cast<ushort4 *>(smem + L.lconn);
-    T *s_bdt2 = reinterpret_cast<T *>(smem + L.bdt2);
+    uint16_t *s_pids = reinterpret_cast<uint16_t *>(smem + L.pids);
     uint16_t *s_incp = reinterpret_cast<uint16_t *>(smem + L.incp);
     uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
     int32_t *s_shid = reinterpret_cast<int32_t *>(smem + L.shid);
     T *s_contrib = reinterpret_cast<T *>(smem + L.contrib);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
 
-    const int n_loc = cd.n_loc, n_int = cd.n_int, n_sh = cd.n_sh, n_elem = cd.n_elem;
-    const int e_pad = (n_elem + kElemPad - 1) / kElemPad * kElemPad;
+    const int n_loc = cd.n_loc, n_int = cd.n_int, n_sh = cd.n_sh, n_patch = cd.n_patch;
+    const int p_pad = (n_patch + kPatchPad - 1) / kPatchPad * kPatchPad;
     const int incp_n = (n_loc + 1 + kIncpPad - 1) / kIncpPad * kIncpPad;
+    const int inc_n = (cd.n_inc + kIncPad - 1) / kIncPad * kIncPad;
     const int sh_n = (n_sh + kShPad - 1) / kShPad * kShPad;
     const N4 *gnode = (sizeof(T) == 4) ? reinterpret_cast<const N4 *>(m.node32) : reinterpret_cast<const N4 *>(m.node64);
     const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
 
     if (threadIdx.x == 0) {
         const uint32_t b_node = (uint32_t)n_loc * sizeof(N4);
-        const uint32_t b_lconn = (uint32_t)e_pad * 8u;
-        const uint32_t b_bdt2 = (uint32_t)e_pad * sizeof(T);
+        const uint32_t b_pids = (uint32_t)p_pad * (kPatchIds * 2u);
         const uint32_t b_incp = (uint32_t)incp_n * 2u;
-        const uint32_t b_inc = (uint32_t)e_pad * 8u;
+        const uint32_t b_inc = (uint32_t)inc_n * 2u;
         const uint32_t b_sh = (uint32_t)sh_n * 4u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_lconn + b_bdt2 + b_incp + b_inc + b_sh);
+        mbar_arrive_expect_tx(s_bar, b_node + b_pids + b_incp + b_inc + b_sh);
         bulk_g2s(s_node, gnode + cd.node_off, b_node, s_bar);
-        bulk_g2s(s_lconn, m.lconn + cd.elem_off, b_lconn, s_bar);
-        bulk_g2s(s_bdt2, gbdt2 + cd.elem_off, b_bdt2, s_bar);
+        bulk_g2s(s_pids, m.pids + (size_t)cd.patch_off * kPatchIds, b_pids, s_bar);
         bulk_g2s(s_incp, m.incp + cd.incp_off, b_incp, s_bar);
-        bulk_g2s(s_inc, m.inc + (size_t)cd.elem_off * 4, b_inc, s_bar);
+        bulk_g2s(s_inc, m.inc + cd.inc_off, b_inc, s_bar);
         if (b_sh) bulk_g2s(s_shid, m.sh_ids + cd.sh_off, b_sh, s_bar);
+    }
+    // interior input values do not depend on the staged data: fetch them
+    // while the bulk copies are in flight (masked below, once records landed)
+    T vin[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int l = threadIdx.x + k * blockDim.x;
+        vin[k] = T(0);
+        if (MODE != kDiag && l < n_int) {
+            const int g = cd.int_begin + l;
+            vin[k] = (MODE == kCG) ? cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]) : a.x[g];
+        }
     }
     bool ok = mbar_wait_bounded(s_bar, phase);
     ok = __syncthreads_and(ok);
@@ -126,55 +136,39 @@ __device__ double process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, un
         mbar_wait_bounded(s_bar, phase);   // let copies in flight land before leaving
         phase ^= 1u;
         failed = true;
-        return 0.0;
+        return Acc();
     }
     phase ^= 1u;
 
     // ---- gather the input vector (masked on Dirichlet nodes)
     if (MODE != kDiag) {
-        for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-            const int g = l < n_int ? cd.int_begin + l : s_shid[l - n_int];
-            T v;
-            if (MODE == kCG) {
-                v = cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]);
-                if (is_dirichlet(s_node[l].w)) v = T(0);
-                if (l < n_int) a.p[g] = v;
-            } else {
-                v = is_dirichlet(s_node[l].w) ? T(0) : a.x[g];
-            }
+        auto finish = [&](int l, T v) {
+            if (is_dirichlet(s_node[l].w)) v = T(0);
+            if (MODE == kCG && l < n_int) a.p[cd.int_begin + l] = v;
             s_val[l] = v;
+        };
+        auto fetch = [&](int l) -> T {
+            const int g = l < n_int ? cd.int_begin + l : s_shid[l - n_int];
+            return (MODE == kCG) ? cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]) : a.x[g];
+        };
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = threadIdx.x + k * blockDim.x;
+            if (l < n_loc) finish(l, l < n_int ? vin[k] : fetch(l));
         }
+        for (int l = threadIdx.x + 4 * blockDim.x; l < n_loc; l += blockDim.x) finish(l, fetch(l));
         __syncthreads();
     }
 
-    // ---- element contributions
-    for (int e = threadIdx.x; e < n_elem; e += blockDim.x) {
-        const ushort4 lc = s_lconn[e];
-        const T bd = s_bdt2[e];
-        T o0, o1, o2, o3 = T(0);
-        if (D == 3) {
-            if (MODE == kDiag)
-                elem_diag_3d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_node[lc.w], bd, o0, o1, o2, o3);
-            else
-                elem_apply_3d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_node[lc.w], s_val[lc.x], s_val[lc.y],
-                                 s_val[lc.z], s_val[lc.w], bd, o0, o1, o2, o3);
-        } else {
-            if (MODE == kDiag)
-                elem_diag_2d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], bd, o0, o1, o2);
-            else
-                elem_apply_2d<T>(s_node[lc.x], s_node[lc.y], s_node[lc.z], s_val[lc.x], s_val[lc.y], s_val[lc.z], bd,
-                                 o0, o1, o2);
-        }
-        T *dst = s_contrib + 4 * e;
-        dst[0] = o0;
-        dst[1] = o1;
-        dst[2] = o2;
-        if (NV == 4) dst[3] = o3;
-    }
+    // ---- patch contributions (one thread per star patch)
+    const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
+    for (int q = threadIdx.x; q < n_patch; q += blockDim.x)
+        patch_eval<D, T, N4, MODE == kDiag>(s_node, s_val, s_pids + q * kPatchIds, g_bdt2 + q * kPatchMax,
+                                            s_contrib + q * kPatchSlots);
     __syncthreads();
 
     // ---- per-node sums in incidence order
-    double dot = 0.0;
+    Acc dot;
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
         const int b = s_incp[l], e = s_incp[l + 1];
         T s = T(0);
@@ -187,11 +181,11 @@ __device__ double process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, un
                 a.y[g] = s;
             } else if (MODE == kCG) {
                 a.y[g] = s;
-                dot += (double)s_val[l] * (double)s;
+                dot.add_prod(s_val[l], s);
             } else if (MODE == kResid) {
                 const T rv = dir ? T(0) : a.b[g] - s;
                 a.y[g] = rv;
-                dot += (double)rv * (double)rv;
+                dot.add_prod(rv, rv);
             } else {  // diag: T == double here
                 const double dv = dir ? 0.0 : 1.0 / (double)s;
                 const_cast<double *>(m.dinv64)[g] = dv;
@@ -207,22 +201,29 @@ __device__ double process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, un
 // Kernel 1: one block per chunk.
 template <int D, typename T, int MODE>
 __global__ void __launch_bounds__(256) k_chunks(MeshDev m, VecArgs<T> a) {
-    if (MODE == kCG && ld_flag(&a.st->done)) return;
     extern __shared__ __align__(128) unsigned char smem[];
     const SmemLayout &L = (sizeof(T) == 4) ? m.sm32 : m.sm64;
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
     double *s_red = reinterpret_cast<double *>(smem + L.red);
+    // CG scalars are read once per block (not per thread: a same-address
+    // hot spot) and broadcast through shared memory.
     if (threadIdx.x == 0) {
+        if (MODE == kCG) {
+            s_red[0] = a.st->beta;
+            s_red[1] = (double)a.st->done;
+        }
         mbar_init(s_bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (MODE == kCG && s_red[1] != 0.0) return;
+    const T beta_cg = (MODE == kCG) ? (T)s_red[0] : T(0);
+    __syncthreads();
     uint32_t phase = 0;
     bool failed = false;
-    const T beta_cg = (MODE == kCG) ? (T)a.st->beta : T(0);
-    double dot = process_chunk<D, T, MODE>(m, a, blockIdx.x, smem, L, phase, beta_cg, failed);
+    const typename DotOf<T>::type acc = process_chunk<D, T, MODE>(m, a, blockIdx.x, smem, L, phase, beta_cg, failed);
     if (MODE == kCG || MODE == kResid) {
-        dot = block_sum(dot, s_red);
+        const double dot = block_sum(acc, s_red);
         if (threadIdx.x == 0) a.dotbuf[blockIdx.x] = dot;
     }
 }
@@ -232,11 +233,18 @@ __global__ void __launch_bounds__(256) k_chunks(MeshDev m, VecArgs<T> a) {
 // kernel's blocks) and updates the CG scalars.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_first) {
-    if (MODE == kCG && ld_flag(&a.st->done)) return;
-    __shared__ double s_red[32];
+    __shared__ double s_red[34];
     __shared__ bool s_last;
-    const T beta_cg = (MODE == kCG) ? (T)a.st->beta : T(0);
-    double dot = 0.0;
+    if (MODE == kCG) {
+        if (threadIdx.x == 0) {
+            s_red[0] = a.st->beta;
+            s_red[1] = (double)a.st->done;
+        }
+        __syncthreads();
+        if (s_red[1] != 0.0) return;
+    }
+    const T beta_cg = (MODE == kCG) ? (T)s_red[0] : T(0);
+    typename DotOf<T>::type acc;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m.n_shared;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = m.n_int + s;
@@ -251,11 +259,11 @@ __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_f
             if (dir) v = T(0);
             a.p[g] = v;
             a.y[g] = sum;
-            dot += (double)v * (double)sum;
+            acc.add_prod(v, sum);
         } else if (MODE == kResid) {
             const T rv = dir ? T(0) : a.b[g] - sum;
             a.y[g] = rv;
-            dot += (double)rv * (double)rv;
+            acc.add_prod(rv, rv);
         } else {
             const double dv = dir ? 0.0 : 1.0 / (double)sum;
             const_cast<double *>(m.dinv64)[g] = dv;
@@ -263,16 +271,14 @@ __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_f
         }
     }
     if (MODE != kCG && MODE != kResid) return;
-    dot = block_sum(dot, s_red);
+    const double dot = block_sum(acc, s_red);
     if (threadIdx.x == 0) {
         a.dotbuf[n_first + blockIdx.x] = dot;
-        __threadfence();
-        const unsigned int t = atomicAdd(&a.st->cnt_a, 1u);
+        const unsigned int t = atomic_add_acq_rel(&a.st->cnt_a, 1u);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const double tot = block_sum_array(a.dotbuf, n_first + gridDim.x, s_red);
     if (threadIdx.x == 0) {
         CgState *st = a.st;
@@ -300,32 +306,35 @@ __global__ void __launch_bounds__(256) k_cg_update(int64_t n_pad, T *__restrict_
                                                    const T *__restrict__ p, const T *__restrict__ q,
                                                    const T *__restrict__ dinv, CgState *st, double *dotbuf,
                                                    int *host_done) {
-    if (ld_flag(&st->done)) return;
-    __shared__ double s_red[32];
+    __shared__ double s_red[34];
     __shared__ bool s_last;
-    const T al = (T)st->alpha;
-    double rz = 0.0, rr = 0.0;
+    if (threadIdx.x == 0) {
+        s_red[0] = st->alpha;
+        s_red[1] = (double)st->done;
+    }
+    __syncthreads();
+    if (s_red[1] != 0.0) return;
+    const T al = (T)s_red[0];
+    typename DotOf<T>::type arz, arr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
         const T xi = x[i] + al * p[i];
         const T ri = r[i] - al * q[i];
         x[i] = xi;
         r[i] = ri;
         const T zi = dinv[i] * ri;
-        rz += (double)ri * (double)zi;
-        rr += (double)ri * (double)ri;
+        arz.add_prod(ri, zi);
+        arr.add_prod(ri, ri);
     }
-    rz = block_sum(rz, s_red);
-    rr = block_sum(rr, s_red);
+    const double rz = block_sum(arz, s_red);
+    const double rr = block_sum(arr, s_red);
     if (threadIdx.x == 0) {
         dotbuf[blockIdx.x] = rz;
         dotbuf[gridDim.x + blockIdx.x] = rr;
-        __threadfence();
-        const unsigned int t = atomicAdd(&st->cnt_b, 1u);
+        const unsigned int t = atomic_add_acq_rel(&st->cnt_b, 1u);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const double rz_new = block_sum_array(dotbuf, gridDim.x, s_red);
     const double rr_new = block_sum_array(dotbuf + gridDim.x, gridDim.x, s_red);
     if (threadIdx.x == 0) {
@@ -361,29 +370,27 @@ __global__ void __launch_bounds__(256) k_cg_start(int64_t n_pad, const double *_
                                                   T *__restrict__ r, T *__restrict__ d, T *__restrict__ p,
                                                   const T *__restrict__ dinv, CgState *st, double *dotbuf,
                                                   double tol2, int relative, long long max_iters) {
-    __shared__ double s_red[32];
+    __shared__ double s_red[34];
     __shared__ bool s_last;
-    double rz = 0.0, rr = 0.0;
+    typename DotOf<T>::type arz, arr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
         T ri = rsrc ? (T)(rsrc[i] * scale) : r[i];
         if (rsrc) r[i] = ri;
         if (d) d[i] = T(0);
         p[i] = T(0);
-        rz += (double)ri * (double)(dinv[i] * ri);
-        rr += (double)ri * (double)ri;
+        arz.add_prod(ri, dinv[i] * ri);
+        arr.add_prod(ri, ri);
     }
-    rz = block_sum(rz, s_red);
-    rr = block_sum(rr, s_red);
+    const double rz = block_sum(arz, s_red);
+    const double rr = block_sum(arr, s_red);
     if (threadIdx.x == 0) {
         dotbuf[blockIdx.x] = rz;
         dotbuf[gridDim.x + blockIdx.x] = rr;
-        __threadfence();
-        const unsigned int t = atomicAdd(&st->cnt_b, 1u);
+        const unsigned int t = atomic_add_acq_rel(&st->cnt_b, 1u);
         s_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const double rz0 = block_sum_array(dotbuf, gridDim.x, s_red);
     const double rr0 = block_sum_array(dotbuf + gridDim.x, gridDim.x, s_red);
     if (threadIdx.x == 0) {

@@ -35,7 +35,7 @@ static int sm_count_of(int dev) {
 
 int grid_for(int64_t n, int dev_sms) {
     int64_t g = (n + kBlock - 1) / kBlock;
-    int64_t cap = (int64_t)dev_sms * 8;
+    int64_t cap = (int64_t)dev_sms * 4;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
@@ -68,19 +68,18 @@ void dfree_all(ps_ctx *ctx, std::vector<DevAlloc> &owner) {
 
 static uint32_t align128(uint64_t v) { return (uint32_t)((v + 127) / 128 * 128); }
 
-SmemLayout make_layout(int esz, int nsz, int max_loc, int max_elem, int max_sh) {
+SmemLayout make_layout(int esz, int nsz, int max_loc, int max_patch, int max_inc, int max_sh) {
     SmemLayout L;
-    const uint64_t epad = (uint64_t)round_up(max_elem, kElemPad);
+    const uint64_t ppad = (uint64_t)round_up(max_patch, kPatchPad);
     uint64_t off = 0;
     L.node = (uint32_t)off;    off += align128((uint64_t)max_loc * nsz);
     L.val = (uint32_t)off;     off += align128((uint64_t)max_loc * esz);
-    L.lconn = (uint32_t)off;   off += align128(epad * 8);
-    L.bdt2 = (uint32_t)off;    off += align128(epad * esz);
+    L.pids = (uint32_t)off;    off += align128(ppad * kPatchIds * 2);
     L.incp = (uint32_t)off;    off += align128((uint64_t)round_up(max_loc + 1, kIncpPad) * 2);
-    L.inc = (uint32_t)off;     off += align128(epad * 8);
+    L.inc = (uint32_t)off;     off += align128((uint64_t)round_up(max_inc > 0 ? max_inc : 1, kIncPad) * 2);
     L.shid = (uint32_t)off;    off += align128((uint64_t)round_up(max_sh > 0 ? max_sh : 1, kShPad) * 4);
-    L.contrib = (uint32_t)off; off += align128(epad * 4 * esz);
-    L.red = (uint32_t)off;     off += 32 * 8;
+    L.contrib = (uint32_t)off; off += align128(ppad * kPatchSlots * esz);
+    L.red = (uint32_t)off;     off += 34 * 8;
     L.bar = (uint32_t)off;     off += 16;
     L.total = (uint32_t)off;
     return L;
@@ -230,10 +229,9 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     ChunkDesc *ch;
     RC(upload(c, m, &ch, pm.chunks.data(), pm.chunks.size() * sizeof(ChunkDesc)));
     d.chunks = ch;
-    ushort4 *lc;
-    RC(upload(c, m, &lc, pm.lconn.data(), pm.lconn.size() * 2));
-    d.lconn = lc;
     uint16_t *u;
+    RC(upload(c, m, &u, pm.pids.data(), pm.pids.size() * 2));
+    d.pids = u;
     RC(upload(c, m, &u, pm.incp.data(), pm.incp.size() * 2));
     d.incp = u;
     RC(upload(c, m, &u, pm.inc.data(), pm.inc.size() * 2));
@@ -279,9 +277,9 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     }
     float *f;
     double *g;
-    RC(upload(c, m, &f, nullptr, pm.elem_total * 4));
+    RC(upload(c, m, &f, nullptr, pm.patch_total * kPatchMax * 4));
     d.bdt2_32 = f;
-    RC(upload(c, m, &g, nullptr, pm.elem_total * 8));
+    RC(upload(c, m, &g, nullptr, pm.patch_total * kPatchMax * 8));
     d.bdt2_64 = g;
     RC(upload(c, m, &f, nullptr, d.n_pad * 4));
     CK(cudaMemset(f, 0, d.n_pad * 4));
@@ -290,8 +288,8 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     CK(cudaMemset(g, 0, d.n_pad * 8));
     d.dinv64 = g;
     d.err = c->d_err;
-    d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_elem, pm.max_sh);
-    d.sm64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_elem, pm.max_sh);
+    d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
+    d.sm64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
     if (d.sm64.total > 227 * 1024) {
         ps_set_last_error("chunk too large for shared memory; lower chunk_elems");
         return PS_EINVAL;
@@ -393,7 +391,8 @@ static int coeff_upload(ps_mesh *m, const double *alpha, const double *beta, dou
     if (rc != PS_OK) return rc;
     cudaError_t e = cudaMemcpy(dbeta, beta, p.n_elems * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_set_beta<<<grid_for(p.elem_total, c->sms), kBlock>>>(p.elem_total, m->d_elem_src, (const double *)dbeta, dt2,
+        const int64_t nslots = p.patch_total * kPatchMax;
+        k_set_beta<<<grid_for(nslots, c->sms), kBlock>>>(nslots, m->d_elem_src, (const double *)dbeta, dt2,
                                                                  const_cast<float *>(d.bdt2_32),
                                                                  const_cast<double *>(d.bdt2_64));
         e = cudaGetLastError();
@@ -867,7 +866,9 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
         stats->chunk_node_refs = pm.loc_total;
         stats->max_chunk_elems = pm.max_elem;
         stats->max_chunk_nodes = pm.max_loc;
-        SmemLayout l64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_elem, pm.max_sh);
+        SmemLayout l64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
+        stats->reserved[0] = pm.n_patches;
+        stats->reserved[1] = pm.inc_total;
         stats->device_bytes = l64.total;  // shared memory per block of the FP64 pass
     }
     return PS_OK;
