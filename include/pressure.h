@@ -184,6 +184,22 @@ int ps_coeff_set_beta(ps_mesh *mesh, const double *beta_elem);
  * inputs give bitwise the same outputs).  Errors: PS_EINVAL, PS_ESTATE. */
 int ps_pressure_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, int precision, void *stream);
 
+/* ---- operator apply without device allocation ---------------------------
+ * Same arguments, result and errors as ps_pressure_apply, for callers that
+ * cannot allocate device memory at the point of the call (their framework's
+ * allocator already holds the memory they may use, or an allocation would
+ * synchronise the device inside a time-critical loop).  The paper has no
+ * counterpart: this is a deployment variant of the same operator.
+ * Scratch (permuted copies of x and y, shared-node partial sums) lives in one
+ * file-scope device array of 16 MiB that every GPU loading the library holds
+ * until exit; meshes needing more (about 2 x n_nodes x 4 or 8 bytes plus the
+ * partial sums) are rejected with PS_EINVAL and a ps_last_error message.  The
+ * first call on a device looks up the array's device address (that device
+ * current); make that first call before any stream capture.  Calls share the
+ * array: calls whose work overlaps on the GPU race.  Calls no cudaMalloc or
+ * cudaFree.  The mesh itself must have been uploaded and its coefficients set. */
+int ps_pressure_apply_noalloc(ps_mesh *mesh, const void *x_dev, void *y_dev, int precision, void *stream);
+
 /* ---- solve A x = b (Section 3.4: SPD system, matrix-free CG, warm start) --
  *   b_dev  device [n_nodes] double, caller numbering (Dirichlet entries ignored)
  *   x_dev  device [n_nodes] double; in: first guess (e.g. the pressure of the

@@ -103,6 +103,7 @@ SIGNATURES = {
     "ps_coeff_set": (C.c_int, [_vp, _vp, _vp, C.c_double]),
     "ps_coeff_set_beta": (C.c_int, [_vp, _vp]),
     "ps_pressure_apply": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
+    "ps_pressure_apply_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ps_pressure_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(ps_solve_opts), C.POINTER(ps_solve_info), _vp]),
     "ps_solve_opts_default": (None, [C.POINTER(ps_solve_opts)]),
     "ps_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
@@ -228,6 +229,12 @@ def ps_coeff_set_beta(mesh, beta):
 def ps_pressure_apply(mesh, x_dev, y_dev, precision, stream=None):
     return _check(_lib.ps_pressure_apply(mesh, _dev(x_dev), _dev(y_dev), int(precision), _stream(stream)),
                   "ps_pressure_apply")
+
+
+def ps_pressure_apply_noalloc(mesh, x_dev, y_dev, precision, stream=None):
+    """Apply without any device allocation (scratch in a fixed 16 MiB device array)."""
+    return _check(_lib.ps_pressure_apply_noalloc(mesh, _dev(x_dev), _dev(y_dev), int(precision), _stream(stream)),
+                  "ps_pressure_apply_noalloc")
 
 
 def ps_solve_opts_default():
