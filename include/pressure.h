@@ -93,8 +93,15 @@ typedef struct {
     int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
     int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
                              /* negative = launch kernels directly, no graph)      */
-    int32_t reserved[6];
+    int32_t engine;          /* PS_ENGINE_AUTO: mixed mode runs the persistent      */
+                             /* one-reduction PCG, FP64 mode the multi-kernel PCG;  */
+                             /* PS_ENGINE_GRAPH forces the multi-kernel (graph) PCG */
+    int32_t reserved[5];
 } ps_solve_opts;
+
+#define PS_ENGINE_AUTO        0
+#define PS_ENGINE_GRAPH       1
+#define PS_ENGINE_PERSISTENT  2
 
 typedef struct {
     int32_t status;          /* PS_OK, PS_ENOTCONV, PS_EBREAKDOWN, ...             */

@@ -1,12 +1,838 @@
-// Batched persistent solver (placeholder until the persistent kernel lands).
+// Batched / persistent solver engine: see batched.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
 #include "../../include/pressure.h"
-#include "internal.h"
+#include "batched.h"
+
 namespace ps {
-int batched_set_attrs() { return 0; }
-void batched_release_mesh(ps_mesh *) {}
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_i32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// bar[0] = arrival count, bar[32] = generation (separate 128-byte lines).
+// The wait is bounded: on timeout the error flag is set and false returned;
+// the caller then leaves the kernel (other blocks time out in turn).
+__device__ bool grid_barrier(unsigned int *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int *count = bar, *gen = bar + 32;
+        const unsigned int g = ld_acquire_u32(gen);
+        const unsigned int arrived = atomic_add_acq_rel(count, 1u);
+        int ok = 0;
+        if (arrived == gridDim.x - 1) {
+            *(volatile unsigned int *)count = 0u;
+            st_release_u32(gen, g + 1u);
+            ok = 1;
+        } else {
+            for (uint32_t i = 0; i < kGridSpinLimit; ++i) {
+                if (ld_acquire_u32(gen) != g) {
+                    ok = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (!ok) atomicOr(err, kErrGridTimeout);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Block sum of three double-float accumulators; result in red[32..34].
+__device__ __forceinline__ void block_sum3(const DotF &a, const DotF &b, const DotF &c, double *red, double out[3]) {
+    out[0] = block_sum(a, red);
+    out[1] = block_sum(b, red);
+    out[2] = block_sum(c, red);
+}
+
+// One-reduction PCG update of one node from its old values (shared by the
+// chunk pass, for every local node, and the shared-node pass):
+//   s' = w + beta s, r' = r - alpha s', u' = D^-1 r', p' = D^-1 r + beta p,
+//   x' = x + alpha p'.  Explicit roundings: the same inputs give bitwise the
+// same outputs wherever this is evaluated.
+struct NodeUpd {
+    float s, r, u, p, x;
+};
+__device__ __forceinline__ NodeUpd node_update(float r, float w, float s, float di, float p, float x, float alpha,
+                                               float beta) {
+    NodeUpd o;
+    o.s = __fmaf_rn(beta, s, w);
+    o.r = __fmaf_rn(-alpha, o.s, r);
+    o.u = __fmul_rn(di, o.r);
+    o.p = __fmaf_rn(beta, p, __fmul_rn(di, r));
+    o.x = __fmaf_rn(alpha, o.p, x);
+    return o;
+}
+
+// Phase 1 for one chunk of mesh M: node updates (written for interior nodes),
+// w' = A u' (interior rows written, shared rows as partial sums), and the
+// chunk's shares of gamma = r'.u', delta = w'.u', rho = r'.r'.
+__device__ void chunk_cg1(const BMesh &M, int c, const ChunkSmem<float> &S, uint32_t &phase, float alpha, float beta,
+                          DotF acc[3], bool &failed) {
+    const MeshDev &m = M.d;
+    const ChunkDesc cd = m.chunks[c];
+    const int n_loc = cd.n_loc, n_int = cd.n_int;
+    stage_issue<float>(m, cd, S);
+    if (!stage_wait<float>(m, S, phase)) {
+        failed = true;
+        return;
+    }
+    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+        const bool interior = l < n_int;
+        const int g = interior ? cd.int_begin + l : S.shid[l - n_int];
+        // vectors written earlier in this launch by other blocks: read at L2 (.cg)
+        const float di = m.dinv32[g];
+        const float r = __ldcg(M.r + g), w = __ldcg(M.w + g), s = __ldcg(M.s + g);
+        const float p = interior ? __ldcg(M.p + g) : 0.f, x = interior ? __ldcg(M.x + g) : 0.f;
+        NodeUpd o = node_update(r, w, s, di, p, x, alpha, beta);
+        if (is_dirichlet(S.node[l].w)) {
+            o.u = 0.f;
+            o.r = 0.f;
+        }
+        S.val[l] = o.u;
+        S.aux[l] = o.r;
+        if (interior) {
+            M.s[g] = o.s;
+            M.r[g] = o.r;
+            M.p[g] = o.p;
+            M.x[g] = o.x;
+        }
+    }
+    __syncthreads();
+    if (m.dim == 3)
+        patches_eval<3, float, false>(m, cd, S);
+    else
+        patches_eval<2, float, false>(m, cd, S);
+    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+        float wv = node_sum(S, l);
+        if (is_dirichlet(S.node[l].w)) wv = 0.f;
+        if (l < n_int) {
+            M.w[cd.int_begin + l] = wv;
+            const float u = S.val[l], r = S.aux[l];
+            acc[0].add_prod(r, u);
+            acc[1].add_prod(wv, u);
+            acc[2].add_prod(r, r);
+        } else {
+            M.part[cd.sh_off + (l - n_int)] = wv;
+        }
+    }
+}
+
+// Reduce mesh M's per-task dot triplets (fixed order) and advance its
+// scalars.  Called by the last block to finish the mesh's phase-2 tasks.
+__device__ void mesh_scalars(const BMesh &M, double *red, int *active_cnt) {
+    const int n = M.d.n_chunks + M.n_segs;
+    double g = 0.0, d = 0.0, rho = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        g += __ldcg(M.dots + 3 * k);
+        d += __ldcg(M.dots + 3 * k + 1);
+        rho += __ldcg(M.dots + 3 * k + 2);
+    }
+    g = block_sum(g, red);
+    d = block_sum(d, red);
+    rho = block_sum(rho, red);
+    if (threadIdx.x != 0) return;
+    BState *st = M.st;
+    st->cnt2 = 0;
+    int done = 0, status = 0;
+    if (st->first) {
+        st->first = 0;
+        st->rho0 = rho;
+        st->stop2 = st->inner_tol2 * rho;
+        if (!(rho > 0.0)) {
+            done = 1;
+            status = kCgConverged;
+        } else if (!(d > 0.0) || !isfinite(g) || !isfinite(d)) {
+            done = 1;
+            status = kCgBreakdown;
+        } else {
+            st->alpha = g / d;
+            st->beta = 0.0;
+        }
+    } else {
+        st->iters += 1;
+        st->iters_total += 1;
+        const double beta = g / st->gamma;
+        const double den = d - beta * g / st->alpha;
+        if (!isfinite(rho) || !isfinite(g) || !isfinite(d) || !(den > 0.0)) {
+            done = 1;
+            status = kCgBreakdown;
+        } else if (rho <= st->stop2) {
+            done = 1;
+            status = kCgConverged;
+        } else if (st->iters_total >= st->max_iters) {
+            done = 1;
+            status = kCgMaxIter;
+        } else {
+            st->beta = beta;
+            st->alpha = g / den;
+        }
+    }
+    st->gamma = g;
+    st->delta = d;
+    st->rho = rho;
+    if (done) {
+        st->status = status;
+        st->done = 1;
+        atomicSub(active_cnt, 1);
+    }
+}
+
+// Phase 2 for one segment of shared nodes of mesh M; the last block of the
+// mesh also advances its scalars.
+__device__ void seg_cg1(const BMesh &M, int seg, float alpha, float beta, double *red, int *active_cnt) {
+    const MeshDev &m = M.d;
+    const int64_t s0 = (int64_t)seg * kSegLen;
+    const int64_t s1 = s0 + kSegLen < m.n_shared ? s0 + kSegLen : m.n_shared;
+    DotF a0, a1, a2;
+    for (int64_t sidx = s0 + threadIdx.x; sidx < s1; sidx += blockDim.x) {
+        const int64_t g = m.n_int + sidx;
+        float wv = 0.f;
+        const int kb = m.shr_ptr[sidx], ke = m.shr_ptr[sidx + 1];
+        for (int k = kb; k < ke; ++k) wv += __ldcg(M.part + m.shr_slot[k]);
+        NodeUpd o = node_update(__ldcg(M.r + g), __ldcg(M.w + g), __ldcg(M.s + g), m.dinv32[g], __ldcg(M.p + g),
+                                __ldcg(M.x + g), alpha, beta);
+        if (m.dirichlet[g]) {
+            o.u = 0.f;
+            o.r = 0.f;
+            wv = 0.f;
+        }
+        M.s[g] = o.s;
+        M.r[g] = o.r;
+        M.p[g] = o.p;
+        M.x[g] = o.x;
+        M.w[g] = wv;
+        a0.add_prod(o.r, o.u);
+        a1.add_prod(wv, o.u);
+        a2.add_prod(o.r, o.r);
+    }
+    double out[3];
+    block_sum3(a0, a1, a2, red, out);
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        const int k = m.n_chunks + seg;
+        M.dots[3 * k] = out[0];
+        M.dots[3 * k + 1] = out[1];
+        M.dots[3 * k + 2] = out[2];
+        const unsigned int t = atomic_add_acq_rel(&M.st->cnt2, 1u);
+        s_last = (t == (unsigned)M.n_segs - 1u);
+    }
+    __syncthreads();
+    if (s_last) mesh_scalars(M, red, active_cnt);
+    __syncthreads();
+}
+
+struct PcgArgs {
+    const BMesh *meshes;
+    const int2 *t1, *t2;
+    int n_t1, n_t2;
+    unsigned int *bar;
+    int *active_cnt;
+    int *err;
+    int max_it;
+    SmemLayout L;
+};
+
+// Reads (done, active, alpha, beta) of a mesh once per block.
+__device__ __forceinline__ bool task_scalars(const BMesh &M, double *sc, float &alpha, float &beta) {
+    if (threadIdx.x == 0) {
+        const BState *st = M.st;
+        sc[0] = (__ldcg(&st->active) && !__ldcg(&st->done)) ? 1.0 : 0.0;
+        sc[1] = __ldcg(&st->alpha);
+        sc[2] = __ldcg(&st->beta);
+    }
+    __syncthreads();
+    const bool run = sc[0] != 0.0;
+    alpha = (float)sc[1];
+    beta = (float)sc[2];
+    __syncthreads();
+    return run;
+}
+
+// The persistent inner solver: up to max_it iterations of every active mesh.
+__global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const ChunkSmem<float> S = chunk_smem<float>(smem, A.L);
+    __shared__ double sc[4];
+    __shared__ int s_act;
+    if (threadIdx.x == 0) {
+        mbar_init(S.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int it = 0; it < A.max_it; ++it) {
+        if (threadIdx.x == 0) s_act = ld_acquire_i32(A.active_cnt);
+        __syncthreads();
+        if (s_act <= 0) break;
+        // ---- phase 1: chunks
+        for (int t = blockIdx.x; t < A.n_t1; t += gridDim.x) {
+            const int2 tk = A.t1[t];
+            const BMesh &M = A.meshes[tk.x];
+            float alpha, beta;
+            if (!task_scalars(M, sc, alpha, beta)) continue;
+            DotF acc[3];
+            chunk_cg1(M, tk.y, S, phase, alpha, beta, acc, failed);
+            if (failed) return;
+            double out[3];
+            block_sum3(acc[0], acc[1], acc[2], S.red, out);
+            if (threadIdx.x == 0) {
+                M.dots[3 * tk.y] = out[0];
+                M.dots[3 * tk.y + 1] = out[1];
+                M.dots[3 * tk.y + 2] = out[2];
+            }
+            __syncthreads();
+        }
+        if (!grid_barrier(A.bar, A.err)) return;
+        // ---- phase 2: shared nodes, then per-mesh scalars
+        for (int t = blockIdx.x; t < A.n_t2; t += gridDim.x) {
+            const int2 tk = A.t2[t];
+            const BMesh &M = A.meshes[tk.x];
+            float alpha, beta;
+            if (!task_scalars(M, sc, alpha, beta)) continue;
+            seg_cg1(M, tk.y, alpha, beta, S.red, A.active_cnt);
+        }
+        if (!grid_barrier(A.bar, A.err)) return;
+    }
+}
+
+// ---- FP64 true residual over the batch: chunk tasks, then shared segments.
+__global__ void __launch_bounds__(256) k_b_resid1(const BMesh *meshes, const int2 *t1, SmemLayout L) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int2 tk = t1[blockIdx.x];
+    const BMesh &M = meshes[tk.x];
+    __shared__ int s_run;
+    if (threadIdx.x == 0) s_run = !M.st->finished;
+    const ChunkSmem<double> S = chunk_smem<double>(smem, L);
+    if (threadIdx.x == 0) {
+        mbar_init(S.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!s_run) return;
+    VecArgs<double> a;
+    a.x = M.x64;
+    a.y = M.r64;
+    a.b = M.b64;
+    a.p = nullptr;
+    a.r = nullptr;
+    a.dinv = nullptr;
+    a.partial = M.part64;
+    a.dotbuf = nullptr;
+    a.st = nullptr;
+    a.host_done = nullptr;
+    uint32_t phase = 0;
+    bool failed = false;
+    DotD acc = (M.d.dim == 3) ? process_chunk<3, double, kResid>(M.d, a, tk.y, smem, L, phase, 0.0, failed)
+                              : process_chunk<2, double, kResid>(M.d, a, tk.y, smem, L, phase, 0.0, failed);
+    const double v = block_sum(acc, S.red);
+    if (threadIdx.x == 0) M.dots64[tk.y] = v;
+}
+
+__global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int2 *t2) {
+    __shared__ double red[34];
+    __shared__ bool s_last;
+    const int2 tk = t2[blockIdx.x];
+    const BMesh &M = meshes[tk.x];
+    const MeshDev &m = M.d;
+    if (M.st->finished) return;
+    const int64_t s0 = (int64_t)tk.y * kSegLen;
+    const int64_t s1 = s0 + kSegLen < m.n_shared ? s0 + kSegLen : m.n_shared;
+    DotD acc;
+    for (int64_t sidx = s0 + threadIdx.x; sidx < s1; sidx += blockDim.x) {
+        const int64_t g = m.n_int + sidx;
+        double sum = 0.0;
+        for (int k = m.shr_ptr[sidx]; k < m.shr_ptr[sidx + 1]; ++k) sum += M.part64[m.shr_slot[k]];
+        const double rv = m.dirichlet[g] ? 0.0 : M.b64[g] - sum;
+        M.r64[g] = rv;
+        acc.add_prod(rv, rv);
+    }
+    const double v = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        M.dots64[m.n_chunks + tk.y] = v;
+        const unsigned int t = atomic_add_acq_rel(&M.st->cnt_r, 1u);
+        s_last = (t == (unsigned)M.n_segs - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    const int n = m.n_chunks + M.n_segs;
+    double rr = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) rr += __ldcg(M.dots64 + k);
+    rr = block_sum(rr, red);
+    if (threadIdx.x == 0) {
+        BState *st = M.st;
+        st->cnt_r = 0;
+        st->rr64 = rr;
+        const double bb = st->bb > 0.0 ? st->bb : 1.0;
+        st->active = (rr > st->tol2 * bb) ? 1 : 0;
+        st->scale = rr > 0.0 ? 1.0 / sqrt(rr) : 1.0;
+        // fresh inner solve state
+        st->first = 1;
+        st->done = 0;
+        st->status = 0;
+        st->iters = 0;
+        st->alpha = 0.0;
+        st->beta = 0.0;
+        st->gamma = 0.0;
+    }
+}
+
+// ---- node-range steps over the batch
+enum VecOp : int { kPrepare = 0, kInnerInit = 1, kCorrect = 2, kFinish = 3 };
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *t3) {
+    __shared__ double red[34];
+    __shared__ bool s_last;
+    const int2 tk = t3[blockIdx.x];
+    const BMesh &M = meshes[tk.x];
+    const MeshDev &m = M.d;
+    const int64_t i0 = (int64_t)tk.y * kVecLen;
+    const int64_t i1 = i0 + kVecLen < m.n_pad ? i0 + kVecLen : m.n_pad;
+    if (OP == kPrepare) {
+        DotD acc;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            double bv = 0.0, xv = 0.0;
+            if (i < m.n_nodes && !m.dirichlet[i]) {
+                const int o = M.old_of_new[i];
+                bv = M.b_user[o];
+                xv = M.x_user[o];
+            }
+            M.b64[i] = bv;
+            M.x64[i] = xv;
+            acc.add_prod(bv, bv);
+        }
+        const double v = block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            M.vdots[tk.y] = v;
+            const unsigned int t = atomic_add_acq_rel(&M.st->cnt_v, 1u);
+            s_last = (t == (unsigned)M.n_vt - 1u);
+        }
+        __syncthreads();
+        if (!s_last) return;
+        double bb = 0.0;
+        for (int k = threadIdx.x; k < M.n_vt; k += blockDim.x) bb += __ldcg(M.vdots + k);
+        bb = block_sum(bb, red);
+        if (threadIdx.x == 0) {
+            M.st->cnt_v = 0;
+            M.st->bb = bb;
+        }
+        return;
+    }
+    if (OP == kFinish) {
+        for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x)
+            if (j < m.n_nodes) M.x_user[j] = M.x64[M.new_of_old[j]];
+        return;
+    }
+    __shared__ double s_sc[2];
+    if (threadIdx.x == 0) {
+        s_sc[0] = (M.st->active && !M.st->finished) ? 1.0 : 0.0;
+        s_sc[1] = M.st->scale;
+    }
+    __syncthreads();
+    if (s_sc[0] == 0.0) return;
+    const double scale = s_sc[1];
+    if (OP == kInnerInit) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            M.r[i] = (float)(M.r64[i] * scale);
+            M.x[i] = 0.f;
+            M.p[i] = 0.f;
+            M.s[i] = 0.f;
+            M.w[i] = 0.f;
+        }
+    } else {  // kCorrect
+        const double inv = 1.0 / scale;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) M.x64[i] += (double)M.x[i] * inv;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return PS_OK;
+    ps_set_last_error(cudaGetErrorString(e));
+    return cuda_status(e);
+}
+
+// Opt a kernel in to the largest dynamic shared memory the device allows
+// next to the kernel's own static shared memory.
+template <typename F>
+static cudaError_t allow_max_dyn_smem(F *func) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void *)func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
+int batched_set_attrs() {
+    cudaError_t e = allow_max_dyn_smem(k_batch_pcg);
+    if (e == cudaSuccess) e = allow_max_dyn_smem(k_b_resid1);
+    return cuda_rc(e);
+}
+
+static int ensure_batch_ws(ps_mesh *m) {
+    if (m->batch_ws) return PS_OK;
+    int rc = ensure_workspace(m);
+    if (rc != PS_OK) return rc;
+    BatchMeshWs *w = new BatchMeshWs();
+    const int64_t np = m->dev.n_pad;
+    w->n_segs = (int)std::max<int64_t>(1, (m->prep.n_shared + kSegLen - 1) / kSegLen);
+    w->n_vt = (int)((np + kVecLen - 1) / kVecLen);
+    void *p;
+    auto A = [&](void **dst, size_t bytes) -> int {
+        int r = dalloc(m->ctx, dst, bytes, w->allocs);
+        if (r == PS_OK) cudaMemset(*dst, 0, bytes);
+        return r;
+    };
+    rc = A(&p, np * 4);
+    w->s32 = (float *)p;
+    if (rc == PS_OK) rc = A(&p, np * 4), w->w32 = (float *)p;
+    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 3 * 8), w->dots = (double *)p;
+    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 8), w->dots64 = (double *)p;
+    if (rc == PS_OK) rc = A(&p, (size_t)w->n_vt * 8), w->vdots = (double *)p;
+    if (rc == PS_OK) rc = A(&p, sizeof(BState)), w->st = (BState *)p;
+    if (rc != PS_OK) {
+        dfree_all(m->ctx, w->allocs);
+        delete w;
+        return rc;
+    }
+    m->batch_ws = w;
+    return PS_OK;
+}
+
+void batched_release_mesh(ps_mesh *m) {
+    if (!m->batch_ws) return;
+    BatchMeshWs *w = static_cast<BatchMeshWs *>(m->batch_ws);
+    dfree_all(m->ctx, w->allocs);
+    delete w;
+    m->batch_ws = nullptr;
+}
+
+void batch_plan_free(BatchPlan &plan) {
+    if (plan.ctx) dfree_all(plan.ctx, plan.allocs);
+    if (plan.h_active) cudaFreeHost(plan.h_active);
+    plan = BatchPlan();
+}
+
+int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, BatchPlan &plan) {
+    batch_plan_free(plan);
+    plan.ctx = ctx;
+    plan.meshes.assign(meshes, meshes + n);
+    std::vector<int2> t1, t2, t3;
+    plan.h_meshes.resize(n);
+    for (int i = 0; i < n; ++i) {
+        ps_mesh *m = meshes[i];
+        int rc = ensure_batch_ws(m);
+        if (rc != PS_OK) return rc;
+        BatchMeshWs *w = static_cast<BatchMeshWs *>(m->batch_ws);
+        BMesh &B = plan.h_meshes[i];
+        std::memset(&B, 0, sizeof(B));
+        B.d = m->dev;
+        B.x = m->ws.x32;
+        B.r = m->ws.r32;
+        B.p = m->ws.p32;
+        B.s = w->s32;
+        B.w = w->w32;
+        B.part = m->ws.part32;
+        B.dots = w->dots;
+        B.x64 = m->ws.x64;
+        B.b64 = m->ws.b64;
+        B.r64 = m->ws.r64;
+        B.part64 = m->ws.part64;
+        B.dots64 = w->dots64;
+        B.vdots = w->vdots;
+        B.old_of_new = m->d_old_of_new;
+        B.new_of_old = m->d_new_of_old;
+        B.n_segs = w->n_segs;
+        B.n_vt = w->n_vt;
+        B.st = w->st;
+        for (int c = 0; c < m->dev.n_chunks; ++c) t1.push_back(make_int2(i, c));
+        for (int s = 0; s < w->n_segs; ++s) t2.push_back(make_int2(i, s));
+        for (int v = 0; v < w->n_vt; ++v) t3.push_back(make_int2(i, v));
+        plan.smem32 = std::max(plan.smem32, m->dev.sm32.total);
+        plan.smem64 = std::max(plan.smem64, m->dev.sm64.total);
+    }
+    // The persistent kernel's shared-memory layout must fit every mesh: use
+    // the element-wise maximum of the per-mesh layouts' segment sizes.
+    plan.n_t1 = (int)t1.size();
+    plan.n_t2 = (int)t2.size();
+    plan.n_t3 = (int)t3.size();
+    void *p;
+    int rc = dalloc(ctx, &p, (size_t)n * sizeof(BMesh), plan.allocs);
+    plan.d_meshes = (BMesh *)p;
+    if (rc == PS_OK) rc = dalloc(ctx, &p, t1.size() * sizeof(int2), plan.allocs), plan.d_t1 = (int2 *)p;
+    if (rc == PS_OK) rc = dalloc(ctx, &p, t2.size() * sizeof(int2), plan.allocs), plan.d_t2 = (int2 *)p;
+    if (rc == PS_OK) rc = dalloc(ctx, &p, t3.size() * sizeof(int2), plan.allocs), plan.d_t3 = (int2 *)p;
+    if (rc != PS_OK) return rc;
+    cudaError_t e = cudaMemcpy(plan.d_t1, t1.data(), t1.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(plan.d_t2, t2.data(), t2.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(plan.d_t3, t3.data(), t3.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&plan.h_active, 64, cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_rc(e);
+    plan.h_st.resize(n);
+    return PS_OK;
+}
+
+// Combined shared-memory layout: every mesh's segments fit.
+static SmemLayout max_layout(const BatchPlan &plan, bool fp64) {
+    int max_loc = 0, max_patch = 0, max_inc = 0, max_sh = 0;
+    for (ps_mesh *m : plan.meshes) {
+        max_loc = std::max(max_loc, m->prep.max_loc);
+        max_patch = std::max(max_patch, m->prep.max_patch);
+        max_inc = std::max(max_inc, m->prep.max_inc);
+        max_sh = std::max(max_sh, m->prep.max_sh);
+    }
+    return fp64 ? make_layout(8, sizeof(NodeD), max_loc, max_patch, max_inc, max_sh)
+                : make_layout(4, sizeof(NodeF), max_loc, max_patch, max_inc, max_sh);
+}
+
+int batch_begin(BatchPlan &plan, const double *const *b_user, double *const *x_user, double tol, double inner_tol,
+                long long max_iters, cudaStream_t s) {
+    const int n = (int)plan.meshes.size();
+    for (int i = 0; i < n; ++i) {
+        plan.h_meshes[i].b_user = b_user[i];
+        plan.h_meshes[i].x_user = x_user[i];
+        BState &st = plan.h_st[i];
+        std::memset(&st, 0, sizeof(st));
+        st.tol2 = tol * tol;
+        st.inner_tol2 = inner_tol * inner_tol;
+        st.max_iters = max_iters;
+        st.active = 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(plan.d_meshes, plan.h_meshes.data(), n * sizeof(BMesh), cudaMemcpyHostToDevice, s);
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(plan.h_meshes[i].st, &plan.h_st[i], sizeof(BState), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_rc(e);
+    k_b_vec<kPrepare><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
+    return cuda_rc(cudaGetLastError());
+}
+
+int batch_read_states(BatchPlan &plan, cudaStream_t s) {
+    const int n = (int)plan.meshes.size();
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&plan.h_st[i], plan.h_meshes[i].st, sizeof(BState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_rc(e);
+}
+
+int batch_residual(BatchPlan &plan, cudaStream_t s, int *n_active) {
+    const SmemLayout L = max_layout(plan, true);
+    k_b_resid1<<<plan.n_t1, 256, L.total, s>>>(plan.d_meshes, plan.d_t1, L);
+    k_b_resid2<<<plan.n_t2, 256, 0, s>>>(plan.d_meshes, plan.d_t2);
+    int rc = cuda_rc(cudaGetLastError());
+    if (rc != PS_OK) return rc;
+    rc = batch_read_states(plan, s);
+    if (rc != PS_OK) return rc;
+    int act = 0;
+    for (auto &st : plan.h_st) act += st.active;
+    *n_active = act;
+    return PS_OK;
+}
+
+int batch_inner(BatchPlan &plan, int epoch, cudaStream_t s) {
+    const int n = (int)plan.meshes.size();
+    int act = 0;
+    for (auto &st : plan.h_st) act += st.active;
+    if (act == 0) return PS_OK;
+    k_b_vec<kInnerInit><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
+    int rc = cuda_rc(cudaGetLastError());
+    if (rc != PS_OK) return rc;
+    ps_ctx *ctx = plan.ctx;
+    if (!ctx->d_bar) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, 1024) != cudaSuccess) return PS_ENOMEM;
+        cudaMemset(p, 0, 1024);
+        ctx->d_bar = (unsigned int *)p;
+    }
+    int *d_active = (int *)(ctx->d_bar + 128);
+    rc = cuda_rc(cudaMemcpyAsync(d_active, &act, sizeof(int), cudaMemcpyHostToDevice, s));
+    if (rc != PS_OK) return rc;
+    const SmemLayout L = max_layout(plan, false);
+    int per_sm = 0;
+    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, L.total));
+    if (rc != PS_OK) return rc;
+    if (per_sm < 1) return PS_EINVAL;
+    int grid = ctx->sms * std::min(per_sm, 4);
+    grid = std::max(1, std::min(grid, std::max(plan.n_t1, 1)));
+    PcgArgs A;
+    A.meshes = plan.d_meshes;
+    A.t1 = plan.d_t1;
+    A.t2 = plan.d_t2;
+    A.n_t1 = plan.n_t1;
+    A.n_t2 = plan.n_t2;
+    A.bar = ctx->d_bar;
+    A.active_cnt = d_active;
+    A.err = ctx->d_err;
+    A.max_it = epoch > 0 ? epoch : 256;
+    A.L = L;
+    long long cap_it = 0;
+    for (auto &st : plan.h_st) cap_it = std::max(cap_it, st.max_iters);
+    const long long max_launches = cap_it / A.max_it + 4;
+    for (long long launch = 0;; ++launch) {
+        if (launch >= max_launches) {
+            ps_set_last_error("persistent solver did not finish within its iteration budget");
+            return PS_ETIMEOUT;
+        }
+        void *args[] = {&A};
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = L.total;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        rc = cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_batch_pcg, args));
+        if (rc != PS_OK) return rc;
+        rc = cuda_rc(cudaMemcpyAsync(plan.h_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (rc != PS_OK) return rc;
+        rc = cuda_rc(cudaStreamSynchronize(s));
+        if (rc != PS_OK) return rc;
+        int herr = 0;
+        cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (herr) {
+            cudaMemset(ctx->d_err, 0, sizeof(int));
+            cudaMemset(ctx->d_bar, 0, 1024);
+            return PS_ETIMEOUT;
+        }
+        if (*plan.h_active <= 0) break;
+    }
+    (void)n;
+    return PS_OK;
+}
+
+int batch_correct(BatchPlan &plan, cudaStream_t s) {
+    k_b_vec<kCorrect><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
+    return cuda_rc(cudaGetLastError());
+}
+
+int batch_finish(BatchPlan &plan, cudaStream_t s) {
+    k_b_vec<kFinish><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
+    return cuda_rc(cudaGetLastError());
+}
+
 }  // namespace ps
 
-extern "C" int ps_batch_solve(ps_mesh *const *, int, const double *const *, double *const *,
-                              const ps_solve_opts *, ps_solve_info *, void *) {
-    return PS_ESTATE;
+using namespace ps;
+
+namespace ps {
+int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
+                       const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s);
+}
+
+extern "C" int ps_batch_solve(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
+                              const ps_solve_opts *opts, ps_solve_info *infos, void *stream) {
+    if (!meshes || n < 1 || !b_dev || !x_dev) return PS_EINVAL;
+    ps_ctx *ctx = meshes[0] ? meshes[0]->ctx : nullptr;
+    if (!ctx) return PS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!meshes[i] || meshes[i]->ctx != ctx || !b_dev[i] || !x_dev[i]) return PS_EINVAL;
+        if (!meshes[i]->coeff_ok) return PS_ESTATE;
+        for (int j = 0; j < i; ++j)
+            if (meshes[j] == meshes[i]) return PS_EINVAL;
+    }
+    ps_solve_opts o;
+    if (opts) o = *opts; else ps_solve_opts_default(&o);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_rc(e);
+    return batch_solve_locked(meshes, n, b_dev, x_dev, o, infos, (cudaStream_t)stream);
+}
+
+int ps::batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
+                           const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s) {
+    ps_ctx *ctx = meshes[0]->ctx;
+    const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+    const long long max_it = o.max_iters > 0 ? o.max_iters : 100000;
+    const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
+    auto t0 = std::chrono::steady_clock::now();
+    BatchPlan plan;
+    int rc = batch_plan_build(ctx, meshes, n, plan);
+    std::vector<int> outer(n, 0);
+    if (rc == PS_OK) rc = batch_begin(plan, b_dev, x_dev, tol, itol, max_it, s);
+    while (rc == PS_OK) {
+        int act = 0;
+        rc = batch_residual(plan, s, &act);
+        if (rc != PS_OK) break;
+        bool changed = false;
+        act = 0;
+        for (int i = 0; i < n; ++i) {
+            BState &st = plan.h_st[i];
+            if (st.finished) continue;
+            if (!st.active || outer[i] >= max_outer || st.iters_total >= max_it || st.status == kCgBreakdown) {
+                st.active = 0;
+                st.finished = 1;
+                changed = true;
+                continue;
+            }
+            ++outer[i];
+            ++act;
+        }
+        if (changed)
+            for (int i = 0; i < n && rc == PS_OK; ++i)
+                rc = cuda_rc(cudaMemcpyAsync(plan.h_meshes[i].st, &plan.h_st[i], sizeof(BState),
+                                             cudaMemcpyHostToDevice, s));
+        if (rc != PS_OK || act == 0) break;
+        rc = batch_inner(plan, o.graph_iters > 0 ? o.graph_iters * 8 : 256, s);
+        if (rc != PS_OK) break;
+        rc = batch_correct(plan, s);
+    }
+    if (rc == PS_OK) rc = batch_finish(plan, s);
+    if (rc == PS_OK) rc = batch_read_states(plan, s);
+    int first_err = PS_OK;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == PS_OK) {
+        for (int i = 0; i < n; ++i) {
+            const BState &st = plan.h_st[i];
+            const double bb = st.bb > 0 ? st.bb : 1.0;
+            const double rel = std::sqrt(st.rr64 / bb);
+            const bool conv = st.rr64 <= st.tol2 * bb;
+            int status = conv ? PS_OK : (st.status == kCgBreakdown ? PS_EBREAKDOWN : PS_ENOTCONV);
+            if (infos) {
+                ps_solve_info &inf = infos[i];
+                std::memset(&inf, 0, sizeof(inf));
+                inf.status = status;
+                inf.converged = conv;
+                inf.iters_outer = outer[i] + 1;
+                inf.iters_inner = st.iters_total;
+                inf.rel_res = rel;
+                inf.bnorm = std::sqrt(st.bb);
+                inf.n_free = meshes[i]->prep.n_free;
+                inf.seconds = secs;
+            }
+            if (status != PS_OK && first_err == PS_OK) first_err = status;
+        }
+    }
+    batch_plan_free(plan);
+    return rc != PS_OK ? rc : first_err;
 }

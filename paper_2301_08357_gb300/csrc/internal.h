@@ -7,6 +7,7 @@
 #include <set>
 #include <vector>
 
+#include "../../include/pressure.h"
 #include "mesh_prep.h"
 #include "ops.cuh"
 
@@ -55,6 +56,8 @@ int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 // batched.cu
 int batched_set_attrs();
 void batched_release_mesh(ps_mesh *m);
+int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
+                       const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s);
 
 }  // namespace ps
 
@@ -67,6 +70,7 @@ struct ps_ctx {
     std::mutex mu;
     std::set<ps_mesh *> meshes;
     int *d_err = nullptr;
+    unsigned int *d_bar = nullptr;   // grid-barrier words + active counter of the persistent solver
 };
 
 struct ps_mesh {

@@ -23,7 +23,7 @@ namespace ps {
 enum Mode : int { kApply = 0, kCG = 1, kResid = 2, kDiag = 3 };
 
 struct SmemLayout {
-    uint32_t node, val, pids, incp, inc, shid, contrib, red, bar, total;
+    uint32_t node, val, aux, pids, incp, inc, shid, contrib, red, bar, total;
 };
 
 struct MeshDev {
@@ -78,6 +78,96 @@ __device__ __forceinline__ double cg_dir(double dinv, double r, double beta, dou
 
 __device__ __forceinline__ int ld_flag(const int *p) { return *(volatile const int *)p; }
 
+// Shared-memory view of one staged chunk.
+template <typename T>
+struct ChunkSmem {
+    typename NodeOf<T>::type *node;
+    T *val, *aux, *contrib;
+    uint16_t *pids, *incp, *inc;
+    int32_t *shid;
+    uint64_t *bar;
+    double *red;
+};
+
+template <typename T>
+__device__ __forceinline__ ChunkSmem<T> chunk_smem(unsigned char *smem, const SmemLayout &L) {
+    ChunkSmem<T> S;
+    S.node = reinterpret_cast<typename NodeOf<T>::type *>(smem + L.node);
+    S.val = reinterpret_cast<T *>(smem + L.val);
+    S.aux = reinterpret_cast<T *>(smem + L.aux);
+    S.contrib = reinterpret_cast<T *>(smem + L.contrib);
+    S.pids = reinterpret_cast<uint16_t *>(smem + L.pids);
+    S.incp = reinterpret_cast<uint16_t *>(smem + L.incp);
+    S.inc = reinterpret_cast<uint16_t *>(smem + L.inc);
+    S.shid = reinterpret_cast<int32_t *>(smem + L.shid);
+    S.bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    S.red = reinterpret_cast<double *>(smem + L.red);
+    return S;
+}
+
+// Thread 0 issues the bulk copies of chunk cd's static data (node records,
+// patch records, incidence pointers and lists, shared-node ids).  When the
+// shared memory was used by an earlier chunk, the caller has synchronised the
+// block; the proxy fence orders those generic-proxy reads before the
+// async-proxy writes.
+template <typename T>
+__device__ __forceinline__ void stage_issue(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S) {
+    using N4 = typename NodeOf<T>::type;
+    if (threadIdx.x != 0) return;
+    const int p_pad = (cd.n_patch + kPatchPad - 1) / kPatchPad * kPatchPad;
+    const int incp_n = (cd.n_loc + 1 + kIncpPad - 1) / kIncpPad * kIncpPad;
+    const int inc_n = (cd.n_inc + kIncPad - 1) / kIncPad * kIncPad;
+    const int sh_n = (cd.n_sh + kShPad - 1) / kShPad * kShPad;
+    const N4 *gnode = (sizeof(T) == 4) ? reinterpret_cast<const N4 *>(m.node32) : reinterpret_cast<const N4 *>(m.node64);
+    const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(N4);
+    const uint32_t b_pids = (uint32_t)p_pad * (kPatchIds * 2u);
+    const uint32_t b_incp = (uint32_t)incp_n * 2u;
+    const uint32_t b_inc = (uint32_t)inc_n * 2u;
+    const uint32_t b_sh = (uint32_t)sh_n * 4u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(S.bar, b_node + b_pids + b_incp + b_inc + b_sh);
+    bulk_g2s(S.node, gnode + cd.node_off, b_node, S.bar);
+    bulk_g2s(S.pids, m.pids + (size_t)cd.patch_off * kPatchIds, b_pids, S.bar);
+    bulk_g2s(S.incp, m.incp + cd.incp_off, b_incp, S.bar);
+    bulk_g2s(S.inc, m.inc + cd.inc_off, b_inc, S.bar);
+    if (b_sh) bulk_g2s(S.shid, m.sh_ids + cd.sh_off, b_sh, S.bar);
+}
+
+// Wait for the staged data (bounded); block-uniform result.  On timeout the
+// error flag is set and the copies in flight are waited for once more.
+template <typename T>
+__device__ __forceinline__ bool stage_wait(const MeshDev &m, const ChunkSmem<T> &S, uint32_t &phase) {
+    bool ok = mbar_wait_bounded(S.bar, phase);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(m.err, kErrMbarTimeout);
+        mbar_wait_bounded(S.bar, phase);
+    }
+    phase ^= 1u;
+    return ok;
+}
+
+// Element contributions of every star patch of the chunk into S.contrib.
+template <int D, typename T, bool DIAG>
+__device__ __forceinline__ void patches_eval(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S) {
+    using N4 = typename NodeOf<T>::type;
+    const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
+    const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
+    for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x)
+        patch_eval<D, T, N4, DIAG>(S.node, S.val, S.pids + q * kPatchIds, g_bdt2 + q * kPatchMax,
+                                   S.contrib + q * kPatchSlots);
+    __syncthreads();
+}
+
+// Sum of the contributions of local node l in incidence order.
+template <typename T>
+__device__ __forceinline__ T node_sum(const ChunkSmem<T> &S, int l) {
+    const int b = S.incp[l], e = S.incp[l + 1];
+    T s = T(0);
+    for (int k = b; k < e; ++k) s += S.contrib[S.inc[k]];
+    return s;
+}
+
 // Process chunk c.  Returns this thread's share of the mode's dot product
 // (CG: p.q, resid: r.r over interior nodes).  `phase` is the mbarrier parity
 // to wait for; it flips on return.  Block-uniform; contains __syncthreads.
@@ -85,38 +175,10 @@ template <int D, typename T, int MODE>
 __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs<T> &a, int c, unsigned char *smem,
                                                  const SmemLayout &L, uint32_t &phase, T beta_cg, bool &failed) {
     using Acc = typename DotOf<T>::type;
-    using N4 = typename NodeOf<T>::type;
     const ChunkDesc cd = m.chunks[c];
-    N4 *s_node = reinterpret_cast<N4 *>(smem + L.node);
-    T *s_val = reinterpret_cast<T *>(smem + L.val);
-    uint16_t *s_pids = reinterpret_cast<uint16_t *>(smem + L.pids);
-    uint16_t *s_incp = reinterpret_cast<uint16_t *>(smem + L.incp);
-    uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
-    int32_t *s_shid = reinterpret_cast<int32_t *>(smem + L.shid);
-    T *s_contrib = reinterpret_cast<T *>(smem + L.contrib);
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-
-    const int n_loc = cd.n_loc, n_int = cd.n_int, n_sh = cd.n_sh, n_patch = cd.n_patch;
-    const int p_pad = (n_patch + kPatchPad - 1) / kPatchPad * kPatchPad;
-    const int incp_n = (n_loc + 1 + kIncpPad - 1) / kIncpPad * kIncpPad;
-    const int inc_n = (cd.n_inc + kIncPad - 1) / kIncPad * kIncPad;
-    const int sh_n = (n_sh + kShPad - 1) / kShPad * kShPad;
-    const N4 *gnode = (sizeof(T) == 4) ? reinterpret_cast<const N4 *>(m.node32) : reinterpret_cast<const N4 *>(m.node64);
-    const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
-
-    if (threadIdx.x == 0) {
-        const uint32_t b_node = (uint32_t)n_loc * sizeof(N4);
-        const uint32_t b_pids = (uint32_t)p_pad * (kPatchIds * 2u);
-        const uint32_t b_incp = (uint32_t)incp_n * 2u;
-        const uint32_t b_inc = (uint32_t)inc_n * 2u;
-        const uint32_t b_sh = (uint32_t)sh_n * 4u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_pids + b_incp + b_inc + b_sh);
-        bulk_g2s(s_node, gnode + cd.node_off, b_node, s_bar);
-        bulk_g2s(s_pids, m.pids + (size_t)cd.patch_off * kPatchIds, b_pids, s_bar);
-        bulk_g2s(s_incp, m.incp + cd.incp_off, b_incp, s_bar);
-        bulk_g2s(s_inc, m.inc + cd.inc_off, b_inc, s_bar);
-        if (b_sh) bulk_g2s(s_shid, m.sh_ids + cd.sh_off, b_sh, s_bar);
-    }
+    const ChunkSmem<T> S = chunk_smem<T>(smem, L);
+    const int n_loc = cd.n_loc, n_int = cd.n_int;
+    stage_issue<T>(m, cd, S);
     // interior input values do not depend on the staged data: fetch them
     // while the bulk copies are in flight (masked below, once records landed)
     T vin[4];
@@ -129,26 +191,20 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
             vin[k] = (MODE == kCG) ? cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]) : a.x[g];
         }
     }
-    bool ok = mbar_wait_bounded(s_bar, phase);
-    ok = __syncthreads_and(ok);
-    if (!ok) {
-        if (threadIdx.x == 0) atomicOr(m.err, kErrMbarTimeout);
-        mbar_wait_bounded(s_bar, phase);   // let copies in flight land before leaving
-        phase ^= 1u;
+    if (!stage_wait<T>(m, S, phase)) {
         failed = true;
         return Acc();
     }
-    phase ^= 1u;
 
     // ---- gather the input vector (masked on Dirichlet nodes)
     if (MODE != kDiag) {
         auto finish = [&](int l, T v) {
-            if (is_dirichlet(s_node[l].w)) v = T(0);
+            if (is_dirichlet(S.node[l].w)) v = T(0);
             if (MODE == kCG && l < n_int) a.p[cd.int_begin + l] = v;
-            s_val[l] = v;
+            S.val[l] = v;
         };
         auto fetch = [&](int l) -> T {
-            const int g = l < n_int ? cd.int_begin + l : s_shid[l - n_int];
+            const int g = l < n_int ? cd.int_begin + l : S.shid[l - n_int];
             return (MODE == kCG) ? cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]) : a.x[g];
         };
 #pragma unroll
@@ -160,20 +216,13 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
         __syncthreads();
     }
 
-    // ---- patch contributions (one thread per star patch)
-    const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
-    for (int q = threadIdx.x; q < n_patch; q += blockDim.x)
-        patch_eval<D, T, N4, MODE == kDiag>(s_node, s_val, s_pids + q * kPatchIds, g_bdt2 + q * kPatchMax,
-                                            s_contrib + q * kPatchSlots);
-    __syncthreads();
+    patches_eval<D, T, MODE == kDiag>(m, cd, S);
 
     // ---- per-node sums in incidence order
     Acc dot;
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const int b = s_incp[l], e = s_incp[l + 1];
-        T s = T(0);
-        for (int k = b; k < e; ++k) s += s_contrib[s_inc[k]];
-        const bool dir = is_dirichlet(s_node[l].w);
+        T s = node_sum(S, l);
+        const bool dir = is_dirichlet(S.node[l].w);
         if (dir) s = T(0);
         if (l < n_int) {
             const int g = cd.int_begin + l;
@@ -181,7 +230,7 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
                 a.y[g] = s;
             } else if (MODE == kCG) {
                 a.y[g] = s;
-                dot.add_prod(s_val[l], s);
+                dot.add_prod(S.val[l], s);
             } else if (MODE == kResid) {
                 const T rv = dir ? T(0) : a.b[g] - s;
                 a.y[g] = rv;

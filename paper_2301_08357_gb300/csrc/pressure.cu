@@ -74,6 +74,7 @@ SmemLayout make_layout(int esz, int nsz, int max_loc, int max_patch, int max_inc
     uint64_t off = 0;
     L.node = (uint32_t)off;    off += align128((uint64_t)max_loc * nsz);
     L.val = (uint32_t)off;     off += align128((uint64_t)max_loc * esz);
+    L.aux = (uint32_t)off;     off += align128((uint64_t)max_loc * esz);
     L.pids = (uint32_t)off;    off += align128(ppad * kPatchIds * 2);
     L.incp = (uint32_t)off;    off += align128((uint64_t)round_up(max_loc + 1, kIncpPad) * 2);
     L.inc = (uint32_t)off;     off += align128((uint64_t)round_up(max_inc > 0 ? max_inc : 1, kIncPad) * 2);
@@ -202,6 +203,7 @@ extern "C" void ps_ctx_destroy(ps_ctx *c) {
     std::vector<ps_mesh *> ms(c->meshes.begin(), c->meshes.end());
     for (ps_mesh *m : ms) ps_mesh_free(m);
     cudaFree(c->d_err);
+    if (c->d_bar) cudaFree(c->d_bar);
     delete c;
 }
 
@@ -797,6 +799,7 @@ extern "C" void ps_solve_opts_default(ps_solve_opts *o) {
     o->inner_tol = 1e-4;
     o->max_outer = 40;
     o->graph_iters = 32;
+    o->engine = PS_ENGINE_AUTO;
 }
 
 extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const ps_solve_opts *opts,
@@ -812,8 +815,16 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
     auto t0 = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
-    RC(ensure_workspace(m));
     cudaStream_t s = (cudaStream_t)stream;
+    if (o.mode == PS_MODE_MIXED && o.engine != PS_ENGINE_GRAPH && o.precond != PS_PRECOND_NONE) {
+        ps_mesh *one[1] = {m};
+        const double *bb[1] = {b};
+        double *xx[1] = {x};
+        int rc = batch_solve_locked(one, 1, bb, xx, o, inf, s);
+        inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return rc;
+    }
+    RC(ensure_workspace(m));
     Workspace &w = m->ws;
     const int64_t n = m->dev.n_nodes;
     const int g = grid_for(n, m->ctx->sms);

@@ -25,6 +25,7 @@ PS_ETIMEOUT, PS_ECUDA, PS_ESTATE, PS_ENOTFOUND = -5, -6, -7, -8
 PS_F32, PS_F64 = 1, 2
 PS_MODE_FP64, PS_MODE_MIXED = 0, 1
 PS_PRECOND_NONE, PS_PRECOND_JACOBI = 0, 1
+PS_ENGINE_AUTO, PS_ENGINE_GRAPH, PS_ENGINE_PERSISTENT = 0, 1, 2
 SOFT = {PS_OK, PS_PENDING, PS_ENOTCONV, PS_EBREAKDOWN}
 
 
@@ -48,7 +49,7 @@ class ps_mesh_opts(C.Structure):
 class ps_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int64), ("mode", C.c_int32), ("precond", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("graph_iters", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("engine", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class ps_solve_info(C.Structure):

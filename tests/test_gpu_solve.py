@@ -44,13 +44,15 @@ def ctx(P, torch_mod):
 
 
 def gpu_solve(P, torch, m, b, x0, **kw):
+    if "engine" not in kw and kw.get("mode") == "graph":
+        kw["mode"], kw["engine"] = 1, P.PS_ENGINE_GRAPH
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     xd = torch.as_tensor(x0, dtype=torch.float64, device="cuda").clone()
     st, info = P.ps_pressure_solve(m, bd, xd, P.make_opts(**kw))
     return st, info, xd.cpu().numpy()
 
 
-MODES = [(0, "fp64"), (1, "mixed")]
+MODES = [(0, "fp64"), (1, "mixed"), ("graph", "mixed_graph")]
 SMALL = [
     ("c1_64", lambda: S.make_c1(64), 0),
     ("c1_32_shuffled", lambda: S.shuffle_case(S.make_c1(32)), 41),
@@ -83,7 +85,7 @@ def test_solve_matches_oracle(P, torch_mod, ctx, name, make, chunk, mode, mname)
         assert res <= 1e-10 * 1.05, (name, mname, res, info.rel_res)
         assert np.all(x[case.dirichlet.astype(bool)] == 0.0)
         # error gate at the tightened tolerance
-        status, info, x = gpu_solve(P, torch_mod, m, b, x0, mode=mode, tol=1e-13)
+        status, info, x = gpu_solve(P, torch_mod, m, b, x0, mode=mode, tol=1e-13, max_outer=12)
         err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
         assert err <= 1e-9, (name, mname, err, info.rel_res)
     finally:
@@ -102,7 +104,7 @@ def test_solve_full_size_c2(P, torch_mod, ctx, mode, mname):
         res = A.residual(case.b, x)
         assert res <= 1e-10 * 1.05, (mname, res, info.rel_res)
         xs, st, it, rr = A.cg(case.b, precond=1, tol=1e-13)
-        status, info, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=mode, tol=1e-13)
+        status, info, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=mode, tol=1e-13, max_outer=12)
         err = np.linalg.norm(x2 - xs) / np.linalg.norm(xs)
         assert err <= 1e-9, (mname, err)
     finally:
