@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
+    ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
     return ap.parse_args()
 
 
@@ -190,7 +191,8 @@ def run_ours(args):
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()
     mode = P.PS_MODE_MIXED if args.mode == "mixed" else P.PS_MODE_FP64
-    opts = P.make_opts(mode=mode, tol=1e-10)
+    engine = {"auto": P.PS_ENGINE_AUTO, "graph": P.PS_ENGINE_GRAPH, "persistent": P.PS_ENGINE_PERSISTENT}[args.engine]
+    opts = P.make_opts(mode=mode, tol=1e-10, engine=engine)
     b = torch.as_tensor(case.b, device="cuda")
     x = torch.zeros_like(b)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")

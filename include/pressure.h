@@ -111,9 +111,11 @@ typedef struct {
     double rel_res;          /* final TRUE relative residual ||b-Ax||/||b||, FP64  */
     double bnorm;            /* ||b||_2 over free nodes                            */
     int64_t n_free;          /* number of free (non-Dirichlet) nodes               */
-    double seconds;          /* wall time of the call                              */
+    double seconds;          /* wall time of the call; for a served request the
+                                latency from submission to completion             */
     int64_t kernel_launches; /* CUDA kernels this call launched (graph nodes included) */
-    double reserved[3];
+    double queue_seconds;    /* served request: time queued before admission       */
+    double reserved[2];
 } ps_solve_info;
 
 typedef struct {
@@ -123,7 +125,9 @@ typedef struct {
     int64_t chunk_node_refs; /* sum over chunks of distinct nodes                  */
     int64_t device_bytes;    /* device memory held by this mesh                     */
     int32_t max_chunk_elems, max_chunk_nodes;
-    int64_t reserved[4];
+    int64_t solve_bytes;     /* device bytes of this mesh's solver state while a solve
+                                is in flight (the serving loop's admission unit)    */
+    int64_t reserved[3];
 } ps_mesh_stats;
 
 /* ---- library --------------------------------------------------------- */

@@ -65,6 +65,13 @@ __device__ __forceinline__ void block_sum3(const DotF &a, const DotF &b, const D
     out[2] = block_sum(c, red);
 }
 
+// A double as an unevaluated float pair (hi + lo), for partial sums that are
+// later reduced with FP32 error-free additions only.
+__device__ __forceinline__ float2 split_df(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 // One-reduction PCG update of one node from its old values (shared by the
 // chunk pass, for every local node, and the shared-node pass):
 //   s' = w + beta s, r' = r - alpha s', u' = D^-1 r', p' = D^-1 r + beta p,
@@ -142,15 +149,16 @@ __device__ void chunk_cg1(const BMesh &M, int c, const ChunkSmem<float> &S, uint
 // scalars.  Called by the last block to finish the mesh's phase-2 tasks.
 __device__ void mesh_scalars(const BMesh &M, double *red, int *active_cnt) {
     const int n = M.d.n_chunks + M.n_segs;
-    double g = 0.0, d = 0.0, rho = 0.0;
+    DotF ag, ad, ar;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        g += __ldcg(M.dots + 3 * k);
-        d += __ldcg(M.dots + 3 * k + 1);
-        rho += __ldcg(M.dots + 3 * k + 2);
+        const float2 g2 = __ldcg(M.dots + 3 * k), d2 = __ldcg(M.dots + 3 * k + 1), r2 = __ldcg(M.dots + 3 * k + 2);
+        ag.merge(g2.x, g2.y);
+        ad.merge(d2.x, d2.y);
+        ar.merge(r2.x, r2.y);
     }
-    g = block_sum(g, red);
-    d = block_sum(d, red);
-    rho = block_sum(rho, red);
+    double out[3];
+    block_sum3(ag, ad, ar, red, out);
+    const double g = out[0], d = out[1], rho = out[2];
     if (threadIdx.x != 0) return;
     BState *st = M.st;
     st->cnt2 = 0;
@@ -194,6 +202,7 @@ __device__ void mesh_scalars(const BMesh &M, double *red, int *active_cnt) {
     if (done) {
         st->status = status;
         st->done = 1;
+        st->phase = kPhCorrect;
         atomicSub(active_cnt, 1);
     }
 }
@@ -231,9 +240,9 @@ __device__ void seg_cg1(const BMesh &M, int seg, float alpha, float beta, double
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
         const int k = m.n_chunks + seg;
-        M.dots[3 * k] = out[0];
-        M.dots[3 * k + 1] = out[1];
-        M.dots[3 * k + 2] = out[2];
+        M.dots[3 * k] = split_df(out[0]);
+        M.dots[3 * k + 1] = split_df(out[1]);
+        M.dots[3 * k + 2] = split_df(out[2]);
         const unsigned int t = atomic_add_acq_rel(&M.st->cnt2, 1u);
         s_last = (t == (unsigned)M.n_segs - 1u);
     }
@@ -241,6 +250,8 @@ __device__ void seg_cg1(const BMesh &M, int seg, float alpha, float beta, double
     if (s_last) mesh_scalars(M, red, active_cnt);
     __syncthreads();
 }
+
+enum VecOp : int { kPrepare = 0, kInnerInit = 1, kCorrect = 2, kFinish = 3 };
 
 struct PcgArgs {
     const BMesh *meshes;
@@ -253,27 +264,31 @@ struct PcgArgs {
     SmemLayout L;
 };
 
-// Reads (done, active, alpha, beta) of a mesh once per block.
-__device__ __forceinline__ bool task_scalars(const BMesh &M, double *sc, float &alpha, float &beta) {
+// (run, alpha, beta) of mesh `mi` for this block, read at L2 once per phase
+// and mesh (the cache is reset at every grid barrier).
+struct ScalarCache {
+    int mesh;
+    int run;
+    float alpha, beta;
+};
+__device__ __forceinline__ void task_scalars(const BMesh *meshes, int mi, ScalarCache *sc) {
+    if (sc->mesh == mi) return;     // block-uniform
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const BState *st = M.st;
-        sc[0] = (__ldcg(&st->active) && !__ldcg(&st->done)) ? 1.0 : 0.0;
-        sc[1] = __ldcg(&st->alpha);
-        sc[2] = __ldcg(&st->beta);
+        const BState *st = meshes[mi].st;
+        sc->run = (__ldcg(&st->phase) == kPhInner && !__ldcg(&st->done)) ? 1 : 0;
+        sc->alpha = (float)__ldcg(&st->alpha);
+        sc->beta = (float)__ldcg(&st->beta);
+        sc->mesh = mi;
     }
     __syncthreads();
-    const bool run = sc[0] != 0.0;
-    alpha = (float)sc[1];
-    beta = (float)sc[2];
-    __syncthreads();
-    return run;
 }
 
 // The persistent inner solver: up to max_it iterations of every active mesh.
 __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const ChunkSmem<float> S = chunk_smem<float>(smem, A.L);
-    __shared__ double sc[4];
+    __shared__ ScalarCache sc;
     __shared__ int s_act;
     if (threadIdx.x == 0) {
         mbar_init(S.bar, 1);
@@ -283,35 +298,39 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
     uint32_t phase = 0;
     bool failed = false;
     for (int it = 0; it < A.max_it; ++it) {
-        if (threadIdx.x == 0) s_act = ld_acquire_i32(A.active_cnt);
+        if (threadIdx.x == 0) {
+            s_act = ld_acquire_i32(A.active_cnt);
+            sc.mesh = -1;
+        }
         __syncthreads();
         if (s_act <= 0) break;
         // ---- phase 1: chunks
         for (int t = blockIdx.x; t < A.n_t1; t += gridDim.x) {
             const int2 tk = A.t1[t];
             const BMesh &M = A.meshes[tk.x];
-            float alpha, beta;
-            if (!task_scalars(M, sc, alpha, beta)) continue;
+            task_scalars(A.meshes, tk.x, &sc);
+            if (!sc.run) continue;
             DotF acc[3];
-            chunk_cg1(M, tk.y, S, phase, alpha, beta, acc, failed);
+            chunk_cg1(M, tk.y, S, phase, sc.alpha, sc.beta, acc, failed);
             if (failed) return;
             double out[3];
             block_sum3(acc[0], acc[1], acc[2], S.red, out);
             if (threadIdx.x == 0) {
-                M.dots[3 * tk.y] = out[0];
-                M.dots[3 * tk.y + 1] = out[1];
-                M.dots[3 * tk.y + 2] = out[2];
+                M.dots[3 * tk.y] = split_df(out[0]);
+                M.dots[3 * tk.y + 1] = split_df(out[1]);
+                M.dots[3 * tk.y + 2] = split_df(out[2]);
             }
             __syncthreads();
         }
         if (!grid_barrier(A.bar, A.err)) return;
         // ---- phase 2: shared nodes, then per-mesh scalars
+        if (threadIdx.x == 0) sc.mesh = -1;
+        __syncthreads();
         for (int t = blockIdx.x; t < A.n_t2; t += gridDim.x) {
             const int2 tk = A.t2[t];
-            const BMesh &M = A.meshes[tk.x];
-            float alpha, beta;
-            if (!task_scalars(M, sc, alpha, beta)) continue;
-            seg_cg1(M, tk.y, alpha, beta, S.red, A.active_cnt);
+            task_scalars(A.meshes, tk.x, &sc);
+            if (!sc.run) continue;
+            seg_cg1(A.meshes[tk.x], tk.y, sc.alpha, sc.beta, S.red, A.active_cnt);
         }
         if (!grid_barrier(A.bar, A.err)) return;
     }
@@ -323,9 +342,9 @@ __global__ void __launch_bounds__(256) k_b_resid1(const BMesh *meshes, const int
     const int2 tk = t1[blockIdx.x];
     const BMesh &M = meshes[tk.x];
     __shared__ int s_run;
-    if (threadIdx.x == 0) s_run = !M.st->finished;
     const ChunkSmem<double> S = chunk_smem<double>(smem, L);
     if (threadIdx.x == 0) {
+        s_run = M.st->phase == kPhResid;
         mbar_init(S.bar, 1);
         fence_mbar_init();
     }
@@ -353,10 +372,13 @@ __global__ void __launch_bounds__(256) k_b_resid1(const BMesh *meshes, const int
 __global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int2 *t2) {
     __shared__ double red[34];
     __shared__ bool s_last;
+    __shared__ int s_run;
     const int2 tk = t2[blockIdx.x];
     const BMesh &M = meshes[tk.x];
     const MeshDev &m = M.d;
-    if (M.st->finished) return;
+    if (threadIdx.x == 0) s_run = M.st->phase == kPhResid;
+    __syncthreads();
+    if (!s_run) return;
     const int64_t s0 = (int64_t)tk.y * kSegLen;
     const int64_t s1 = s0 + kSegLen < m.n_shared ? s0 + kSegLen : m.n_shared;
     DotD acc;
@@ -385,33 +407,49 @@ __global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int
         st->cnt_r = 0;
         st->rr64 = rr;
         const double bb = st->bb > 0.0 ? st->bb : 1.0;
-        st->active = (rr > st->tol2 * bb) ? 1 : 0;
-        st->scale = rr > 0.0 ? 1.0 / sqrt(rr) : 1.0;
-        // fresh inner solve state
-        st->first = 1;
-        st->done = 0;
-        st->status = 0;
-        st->iters = 0;
-        st->alpha = 0.0;
-        st->beta = 0.0;
-        st->gamma = 0.0;
+        if (rr <= st->tol2 * bb) {
+            st->converged = 1;
+            st->phase = kPhOutput;
+        } else if (st->outer >= st->max_outer || st->iters_total >= st->max_iters || st->status == kCgBreakdown) {
+            st->phase = kPhOutput;
+        } else {
+            st->outer += 1;
+            st->scale = 1.0 / sqrt(rr);
+            st->first = 1;
+            st->done = 0;
+            st->status = 0;
+            st->iters = 0;
+            st->alpha = 0.0;
+            st->beta = 0.0;
+            st->gamma = 0.0;
+            st->phase = kPhInnerInit;
+        }
     }
 }
 
-// ---- node-range steps over the batch
-enum VecOp : int { kPrepare = 0, kInnerInit = 1, kCorrect = 2, kFinish = 3 };
-
+// ---- node-range steps over the batch; each acts on meshes in one phase and
+// the last block of a mesh advances it.
 template <int OP>
-__global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *t3) {
+__global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *t3, int *active_cnt) {
+    constexpr int want = OP == kPrepare ? kPhPrepare : OP == kInnerInit ? kPhInnerInit
+                       : OP == kCorrect ? kPhCorrect : kPhOutput;
     __shared__ double red[34];
     __shared__ bool s_last;
+    __shared__ double s_sc[2];
     const int2 tk = t3[blockIdx.x];
     const BMesh &M = meshes[tk.x];
     const MeshDev &m = M.d;
+    if (threadIdx.x == 0) {
+        s_sc[0] = M.st->phase == want ? 1.0 : 0.0;
+        s_sc[1] = M.st->scale;
+    }
+    __syncthreads();
+    if (s_sc[0] == 0.0) return;
+    const double scale = s_sc[1];
     const int64_t i0 = (int64_t)tk.y * kVecLen;
     const int64_t i1 = i0 + kVecLen < m.n_pad ? i0 + kVecLen : m.n_pad;
+    DotD acc;
     if (OP == kPrepare) {
-        DotD acc;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             double bv = 0.0, xv = 0.0;
             if (i < m.n_nodes && !m.dirichlet[i]) {
@@ -423,37 +461,7 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
             M.x64[i] = xv;
             acc.add_prod(bv, bv);
         }
-        const double v = block_sum(acc, red);
-        if (threadIdx.x == 0) {
-            M.vdots[tk.y] = v;
-            const unsigned int t = atomic_add_acq_rel(&M.st->cnt_v, 1u);
-            s_last = (t == (unsigned)M.n_vt - 1u);
-        }
-        __syncthreads();
-        if (!s_last) return;
-        double bb = 0.0;
-        for (int k = threadIdx.x; k < M.n_vt; k += blockDim.x) bb += __ldcg(M.vdots + k);
-        bb = block_sum(bb, red);
-        if (threadIdx.x == 0) {
-            M.st->cnt_v = 0;
-            M.st->bb = bb;
-        }
-        return;
-    }
-    if (OP == kFinish) {
-        for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x)
-            if (j < m.n_nodes) M.x_user[j] = M.x64[M.new_of_old[j]];
-        return;
-    }
-    __shared__ double s_sc[2];
-    if (threadIdx.x == 0) {
-        s_sc[0] = (M.st->active && !M.st->finished) ? 1.0 : 0.0;
-        s_sc[1] = M.st->scale;
-    }
-    __syncthreads();
-    if (s_sc[0] == 0.0) return;
-    const double scale = s_sc[1];
-    if (OP == kInnerInit) {
+    } else if (OP == kInnerInit) {
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             M.r[i] = (float)(M.r64[i] * scale);
             M.x[i] = 0.f;
@@ -461,9 +469,41 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
             M.s[i] = 0.f;
             M.w[i] = 0.f;
         }
-    } else {  // kCorrect
+    } else if (OP == kCorrect) {
         const double inv = 1.0 / scale;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) M.x64[i] += (double)M.x[i] * inv;
+    } else {  // kFinish
+        for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x)
+            if (j < m.n_nodes) M.x_user[j] = M.x64[M.new_of_old[j]];
+    }
+    double v = 0.0;
+    if (OP == kPrepare) v = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        if (OP == kPrepare) M.vdots[tk.y] = v;
+        const unsigned int t = atomic_add_acq_rel(&M.st->cnt_v, 1u);
+        s_last = (t == (unsigned)M.n_vt - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    double bb = 0.0;
+    if (OP == kPrepare) {
+        for (int k = threadIdx.x; k < M.n_vt; k += blockDim.x) bb += __ldcg(M.vdots + k);
+        bb = block_sum(bb, red);
+    }
+    if (threadIdx.x == 0) {
+        BState *st = M.st;
+        st->cnt_v = 0;
+        if (OP == kPrepare) {
+            st->bb = bb;
+            st->phase = kPhResid;
+        } else if (OP == kInnerInit) {
+            st->phase = kPhInner;
+            atomicAdd(active_cnt, 1);
+        } else if (OP == kCorrect) {
+            st->phase = kPhResid;
+        } else {
+            st->phase = kPhDone;
+        }
     }
 }
 
@@ -512,10 +552,9 @@ static int ensure_batch_ws(ps_mesh *m) {
     rc = A(&p, np * 4);
     w->s32 = (float *)p;
     if (rc == PS_OK) rc = A(&p, np * 4), w->w32 = (float *)p;
-    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 3 * 8), w->dots = (double *)p;
+    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 3 * sizeof(float2)), w->dots = (float2 *)p;
     if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 8), w->dots64 = (double *)p;
     if (rc == PS_OK) rc = A(&p, (size_t)w->n_vt * 8), w->vdots = (double *)p;
-    if (rc == PS_OK) rc = A(&p, sizeof(BState)), w->st = (BState *)p;
     if (rc != PS_OK) {
         dfree_all(m->ctx, w->allocs);
         delete w;
@@ -523,6 +562,12 @@ static int ensure_batch_ws(ps_mesh *m) {
     }
     m->batch_ws = w;
     return PS_OK;
+}
+
+int64_t batch_ws_bytes(const ps_mesh *m) {
+    // vectors of ps_mesh::ws and BatchMeshWs (an estimate for admission)
+    const int64_t np = m->dev.n_pad, sh = m->prep.sh_total;
+    return np * (5 * 8 + 6 * 4) + sh * 12 + (int64_t)m->dev.n_chunks * 40;
 }
 
 void batched_release_mesh(ps_mesh *m) {
@@ -534,20 +579,43 @@ void batched_release_mesh(ps_mesh *m) {
 }
 
 void batch_plan_free(BatchPlan &plan) {
+    if (plan.graph) cudaGraphExecDestroy(plan.graph);
+    if (plan.cap) cudaStreamDestroy(plan.cap);
     if (plan.ctx) dfree_all(plan.ctx, plan.allocs);
-    if (plan.h_active) cudaFreeHost(plan.h_active);
+    if (plan.h_st) cudaFreeHost(plan.h_st);
     plan = BatchPlan();
 }
 
-int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, BatchPlan &plan) {
+// Combined shared-memory layout: every mesh's segments fit.
+static SmemLayout max_layout(const std::vector<ps_mesh *> &meshes, bool fp64) {
+    int max_loc = 0, max_patch = 0, max_inc = 0, max_sh = 0;
+    for (ps_mesh *m : meshes) {
+        max_loc = std::max(max_loc, m->prep.max_loc);
+        max_patch = std::max(max_patch, m->prep.max_patch);
+        max_inc = std::max(max_inc, m->prep.max_inc);
+        max_sh = std::max(max_sh, m->prep.max_sh);
+    }
+    return fp64 ? make_layout(8, sizeof(NodeD), max_loc, max_patch, max_inc, max_sh)
+                : make_layout(4, sizeof(NodeF), max_loc, max_patch, max_inc, max_sh);
+}
+
+int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, BatchPlan &plan) {
     batch_plan_free(plan);
     plan.ctx = ctx;
     plan.meshes.assign(meshes, meshes + n);
+    plan.epoch_iters = epoch_iters > 0 ? epoch_iters : 256;
     std::vector<int2> t1, t2, t3;
     plan.h_meshes.resize(n);
+    void *p = nullptr;
+    int rc = dalloc(ctx, &p, (size_t)n * sizeof(BState) + 4096, plan.allocs);
+    if (rc != PS_OK) return rc;
+    plan.d_st = (BState *)p;
+    // grid-barrier words and the active-mesh counter live after the states
+    rc = cuda_rc(cudaMemset(p, 0, (size_t)n * sizeof(BState) + 4096));
+    if (rc != PS_OK) return rc;
     for (int i = 0; i < n; ++i) {
         ps_mesh *m = meshes[i];
-        int rc = ensure_batch_ws(m);
+        rc = ensure_batch_ws(m);
         if (rc != PS_OK) return rc;
         BatchMeshWs *w = static_cast<BatchMeshWs *>(m->batch_ws);
         BMesh &B = plan.h_meshes[i];
@@ -570,20 +638,15 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, BatchPlan &plan
         B.new_of_old = m->d_new_of_old;
         B.n_segs = w->n_segs;
         B.n_vt = w->n_vt;
-        B.st = w->st;
+        B.st = plan.d_st + i;
         for (int c = 0; c < m->dev.n_chunks; ++c) t1.push_back(make_int2(i, c));
-        for (int s = 0; s < w->n_segs; ++s) t2.push_back(make_int2(i, s));
+        for (int sg = 0; sg < w->n_segs; ++sg) t2.push_back(make_int2(i, sg));
         for (int v = 0; v < w->n_vt; ++v) t3.push_back(make_int2(i, v));
-        plan.smem32 = std::max(plan.smem32, m->dev.sm32.total);
-        plan.smem64 = std::max(plan.smem64, m->dev.sm64.total);
     }
-    // The persistent kernel's shared-memory layout must fit every mesh: use
-    // the element-wise maximum of the per-mesh layouts' segment sizes.
     plan.n_t1 = (int)t1.size();
     plan.n_t2 = (int)t2.size();
     plan.n_t3 = (int)t3.size();
-    void *p;
-    int rc = dalloc(ctx, &p, (size_t)n * sizeof(BMesh), plan.allocs);
+    rc = dalloc(ctx, &p, (size_t)n * sizeof(BMesh), plan.allocs);
     plan.d_meshes = (BMesh *)p;
     if (rc == PS_OK) rc = dalloc(ctx, &p, t1.size() * sizeof(int2), plan.allocs), plan.d_t1 = (int2 *)p;
     if (rc == PS_OK) rc = dalloc(ctx, &p, t2.size() * sizeof(int2), plan.allocs), plan.d_t2 = (int2 *)p;
@@ -592,162 +655,203 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, BatchPlan &plan
     cudaError_t e = cudaMemcpy(plan.d_t1, t1.data(), t1.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(plan.d_t2, t2.data(), t2.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(plan.d_t3, t3.data(), t3.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&plan.h_active, 64, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&plan.h_st, (size_t)n * sizeof(BState), cudaHostAllocDefault);
     if (e != cudaSuccess) return cuda_rc(e);
-    plan.h_st.resize(n);
+    std::memset(plan.h_st, 0, (size_t)n * sizeof(BState));
+    plan.L32 = max_layout(plan.meshes, false);
+    plan.L64 = max_layout(plan.meshes, true);
+    int per_sm = 0;
+    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, plan.L32.total));
+    if (rc != PS_OK) return rc;
+    if (per_sm < 1) {
+        ps_set_last_error("batch: shared-memory layout too large for the persistent kernel");
+        return PS_EINVAL;
+    }
+    plan.grid_pcg = std::max(1, std::min(ctx->sms * std::min(per_sm, 4), std::max(plan.n_t1, 1)));
     return PS_OK;
 }
 
-// Combined shared-memory layout: every mesh's segments fit.
-static SmemLayout max_layout(const BatchPlan &plan, bool fp64) {
-    int max_loc = 0, max_patch = 0, max_inc = 0, max_sh = 0;
-    for (ps_mesh *m : plan.meshes) {
-        max_loc = std::max(max_loc, m->prep.max_loc);
-        max_patch = std::max(max_patch, m->prep.max_patch);
-        max_inc = std::max(max_inc, m->prep.max_inc);
-        max_sh = std::max(max_sh, m->prep.max_sh);
-    }
-    return fp64 ? make_layout(8, sizeof(NodeD), max_loc, max_patch, max_inc, max_sh)
-                : make_layout(4, sizeof(NodeF), max_loc, max_patch, max_inc, max_sh);
+void batch_arm(BatchPlan &plan, int i, const double *b_user, double *x_user, const ps_solve_opts &o) {
+    plan.h_meshes[i].b_user = b_user;
+    plan.h_meshes[i].x_user = x_user;
+    BState &st = plan.h_st[i];
+    std::memset(&st, 0, sizeof(st));
+    const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
+    st.tol2 = tol * tol;
+    st.inner_tol2 = itol * itol;
+    st.max_iters = o.max_iters > 0 ? o.max_iters : 100000;
+    st.max_outer = o.max_outer > 0 ? o.max_outer : 40;
+    st.phase = kPhPrepare;
 }
 
-int batch_begin(BatchPlan &plan, const double *const *b_user, double *const *x_user, double tol, double inner_tol,
-                long long max_iters, cudaStream_t s) {
+static unsigned int *plan_bar(const BatchPlan &plan) {
+    return (unsigned int *)((char *)plan.d_st + plan.meshes.size() * sizeof(BState) + 1024);
+}
+
+int batch_upload_states(BatchPlan &plan, cudaStream_t s) {
     const int n = (int)plan.meshes.size();
-    for (int i = 0; i < n; ++i) {
-        plan.h_meshes[i].b_user = b_user[i];
-        plan.h_meshes[i].x_user = x_user[i];
-        BState &st = plan.h_st[i];
-        std::memset(&st, 0, sizeof(st));
-        st.tol2 = tol * tol;
-        st.inner_tol2 = inner_tol * inner_tol;
-        st.max_iters = max_iters;
-        st.active = 1;
-    }
+    // meshes carried over mid inner solve are counted as active
+    int act = 0;
+    for (int i = 0; i < n; ++i) act += plan.h_st[i].phase == kPhInner && !plan.h_st[i].done;
+    plan.h_active = act;
+    int *active = (int *)(plan_bar(plan) + 128);
     cudaError_t e = cudaMemcpyAsync(plan.d_meshes, plan.h_meshes.data(), n * sizeof(BMesh), cudaMemcpyHostToDevice, s);
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(plan.h_meshes[i].st, &plan.h_st[i], sizeof(BState), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_rc(e);
-    k_b_vec<kPrepare><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
-    return cuda_rc(cudaGetLastError());
-}
-
-int batch_read_states(BatchPlan &plan, cudaStream_t s) {
-    const int n = (int)plan.meshes.size();
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(&plan.h_st[i], plan.h_meshes[i].st, sizeof(BState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(plan.d_st, plan.h_st, n * sizeof(BState), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(active, &plan.h_active, sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_rc(e);
 }
 
-int batch_residual(BatchPlan &plan, cudaStream_t s, int *n_active) {
-    const SmemLayout L = max_layout(plan, true);
-    k_b_resid1<<<plan.n_t1, 256, L.total, s>>>(plan.d_meshes, plan.d_t1, L);
-    k_b_resid2<<<plan.n_t2, 256, 0, s>>>(plan.d_meshes, plan.d_t2);
-    int rc = cuda_rc(cudaGetLastError());
-    if (rc != PS_OK) return rc;
-    rc = batch_read_states(plan, s);
-    if (rc != PS_OK) return rc;
-    int act = 0;
-    for (auto &st : plan.h_st) act += st.active;
-    *n_active = act;
-    return PS_OK;
-}
-
-int batch_inner(BatchPlan &plan, int epoch, cudaStream_t s) {
+// Enqueue one epoch on stream s (also used under stream capture).
+static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
     const int n = (int)plan.meshes.size();
-    int act = 0;
-    for (auto &st : plan.h_st) act += st.active;
-    if (act == 0) return PS_OK;
-    k_b_vec<kInnerInit><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
+    unsigned int *bar = plan_bar(plan);
+    int *active = (int *)(bar + 128);
+    k_b_vec<kPrepare><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3, active);
+    k_b_resid1<<<plan.n_t1, 256, plan.L64.total, s>>>(plan.d_meshes, plan.d_t1, plan.L64);
+    k_b_resid2<<<plan.n_t2, 256, 0, s>>>(plan.d_meshes, plan.d_t2);
+    k_b_vec<kInnerInit><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3, active);
     int rc = cuda_rc(cudaGetLastError());
     if (rc != PS_OK) return rc;
-    ps_ctx *ctx = plan.ctx;
-    if (!ctx->d_bar) {
-        void *p = nullptr;
-        if (cudaMalloc(&p, 1024) != cudaSuccess) return PS_ENOMEM;
-        cudaMemset(p, 0, 1024);
-        ctx->d_bar = (unsigned int *)p;
-    }
-    int *d_active = (int *)(ctx->d_bar + 128);
-    rc = cuda_rc(cudaMemcpyAsync(d_active, &act, sizeof(int), cudaMemcpyHostToDevice, s));
-    if (rc != PS_OK) return rc;
-    const SmemLayout L = max_layout(plan, false);
-    int per_sm = 0;
-    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, L.total));
-    if (rc != PS_OK) return rc;
-    if (per_sm < 1) return PS_EINVAL;
-    int grid = ctx->sms * std::min(per_sm, 4);
-    grid = std::max(1, std::min(grid, std::max(plan.n_t1, 1)));
     PcgArgs A;
     A.meshes = plan.d_meshes;
     A.t1 = plan.d_t1;
     A.t2 = plan.d_t2;
     A.n_t1 = plan.n_t1;
     A.n_t2 = plan.n_t2;
-    A.bar = ctx->d_bar;
-    A.active_cnt = d_active;
-    A.err = ctx->d_err;
-    A.max_it = epoch > 0 ? epoch : 256;
-    A.L = L;
-    long long cap_it = 0;
-    for (auto &st : plan.h_st) cap_it = std::max(cap_it, st.max_iters);
-    const long long max_launches = cap_it / A.max_it + 4;
-    for (long long launch = 0;; ++launch) {
-        if (launch >= max_launches) {
-            ps_set_last_error("persistent solver did not finish within its iteration budget");
-            return PS_ETIMEOUT;
+    A.bar = bar;
+    A.active_cnt = active;
+    A.err = plan.ctx->d_err;
+    A.max_it = plan.epoch_iters;
+    A.L = plan.L32;
+    void *args[] = {&A};
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(plan.grid_pcg);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = plan.L32.total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    rc = cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_batch_pcg, args));
+    if (rc != PS_OK) return rc;
+    k_b_vec<kCorrect><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3, active);
+    k_b_vec<kFinish><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3, active);
+    rc = cuda_rc(cudaGetLastError());
+    if (rc != PS_OK) return rc;
+    return cuda_rc(cudaMemcpyAsync(plan.h_st, plan.d_st, n * sizeof(BState), cudaMemcpyDeviceToHost, s));
+}
+
+int batch_epoch(BatchPlan &plan, cudaStream_t s) {
+    if (plan.graph_ok && !plan.graph) {
+        // capture the epoch once per plan; fall back to direct launches if
+        // the runtime refuses to capture any of it
+        if (!plan.cap && cudaStreamCreateWithFlags(&plan.cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            plan.graph_ok = false;
         }
-        void *args[] = {&A};
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof(cfg));
-        cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = L.total;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        rc = cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_batch_pcg, args));
-        if (rc != PS_OK) return rc;
-        rc = cuda_rc(cudaMemcpyAsync(plan.h_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-        if (rc != PS_OK) return rc;
-        rc = cuda_rc(cudaStreamSynchronize(s));
-        if (rc != PS_OK) return rc;
-        int herr = 0;
-        cudaMemcpy(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-        if (herr) {
-            cudaMemset(ctx->d_err, 0, sizeof(int));
-            cudaMemset(ctx->d_bar, 0, 1024);
-            return PS_ETIMEOUT;
+        if (plan.graph_ok) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(plan.cap, cudaStreamCaptureModeThreadLocal);
+            int rc = e == cudaSuccess ? epoch_enqueue(plan, plan.cap) : PS_ECUDA;
+            cudaError_t e2 = cudaStreamEndCapture(plan.cap, &g);
+            if (e == cudaSuccess && rc == PS_OK && e2 == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&plan.graph, g, 0) != cudaSuccess) plan.graph = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+            if (!plan.graph) {
+                cudaGetLastError();
+                plan.graph_ok = false;
+            }
         }
-        if (*plan.h_active <= 0) break;
     }
-    (void)n;
+    int rc;
+    if (plan.graph)
+        rc = cuda_rc(cudaGraphLaunch(plan.graph, s));
+    else
+        rc = epoch_enqueue(plan, s);
+    if (rc != PS_OK) return rc;
+    rc = cuda_rc(cudaStreamSynchronize(s));
+    if (rc != PS_OK) return rc;
+    int herr = 0;
+    cudaMemcpy(&herr, plan.ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (herr) {
+        cudaMemset(plan.ctx->d_err, 0, sizeof(int));
+        cudaMemset(plan_bar(plan), 0, 1024);
+        ps_set_last_error("batch epoch: a bounded device wait timed out");
+        return PS_ETIMEOUT;
+    }
     return PS_OK;
 }
 
-int batch_correct(BatchPlan &plan, cudaStream_t s) {
-    k_b_vec<kCorrect><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
-    return cuda_rc(cudaGetLastError());
+void batch_info(const BatchPlan &plan, int i, ps_solve_info *inf) {
+    const BState &st = plan.h_st[i];
+    std::memset(inf, 0, sizeof(*inf));
+    const double bb = st.bb > 0 ? st.bb : 1.0;
+    inf->converged = st.converged;
+    inf->status = st.converged ? PS_OK : (st.status == kCgBreakdown ? PS_EBREAKDOWN : PS_ENOTCONV);
+    inf->iters_outer = st.outer + 1;
+    inf->iters_inner = st.iters_total;
+    inf->rel_res = std::sqrt(st.rr64 / bb);
+    inf->bnorm = std::sqrt(st.bb);
+    inf->n_free = plan.meshes[i]->prep.n_free;
 }
 
-int batch_finish(BatchPlan &plan, cudaStream_t s) {
-    k_b_vec<kFinish><<<plan.n_t3, 256, 0, s>>>(plan.d_meshes, plan.d_t3);
-    return cuda_rc(cudaGetLastError());
+int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
+                       const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s) {
+    ps_ctx *ctx = meshes[0]->ctx;
+    auto t0 = std::chrono::steady_clock::now();
+    BatchPlan plan;
+    const int epoch = o.graph_iters > 0 ? o.graph_iters * 8 : 256;
+    int rc = batch_plan_build(ctx, meshes, n, epoch, plan);
+    if (rc == PS_OK) {
+        for (int i = 0; i < n; ++i) batch_arm(plan, i, b_dev[i], x_dev[i], o);
+        rc = batch_upload_states(plan, s);
+    }
+    if (rc == PS_OK && o.graph_iters < 0) plan.graph_ok = false;
+    // every epoch advances each unfinished mesh by at least one phase step;
+    // bound the number of epochs by the iteration and outer-step caps
+    long long max_epochs = 8;
+    for (int i = 0; i < n && rc == PS_OK; ++i) {
+        const BState &st = plan.h_st[i];
+        max_epochs = std::max(max_epochs, (long long)st.max_outer * 3 + st.max_iters / plan.epoch_iters + 8);
+    }
+    long long ep = 0;
+    while (rc == PS_OK) {
+        bool all = true;
+        for (int i = 0; i < n; ++i) all = all && plan.h_st[i].phase == kPhDone;
+        if (all) break;
+        if (++ep > max_epochs) {
+            ps_set_last_error("batch solve: epoch budget exhausted");
+            rc = PS_ETIMEOUT;
+            break;
+        }
+        rc = batch_epoch(plan, s);
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int first_err = PS_OK;
+    if (rc == PS_OK) {
+        for (int i = 0; i < n; ++i) {
+            ps_solve_info tmp;
+            batch_info(plan, i, &tmp);
+            tmp.seconds = secs;
+            tmp.kernel_launches = ep * (plan.graph ? 7 : 7);
+            if (infos) infos[i] = tmp;
+            if (tmp.status != PS_OK && first_err == PS_OK) first_err = tmp.status;
+        }
+    }
+    batch_plan_free(plan);
+    return rc != PS_OK ? rc : first_err;
 }
 
 }  // namespace ps
 
 using namespace ps;
-
-namespace ps {
-int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
-                       const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s);
-}
 
 extern "C" int ps_batch_solve(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
                               const ps_solve_opts *opts, ps_solve_info *infos, void *stream) {
@@ -766,73 +870,4 @@ extern "C" int ps_batch_solve(ps_mesh *const *meshes, int n, const double *const
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_rc(e);
     return batch_solve_locked(meshes, n, b_dev, x_dev, o, infos, (cudaStream_t)stream);
-}
-
-int ps::batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
-                           const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s) {
-    ps_ctx *ctx = meshes[0]->ctx;
-    const double tol = o.tol > 0 ? o.tol : 1e-10;
-    const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
-    const long long max_it = o.max_iters > 0 ? o.max_iters : 100000;
-    const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
-    auto t0 = std::chrono::steady_clock::now();
-    BatchPlan plan;
-    int rc = batch_plan_build(ctx, meshes, n, plan);
-    std::vector<int> outer(n, 0);
-    if (rc == PS_OK) rc = batch_begin(plan, b_dev, x_dev, tol, itol, max_it, s);
-    while (rc == PS_OK) {
-        int act = 0;
-        rc = batch_residual(plan, s, &act);
-        if (rc != PS_OK) break;
-        bool changed = false;
-        act = 0;
-        for (int i = 0; i < n; ++i) {
-            BState &st = plan.h_st[i];
-            if (st.finished) continue;
-            if (!st.active || outer[i] >= max_outer || st.iters_total >= max_it || st.status == kCgBreakdown) {
-                st.active = 0;
-                st.finished = 1;
-                changed = true;
-                continue;
-            }
-            ++outer[i];
-            ++act;
-        }
-        if (changed)
-            for (int i = 0; i < n && rc == PS_OK; ++i)
-                rc = cuda_rc(cudaMemcpyAsync(plan.h_meshes[i].st, &plan.h_st[i], sizeof(BState),
-                                             cudaMemcpyHostToDevice, s));
-        if (rc != PS_OK || act == 0) break;
-        rc = batch_inner(plan, o.graph_iters > 0 ? o.graph_iters * 8 : 256, s);
-        if (rc != PS_OK) break;
-        rc = batch_correct(plan, s);
-    }
-    if (rc == PS_OK) rc = batch_finish(plan, s);
-    if (rc == PS_OK) rc = batch_read_states(plan, s);
-    int first_err = PS_OK;
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (rc == PS_OK) {
-        for (int i = 0; i < n; ++i) {
-            const BState &st = plan.h_st[i];
-            const double bb = st.bb > 0 ? st.bb : 1.0;
-            const double rel = std::sqrt(st.rr64 / bb);
-            const bool conv = st.rr64 <= st.tol2 * bb;
-            int status = conv ? PS_OK : (st.status == kCgBreakdown ? PS_EBREAKDOWN : PS_ENOTCONV);
-            if (infos) {
-                ps_solve_info &inf = infos[i];
-                std::memset(&inf, 0, sizeof(inf));
-                inf.status = status;
-                inf.converged = conv;
-                inf.iters_outer = outer[i] + 1;
-                inf.iters_inner = st.iters_total;
-                inf.rel_res = rel;
-                inf.bnorm = std::sqrt(st.bb);
-                inf.n_free = meshes[i]->prep.n_free;
-                inf.seconds = secs;
-            }
-            if (status != PS_OK && first_err == PS_OK) first_err = status;
-        }
-    }
-    batch_plan_free(plan);
-    return rc != PS_OK ? rc : first_err;
 }

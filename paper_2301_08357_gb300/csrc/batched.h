@@ -17,8 +17,21 @@
 
 namespace ps {
 
-constexpr int kSegLen = 2048;   // shared nodes per phase-2 task
+constexpr int kSegLen = 256;    // shared nodes per phase-2 task (one per thread)
 constexpr int kVecLen = 8192;   // nodes per node-range task
+
+// Per-mesh phase of a batched solve; every kernel of an epoch acts only on the
+// meshes in its phase, and the last block to finish a mesh's part advances it.
+enum BPhase : int {
+    kPhIdle = 0,       // not part of the current work
+    kPhPrepare = 1,    // copy b, x0 from the caller's numbering; ||b||^2
+    kPhResid = 2,      // FP64 true residual, convergence / caps decision
+    kPhInnerInit = 3,  // r32 = r64 / ||r64||, inner vectors zeroed
+    kPhInner = 4,      // FP32 one-reduction PCG in the persistent kernel
+    kPhCorrect = 5,    // x64 += d32 * ||r64||
+    kPhOutput = 6,     // x back to the caller's numbering
+    kPhDone = 7
+};
 
 struct BState {
     // inner FP32 solve (one-reduction PCG)
@@ -26,16 +39,16 @@ struct BState {
     // outer FP64 defect correction
     double rr64, bb, scale, tol2;
     long long iters, max_iters, iters_total;
-    int first, done, status, active;   // active: this mesh runs an inner solve in this outer step
-    int finished;                      // set by the host: the mesh's solve is over
-    unsigned int cnt2, cnt_r, cnt_v;
+    int first, done, status, phase;
+    int outer, max_outer, converged, pad0;
+    unsigned int cnt2, cnt_r, cnt_v, pad1;
 };
 
 struct BMesh {
     MeshDev d;
     float *x, *r, *p, *s, *w;      // FP32 inner vectors
     float *part;                   // shared-node partial sums (FP32)
-    double *dots;                  // [(n_chunks + n_segs) * 3]
+    float2 *dots;                  // [(n_chunks + n_segs) * 3] double-float partials
     double *x64, *b64, *r64;
     double *part64;                // shared-node partial sums (FP64)
     double *dots64;                // [n_chunks + n_segs]
@@ -47,7 +60,9 @@ struct BMesh {
     BState *st;
 };
 
-// Host-side batch plan (device arrays of meshes and task lists).
+
+// Host-side batch plan: device arrays of meshes and task lists, the per-mesh
+// states (device + pinned host mirror) and the captured epoch graph.
 struct BatchPlan {
     ps_ctx *ctx = nullptr;
     std::vector<ps_mesh *> meshes;
@@ -55,36 +70,41 @@ struct BatchPlan {
     BMesh *d_meshes = nullptr;
     int2 *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr;
     int n_t1 = 0, n_t2 = 0, n_t3 = 0;
-    BState *d_st = nullptr;
-    std::vector<BState> h_st;
+    BState *d_st = nullptr;        // [n] contiguous device states
+    BState *h_st = nullptr;        // [n] pinned host mirror (written by the epoch)
     std::vector<BMesh> h_meshes;
-    uint32_t smem32 = 0, smem64 = 0;
+    SmemLayout L32, L64;
     int grid_pcg = 0;
-    int *h_active = nullptr;       // pinned: active-mesh count read back per launch
+    int epoch_iters = 256;
+    int h_active = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_ok = true;
 };
 
 // Per-mesh batch workspace (extra FP32 vectors beyond ps_mesh::ws).
 struct BatchMeshWs {
     std::vector<DevAlloc> allocs;
     float *s32 = nullptr, *w32 = nullptr;
-    double *dots = nullptr, *dots64 = nullptr, *vdots = nullptr;
-    BState *st = nullptr;
+    float2 *dots = nullptr;
+    double *dots64 = nullptr, *vdots = nullptr;
     int n_segs = 0, n_vt = 0;
 };
 
-int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, BatchPlan &plan);
+// Build the plan for `n` distinct meshes of one context (workspaces allocated
+// on first use); states start in kPhIdle.
+int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, BatchPlan &plan);
 void batch_plan_free(BatchPlan &plan);
-// Set the per-call user vectors and options; resets every mesh's state.
-int batch_begin(BatchPlan &plan, const double *const *b_user, double *const *x_user, double tol, double inner_tol,
-                long long max_iters, cudaStream_t s);
-// One outer step for all meshes not yet finished: FP64 residual; returns the
-// number of meshes that still need an inner solve (after applying max_outer).
-int batch_residual(BatchPlan &plan, cudaStream_t s, int *n_active);
-// Inner FP32 solves of the active meshes, at most `epoch` iterations per
-// persistent launch, until all of them finish.
-int batch_inner(BatchPlan &plan, int epoch, cudaStream_t s);
-int batch_correct(BatchPlan &plan, cudaStream_t s);
-int batch_finish(BatchPlan &plan, cudaStream_t s);
-int batch_read_states(BatchPlan &plan, cudaStream_t s);
+// Start a solve of mesh i: caller-numbering device vectors b (read) and x
+// (first guess in, solution out), options; state -> kPhPrepare.  Takes effect
+// at the next batch_upload_states.
+void batch_arm(BatchPlan &plan, int i, const double *b_user, double *x_user, const ps_solve_opts &o);
+int batch_upload_states(BatchPlan &plan, cudaStream_t s);
+// One epoch: prepare / residual / inner-init / persistent PCG (<= epoch_iters
+// iterations) / correct / output for every mesh in the matching phase, then
+// the states are copied to plan.h_st.  Synchronises the stream.
+int batch_epoch(BatchPlan &plan, cudaStream_t s);
+// Fill a solve info from a finished mesh's state.
+void batch_info(const BatchPlan &plan, int i, ps_solve_info *info);
 
 }  // namespace ps

@@ -56,6 +56,7 @@ int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 // batched.cu
 int batched_set_attrs();
 void batched_release_mesh(ps_mesh *m);
+int64_t batch_ws_bytes(const ps_mesh *m);
 int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev, double *const *x_dev,
                        const ps_solve_opts &o, ps_solve_info *infos, cudaStream_t s);
 

@@ -379,6 +379,7 @@ extern "C" int ps_mesh_get_stats(const ps_mesh *m, ps_mesh_stats *o) {
     o->device_bytes = b;
     o->max_chunk_elems = p.max_elem;
     o->max_chunk_nodes = p.max_loc;
+    o->solve_bytes = batch_ws_bytes(m);
     return PS_OK;
 }
 
@@ -880,6 +881,7 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
         SmemLayout l64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
         stats->reserved[0] = pm.n_patches;
         stats->reserved[1] = pm.inc_total;
+        stats->reserved[2] = pm.loc_total;
         stats->device_bytes = l64.total;  // shared memory per block of the FP64 pass
     }
     return PS_OK;

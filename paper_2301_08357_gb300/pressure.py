@@ -56,7 +56,7 @@ class ps_solve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("iters_outer", C.c_int64),
                 ("iters_inner", C.c_int64), ("rel_res", C.c_double), ("bnorm", C.c_double),
                 ("n_free", C.c_int64), ("seconds", C.c_double), ("kernel_launches", C.c_int64),
-                ("reserved", C.c_double * 3)]
+                ("queue_seconds", C.c_double), ("reserved", C.c_double * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -66,7 +66,7 @@ class ps_mesh_stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_free", C.c_int64), ("dim", C.c_int32),
                 ("n_chunks", C.c_int32), ("n_shared", C.c_int64), ("chunk_node_refs", C.c_int64),
                 ("device_bytes", C.c_int64), ("max_chunk_elems", C.c_int32), ("max_chunk_nodes", C.c_int32),
-                ("reserved", C.c_int64 * 4)]
+                ("solve_bytes", C.c_int64), ("reserved", C.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
