@@ -50,6 +50,14 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
+                         "c4 = 256-mesh batch; c5 = served Poisson stream")
+    ap.add_argument("--meshes", type=int, default=256, help="c4: meshes in the batch")
+    ap.add_argument("--cases", type=int, default=64, help="c5: simulated cases")
+    ap.add_argument("--case-steps", type=int, default=20, help="c5: time steps per case")
+    ap.add_argument("--rates", default="0.5,1,2", help="c5: arrival rates as multiples of saturation")
+    ap.add_argument("--size-scale", type=float, default=1.0, help="c4/c5: scale the mesh-size range")
     return ap.parse_args()
 
 
@@ -265,7 +273,7 @@ def run_ours(args):
     which = P.PS_KERNEL_CG_F32 if mode == P.PS_MODE_MIXED else P.PS_KERNEL_CG_F64
     kern_ms = P.ps_profile_kernel(m, which, reps=50, stream=stream)
     kern_other = {name: P.ps_profile_kernel(m, k, reps=50, stream=stream)
-                  for name, k in (("shared_f32", P.PS_KERNEL_SHARED_F32), ("update_f32", P.PS_KERNEL_UPDATE_F32),
+                  for name, k in (("update_f32", P.PS_KERNEL_UPDATE_F32), ("apply_f32", P.PS_KERNEL_APPLY_F32),
                                   ("resid_f64", P.PS_KERNEL_RESID_F64))}
     E, N = stats.n_elems, stats.n_nodes
     if mode == P.PS_MODE_MIXED:
@@ -312,10 +320,228 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _pctl(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_single(args, which):
+    """c1 (2D 64^2, FP64 plain PCG) and c3 (160^3 stiff, mixed, warm start)."""
+    import contextlib
+    import torch
+    from __graft_entry__ import build
+    with contextlib.redirect_stdout(sys.stderr):
+        build()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_c1() if which == "c1" else S.make_c3()
+    mode = P.PS_MODE_FP64 if (which == "c1" or args.mode == "fp64") else P.PS_MODE_MIXED
+    ctx = P.ps_ctx_create(0)
+    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk)
+    P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+    stream = torch.cuda.current_stream()
+    if which == "c3":
+        # b = A xstar with the library's FP64 operator (an input of the timed
+        # solve, not a parity value); x0 = xstar (1 + 0.01 xi)
+        xs = torch.as_tensor(case.extra["xstar"], device="cuda")
+        b = torch.empty_like(xs)
+        P.ps_pressure_apply(m, xs, b, P.PS_F64, stream)
+        x0 = torch.as_tensor(case.x0, device="cuda")
+    else:
+        b = torch.as_tensor(case.b, device="cuda")
+        x0 = torch.zeros_like(b)
+    opts = P.make_opts(mode=mode, tol=1e-10)
+    x = x0.clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        x.copy_(x0)
+        P.ps_pressure_solve(m, b, x, opts, stream)
+    times, iters, infos = [], 0, None
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        x.copy_(x0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = P.ps_pressure_solve(m, b, x, opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters += info.iters_inner + info.iters_outer
+        infos = info
+    err = None
+    if which == "c3":
+        xs_h = case.extra["xstar"]
+        err = float(np.linalg.norm(x.cpu().numpy() - xs_h) / np.linalg.norm(xs_h))
+    tot = float(np.sum(times))
+    out = {"metric": METRIC, "value": case.n_free * iters / (tot / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if mode == P.PS_MODE_FP64 else "f32+f64", "data": "synthetic",
+           "config": {"workload": case.name, "n_free": case.n_free, "n_elems": case.n_elems,
+                      "mode": "fp64" if mode == P.PS_MODE_FP64 else "mixed",
+                      "iters_per_solve": infos.iters_inner + infos.iters_outer, "outer_per_solve": infos.iters_outer,
+                      "rel_res": infos.rel_res, "rel_err_vs_xstar": err,
+                      "l2": "flushed between steps (256 MB write)"},
+           "solves_per_s": 1e3 * args.steps / tot, "p50_ms": _pctl(times, 50), "p99_ms": _pctl(times, 99)}
+    print(json.dumps(out))
+    P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+
+
+def run_batch(args):
+    """c4: 256 independent meshes (half 2D, half 3D, 2k-200k nodes) in one batched solve."""
+    import contextlib
+    import torch
+    from __graft_entry__ import build
+    with contextlib.redirect_stdout(sys.stderr):
+        build()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    ctx = P.ps_ctx_create(0)
+    meshes, bs, xs, n_free = [], [], [], []
+    t0 = time.perf_counter()
+    for i in range(args.meshes):
+        c = S.make_batch_case(i, lo=2e3 * args.size_scale, hi=2e5 * args.size_scale)
+        m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet)
+        P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
+        meshes.append(m)
+        bs.append(torch.as_tensor(c.b, device="cuda"))
+        xs.append(torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda"))
+        n_free.append(c.n_free)
+    setup_s = time.perf_counter() - t0
+    opts = P.make_opts(tol=1e-10)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        for x in xs:
+            x.zero_()
+        P.ps_batch_solve(meshes, bs, xs, opts, stream)
+    times, dof_iters = [], 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, infos = P.ps_batch_solve(meshes, bs, xs, opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        assert st == P.PS_OK, st
+        dof_iters += sum(nf * (inf.iters_inner + inf.iters_outer) for nf, inf in zip(n_free, infos))
+    tot = float(np.sum(times))
+    out = {"metric": METRIC, "value": dof_iters / (tot / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "c4_batch_%d_meshes" % args.meshes, "n_free_total": int(sum(n_free)),
+                      "max_rel_res": max(inf.rel_res for inf in infos),
+                      "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
+                      "setup_s": setup_s, "l2": "flushed between steps (256 MB write)"},
+           "solves_per_s": 1e3 * args.meshes * args.steps / tot}
+    print(json.dumps(out))
+    for m in meshes:
+        P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+
+
+def run_served(args):
+    """c5: Poisson arrivals of time-step solves from simulated cases."""
+    import contextlib
+    import threading
+    import torch
+    from __graft_entry__ import build
+    with contextlib.redirect_stdout(sys.stderr):
+        build()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    ctx = P.ps_ctx_create(0)
+    cases, meshes = [], []
+    for c in range(args.cases):
+        cs = S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
+        m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet)
+        P.ps_coeff_set(m, cs.alpha, cs.beta, cs.dt2)
+        cases.append(cs)
+        meshes.append(m)
+    nodes_total = sum(c.n_nodes for c in cases)
+
+    def one_run(rate):
+        """rate None = closed loop (each case submits its next step when the last completes)."""
+        srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32)
+        ids = [P.ps_server_add_case(srv, m) for m in meshes]
+        state = [(c.beta.copy(), c.b.copy()) for c in cases]
+        lat, qwait, done_iters = [], [], 0
+        rng = np.random.default_rng(7)
+        t_start = time.perf_counter()
+        order = [(k, ci) for k in range(args.case_steps) for ci in range(len(cases))]
+        pending = {}
+        if rate is None:
+            for ci in range(len(cases)):
+                pending[P.ps_solve_submit(srv, ids[ci], state[ci][1])] = (ci, 0)
+            while pending:
+                t = next(iter(pending))
+                ci, k = pending.pop(t)
+                st, info = P.ps_solve_wait(srv, t, 600.0)
+                P.ps_server_release(srv, t)
+                lat.append(info.seconds)
+                qwait.append(info.queue_seconds)
+                done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
+                if k + 1 < args.case_steps:
+                    beta, b = S.served_step_drift(cases[ci], *state[ci])
+                    state[ci] = (beta, b)
+                    pending[P.ps_solve_submit(srv, ids[ci], b, beta)] = (ci, k + 1)
+        else:
+            next_t = time.perf_counter()
+            for k, ci in order:
+                next_t += rng.exponential(1.0 / rate)
+                while time.perf_counter() < next_t:
+                    time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
+                if k > 0:
+                    state[ci] = S.served_step_drift(cases[ci], *state[ci])
+                beta = state[ci][0] if k > 0 else None
+                pending[P.ps_solve_submit(srv, ids[ci], state[ci][1], beta)] = (ci, k)
+            for t, (ci, k) in list(pending.items()):
+                st, info = P.ps_solve_wait(srv, t, 600.0)
+                P.ps_server_release(srv, t)
+                lat.append(info.seconds)
+                qwait.append(info.queue_seconds)
+                done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
+        wall = time.perf_counter() - t_start
+        stats = P.ps_server_get_stats(srv).as_dict()
+        P.ps_server_destroy(srv)
+        n = len(lat)
+        return {"rate": rate, "solves": n, "wall_s": wall, "solves_per_s": n / wall,
+                "dof_iters_per_s": done_iters / wall, "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99),
+                "queue_p50_ms": 1e3 * _pctl(qwait, 50), "peak_in_flight": stats["peak_in_flight"],
+                "epochs": stats["epochs"]}
+
+    sat = one_run(None)
+    runs = [sat]
+    for f in [float(v) for v in args.rates.split(",") if v]:
+        runs.append(dict(one_run(f * sat["solves_per_s"]), rate_x_sat=f))
+    out = {"metric": METRIC, "value": sat["dof_iters_per_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.case_steps, "warmup": 0, "ms_per_step": 1e3 / sat["solves_per_s"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": "c5_served_%d_cases_x_%d_steps" % (args.cases, args.case_steps),
+                      "nodes_total": nodes_total},
+           "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+           "runs": runs}
+    print(json.dumps(out))
+    for m in meshes:
+        P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("c1", "c3"):
+        run_single(args, args.workload)
+    elif args.workload == "c4":
+        run_batch(args)
+    elif args.workload == "c5":
+        run_served(args)
     else:
         run_ours(args)
 

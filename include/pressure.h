@@ -93,9 +93,11 @@ typedef struct {
     int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
     int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
                              /* negative = launch kernels directly, no graph)      */
-    int32_t engine;          /* PS_ENGINE_AUTO: mixed mode runs the persistent      */
-                             /* one-reduction PCG, FP64 mode the multi-kernel PCG;  */
-                             /* PS_ENGINE_GRAPH forces the multi-kernel (graph) PCG */
+    int32_t engine;          /* single solves: PS_ENGINE_AUTO / PS_ENGINE_GRAPH run */
+                             /* the multi-kernel PCG captured in CUDA graphs;       */
+                             /* PS_ENGINE_PERSISTENT (mixed mode) runs the batched  */
+                             /* persistent engine on a batch of one, which gives    */
+                             /* bitwise the result the mesh gets in any batch       */
     int32_t reserved[5];
 } ps_solve_opts;
 
@@ -317,15 +319,16 @@ int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_e
  * average device time per launch in *avg_ms.  The workspace vectors are used
  * as inputs as they stand (run a solve first for meaningful data); results
  * are discarded.  which:
- *   PS_KERNEL_CG_F32     FP32 CG operator pass, chunk kernel (apply + p update + p.q)
- *   PS_KERNEL_SHARED_F32 FP32 CG shared-node reduction kernel
- *   PS_KERNEL_UPDATE_F32 FP32 CG vector update kernel
+ *   PS_KERNEL_CG_F32     FP32 CG operator kernel: chunk staging, p = D^-1 r + beta p,
+ *                        q = A p, chunk shares of p.Ap (the solver's dominant kernel)
+ *   PS_KERNEL_UPDATE_F32 FP32 CG update kernel: shared-node rows, x and r update, rz, rr
+ *   PS_KERNEL_APPLY_F32  FP32 operator apply alone (chunk kernel + shared-node sums)
  *   PS_KERNEL_RESID_F64  FP64 true-residual chunk kernel
- *   PS_KERNEL_CG_F64     FP64 CG operator pass, chunk kernel
+ *   PS_KERNEL_CG_F64     FP64 CG operator kernel
  * Errors: PS_EINVAL, PS_ESTATE (coefficients not set). */
 #define PS_KERNEL_CG_F32     0
-#define PS_KERNEL_SHARED_F32 1
-#define PS_KERNEL_UPDATE_F32 2
+#define PS_KERNEL_UPDATE_F32 1
+#define PS_KERNEL_APPLY_F32  2
 #define PS_KERNEL_RESID_F64  3
 #define PS_KERNEL_CG_F64     4
 int ps_profile_kernel(ps_mesh *mesh, int which, int reps, void *stream, double *avg_ms);

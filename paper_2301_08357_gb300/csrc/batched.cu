@@ -140,7 +140,7 @@ __device__ void chunk_cg1(const BMesh &M, int c, const ChunkSmem<float> &S, uint
             acc[1].add_prod(wv, u);
             acc[2].add_prod(r, r);
         } else {
-            M.part[cd.sh_off + (l - n_int)] = wv;
+            M.part[m.sh_dest[cd.sh_off + (l - n_int)]] = wv;
         }
     }
 }
@@ -218,7 +218,7 @@ __device__ void seg_cg1(const BMesh &M, int seg, float alpha, float beta, double
         const int64_t g = m.n_int + sidx;
         float wv = 0.f;
         const int kb = m.shr_ptr[sidx], ke = m.shr_ptr[sidx + 1];
-        for (int k = kb; k < ke; ++k) wv += __ldcg(M.part + m.shr_slot[k]);
+        for (int k = kb; k < ke; ++k) wv += __ldcg(M.part + k);
         NodeUpd o = node_update(__ldcg(M.r + g), __ldcg(M.w + g), __ldcg(M.s + g), m.dinv32[g], __ldcg(M.p + g),
                                 __ldcg(M.x + g), alpha, beta);
         if (m.dirichlet[g]) {
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int
     for (int64_t sidx = s0 + threadIdx.x; sidx < s1; sidx += blockDim.x) {
         const int64_t g = m.n_int + sidx;
         double sum = 0.0;
-        for (int k = m.shr_ptr[sidx]; k < m.shr_ptr[sidx + 1]; ++k) sum += M.part64[m.shr_slot[k]];
+        for (int k = m.shr_ptr[sidx]; k < m.shr_ptr[sidx + 1]; ++k) sum += M.part64[k];
         const double rv = m.dirichlet[g] ? 0.0 : M.b64[g] - sum;
         M.r64[g] = rv;
         acc.add_prod(rv, rv);

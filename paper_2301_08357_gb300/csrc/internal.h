@@ -35,6 +35,7 @@ struct Workspace {
     float *part32 = nullptr;
     double *part64 = nullptr;
     double *dot1 = nullptr, *dot2 = nullptr;
+    double *pq2 = nullptr, *z3 = nullptr;   // two-kernel CG partials
     CgState *st = nullptr;
     CgState *h_st = nullptr;
     float *one32 = nullptr;
@@ -81,7 +82,9 @@ struct ps_mesh {
     std::vector<ps::DevAlloc> allocs;
     int32_t *d_loc_node = nullptr, *d_elem_src = nullptr;
     int32_t *d_old_of_new = nullptr, *d_new_of_old = nullptr;
-    int grid2 = 1, grid3 = 1;
+    int grid2 = 1, grid3 = 1, g3c = 1;
+    ps::SmemLayout pipe_L0, pipe_L1;   // two-stage layout of the pipelined CG kernel
+    int pipe_grid = 0;                 // its persistent grid (0 = not used)
     bool coeff_ok = false, alpha_set = false;
     double dt2 = 0.0;
     ps::Workspace ws;

@@ -8,8 +8,9 @@
 // are numbered after all interior nodes.  A chunk computes its element
 // contributions in shared memory, sums them per local node through a fixed
 // incidence list (deterministic, no atomics), writes its interior rows
-// directly and writes one partial sum per shared local node; a second pass
-// adds the partial sums of every shared node in a fixed order.
+// directly and writes one partial sum per shared local node, into a
+// shared-node-major array (the partials of one shared node are contiguous); a
+// second pass adds the partial sums of every shared node in chunk order.
 //
 // Every per-chunk segment starts on a 16-byte boundary so that it can be moved
 // into shared memory with one cp.async.bulk copy.

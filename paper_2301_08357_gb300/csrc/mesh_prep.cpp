@@ -265,9 +265,9 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     // ---- chunk sizes
     int ec = opt.chunk_elems;
     if (ec <= 0) {
-        // aim for >= 4 chunks per SM of a 152-SM part, 96..3072 elements each
+        // aim for >= 4 chunks per SM of a 152-SM part, 96..1536 elements each
         int64_t t = n_elems / 608;
-        t = std::max<int64_t>(96, std::min<int64_t>(3072, t));
+        t = std::max<int64_t>(96, std::min<int64_t>(1536, t));
         ec = (int)round_up(t, 32);
     }
     ec = std::max(1, std::min(ec, kMaxChunkPatches));
@@ -472,6 +472,9 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
             }
         }
     }
+    // partial sums are stored shared-node-major: chunk slot -> its position
+    m.sh_dest.assign(m.sh_total, -1);
+    for (size_t k = 0; k < m.shr_slot.size(); ++k) m.sh_dest[m.shr_slot[k]] = (int32_t)k;
     return "";
 }
 
@@ -541,6 +544,7 @@ std::string validate_prep(const PrepMesh &m, const int32_t *conn) {
         for (int32_t k = m.shr_ptr[s]; k < m.shr_ptr[s + 1]; ++k) {
             int32_t slot = m.shr_slot[k];
             if (m.sh_ids[slot] != m.n_int + s) return "partial slot maps to wrong node";
+            if (m.sh_dest[slot] != k) return "partial destination is not the inverse slot map";
             slot_hits[slot]++;
         }
     for (int64_t k = 0; k < m.sh_total; ++k)

@@ -40,7 +40,8 @@ struct PrepMesh {
     std::vector<int32_t> loc_node;                 // [loc_total] new id of each local node
     std::vector<double> loc_rel;                   // [loc_total * dim] coords - chunk origin
     std::vector<int32_t> shr_ptr;                  // [n_shared + 1]
-    std::vector<int32_t> shr_slot;                 // partial slots of each shared node
+    std::vector<int32_t> shr_slot;                 // chunk-major slot of each shared-node-major partial
+    std::vector<int32_t> sh_dest;                  // [sh_total] shared-node-major position of a chunk slot, -1 pad
 };
 
 // Returns "" on success, else an error message (bad input).

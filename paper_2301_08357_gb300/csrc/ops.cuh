@@ -32,7 +32,7 @@ struct MeshDev {
     const ChunkDesc *chunks;
     const uint16_t *pids;    // [patch_total * kPatchIds]
     const uint16_t *incp, *inc;
-    const int32_t *sh_ids, *shr_ptr, *shr_slot;
+    const int32_t *sh_ids, *shr_ptr, *sh_dest;
     const NodeF *node32;
     const NodeD *node64;
     const float *bdt2_32;
@@ -241,7 +241,7 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
                 const_cast<float *>(m.dinv32)[g] = (float)dv;
             }
         } else {
-            a.partial[cd.sh_off + (l - n_int)] = s;
+            a.partial[m.sh_dest[cd.sh_off + (l - n_int)]] = s;
         }
     }
     return dot;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_f
         const int64_t g = m.n_int + s;
         T sum = T(0);
         const int kb = m.shr_ptr[s], ke = m.shr_ptr[s + 1];
-        for (int k = kb; k < ke; ++k) sum += a.partial[m.shr_slot[k]];
+        for (int k = kb; k < ke; ++k) sum += a.partial[k];
         const bool dir = m.dirichlet[g] != 0;
         if (MODE == kApply) {
             a.y[g] = sum;

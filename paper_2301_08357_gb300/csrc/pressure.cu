@@ -20,6 +20,7 @@
 
 #include "../../include/pressure.h"
 #include "internal.h"
+#include "cg2.cuh"
 
 using namespace ps;
 
@@ -86,6 +87,37 @@ SmemLayout make_layout(int esz, int nsz, int max_loc, int max_patch, int max_inc
     return L;
 }
 
+// Two-stage layout for the pipelined CG kernel: static chunk data twice
+// (node records, patch records, incidence pointers / lists, shared-node ids,
+// mbarrier), one copy of the node values and element contributions.
+void make_layout2(int esz, int nsz, int max_loc, int max_patch, int max_inc, int max_sh, SmemLayout &L0,
+                  SmemLayout &L1) {
+    const uint64_t ppad = (uint64_t)round_up(max_patch, kPatchPad);
+    const uint64_t b_node = align128((uint64_t)max_loc * nsz), b_pids = align128(ppad * kPatchIds * 2),
+                   b_incp = align128((uint64_t)round_up(max_loc + 1, kIncpPad) * 2),
+                   b_inc = align128((uint64_t)round_up(max_inc > 0 ? max_inc : 1, kIncPad) * 2),
+                   b_shid = align128((uint64_t)round_up(max_sh > 0 ? max_sh : 1, kShPad) * 4);
+    uint64_t off = 0;
+    for (SmemLayout *L : {&L0, &L1}) {
+        L->node = (uint32_t)off;  off += b_node;
+        L->pids = (uint32_t)off;  off += b_pids;
+        L->incp = (uint32_t)off;  off += b_incp;
+        L->inc = (uint32_t)off;   off += b_inc;
+        L->shid = (uint32_t)off;  off += b_shid;
+        L->bar = (uint32_t)off;   off += 128;
+    }
+    const uint32_t val = (uint32_t)off;     off += align128((uint64_t)max_loc * esz);
+    const uint32_t contrib = (uint32_t)off; off += align128(ppad * kPatchSlots * esz);
+    const uint32_t red = (uint32_t)off;     off += 34 * 8;
+    for (SmemLayout *L : {&L0, &L1}) {
+        L->val = val;
+        L->aux = val;
+        L->contrib = contrib;
+        L->red = red;
+        L->total = (uint32_t)off;
+    }
+}
+
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return PS_OK;
     return e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA;
@@ -115,6 +147,20 @@ extern "C" const char *ps_last_error(void) { return g_last_error.c_str(); }
 // ---------------------------------------------------------------- kernels setup
 namespace ps {
 
+// Largest dynamic shared memory next to the kernel's static shared memory.
+template <typename F>
+static cudaError_t set_max_dyn_smem(F *func) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void *)func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 static int set_smem_attrs() {
     const int lim = 227 * 1024;
     CK(cudaFuncSetAttribute(k_chunks<2, float, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -129,6 +175,12 @@ static int set_smem_attrs() {
     CK(cudaFuncSetAttribute(k_chunks<3, double, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     CK(cudaFuncSetAttribute(k_chunks<2, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     CK(cudaFuncSetAttribute(k_chunks<3, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(set_max_dyn_smem(k_cg2_chunks<2, float>));
+    CK(set_max_dyn_smem(k_cg2_chunks<3, float>));
+    CK(set_max_dyn_smem(k_cg2_chunks<2, double>));
+    CK(set_max_dyn_smem(k_cg2_chunks<3, double>));
+    CK(set_max_dyn_smem(k_cg2_chunks_pipe<2>));
+    CK(set_max_dyn_smem(k_cg2_chunks_pipe<3>));
     return batched_set_attrs();
 }
 
@@ -243,8 +295,8 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     d.sh_ids = i32;
     RC(upload(c, m, &i32, pm.shr_ptr.data(), pm.shr_ptr.size() * 4));
     d.shr_ptr = i32;
-    RC(upload(c, m, &i32, pm.shr_slot.data(), pm.shr_slot.size() * 4));
-    d.shr_slot = i32;
+    RC(upload(c, m, &i32, pm.sh_dest.data(), pm.sh_dest.size() * 4));
+    d.sh_dest = i32;
     RC(upload(c, m, &m->d_loc_node, pm.loc_node.data(), pm.loc_node.size() * 4));
     RC(upload(c, m, &m->d_elem_src, pm.elem_src.data(), pm.elem_src.size() * 4));
     RC(upload(c, m, &m->d_old_of_new, pm.old_of_new.data(), pm.old_of_new.size() * 4));
@@ -298,6 +350,21 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     }
     m->grid2 = grid_for(pm.n_shared, c->sms);
     m->grid3 = grid_for(d.n_pad, c->sms);
+    make_layout2(4, sizeof(NodeF), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh, m->pipe_L0, m->pipe_L1);
+    {
+        int per_sm = 0;
+        cudaError_t oe = pm.dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_chunks_pipe<2>,
+                                                                                      kBlock, m->pipe_L0.total)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_chunks_pipe<3>,
+                                                                                      kBlock, m->pipe_L0.total);
+        if (oe != cudaSuccess || m->pipe_L0.total > 200 * 1024) per_sm = 0;
+        cudaGetLastError();
+        m->pipe_grid = per_sm > 0 ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
+    }
+    {
+        int64_t g = (d.n_pad / 4 + kBlock - 1) / kBlock;
+        m->g3c = (int)std::max<int64_t>(1, std::min<int64_t>(g, 2 * (int64_t)c->sms));
+    }
     return PS_OK;
 }
 
@@ -513,6 +580,8 @@ int ensure_workspace(ps_mesh *m) {
     WA(dot1, double, m->dev.n_chunks + m->grid2 + 8);
     WA(dot2, double, 2 * m->grid3 + 8);
     WA(st, CgState, 1);
+    WA(pq2, double, m->dev.n_chunks + 8);
+    WA(z3, double, 6 * m->g3c + 8);
 #undef WA
     if (rc != PS_OK) {
         dfree_all(c, w.allocs);
@@ -524,52 +593,53 @@ int ensure_workspace(ps_mesh *m) {
     return PS_OK;
 }
 
-static VecArgs<float> cg_args32(ps_mesh *m) {
+template <typename T>
+static Cg2Args<T> cg2_args(ps_mesh *m) {
     Workspace &w = m->ws;
-    VecArgs<float> a;
+    Cg2Args<T> a;
     std::memset(&a, 0, sizeof(a));
-    a.y = w.q32;
-    a.p = w.p32;
-    a.r = w.r32;
-    a.dinv = m->dev.dinv32;
-    a.partial = w.part32;
-    a.dotbuf = w.dot1;
-    a.st = w.st;
-    return a;
-}
-
-static VecArgs<double> cg_args64(ps_mesh *m) {
-    Workspace &w = m->ws;
-    VecArgs<double> a;
-    std::memset(&a, 0, sizeof(a));
-    a.y = w.q64;
-    a.p = w.p64;
-    a.r = w.r64;
-    a.dinv = m->dev.dinv64;
-    a.partial = w.part64;
-    a.dotbuf = w.dot1;
+    if (sizeof(T) == 4) {
+        a.x = (T *)w.x32;
+        a.r = (T *)w.r32;
+        a.p = (T *)w.p32;
+        a.q = (T *)w.q32;
+        a.dinv = (const T *)m->dev.dinv32;
+        a.partial = (T *)w.part32;
+    } else {
+        a.x = (T *)w.x64;
+        a.r = (T *)w.r64;
+        a.p = (T *)w.p64;
+        a.q = (T *)w.q64;
+        a.dinv = (const T *)m->dev.dinv64;
+        a.partial = (T *)w.part64;
+    }
+    a.pq = (typename PartOf<T>::type *)w.pq2;
+    a.z2 = (typename PartOf<T>::type *)w.z3;
+    a.g3 = m->g3c;
     a.st = w.st;
     return a;
 }
 
 // Enqueue `iters` CG iterations (no host sync) of precision T.
 template <typename T>
-static int enqueue_cg_iters(ps_mesh *m, int iters, cudaStream_t s) {
-    Workspace &w = m->ws;
+static int enqueue_cg_iters(ps_mesh *m, int iters, int, cudaStream_t s) {
+    const Cg2Args<T> a = cg2_args<T>(m);
+    const SmemLayout &L = sizeof(T) == 4 ? m->dev.sm32 : m->dev.sm64;
     for (int k = 0; k < iters; ++k) {
-        if (sizeof(T) == 4) {
-            VecArgs<float> a = cg_args32(m);
-            RC((launch_pass<float, kCG>(m, a, s)));
-            k_cg_update<float><<<m->grid3, kBlock, 0, s>>>(m->dev.n_pad, w.x32, w.r32, w.p32, w.q32, m->dev.dinv32,
-                                                           w.st, w.dot2, nullptr);
-            m->launches += 1;
-        } else {
-            VecArgs<double> a = cg_args64(m);
-            RC((launch_pass<double, kCG>(m, a, s)));
-            k_cg_update<double><<<m->grid3, kBlock, 0, s>>>(m->dev.n_pad, w.x64, w.r64, w.p64, w.q64,
-                                                            m->dev.dinv64, w.st, w.dot2, nullptr);
-            m->launches += 1;
-        }
+        if (sizeof(T) == 4 && m->pipe_grid > 0) {
+            const Cg2Args<float> &af = reinterpret_cast<const Cg2Args<float> &>(a);
+            if (m->dev.dim == 2)
+                k_cg2_chunks_pipe<2><<<m->pipe_grid, kBlock, m->pipe_L0.total, s>>>(m->dev, af, m->pipe_L0,
+                                                                                     m->pipe_L1);
+            else
+                k_cg2_chunks_pipe<3><<<m->pipe_grid, kBlock, m->pipe_L0.total, s>>>(m->dev, af, m->pipe_L0,
+                                                                                     m->pipe_L1);
+        } else if (m->dev.dim == 2)
+            k_cg2_chunks<2, T><<<m->dev.n_chunks, kBlock, L.total, s>>>(m->dev, a);
+        else
+            k_cg2_chunks<3, T><<<m->dev.n_chunks, kBlock, L.total, s>>>(m->dev, a);
+        k_cg2_update<T><<<m->g3c, kBlock, 0, s>>>(m->dev, a);
+        m->launches += 2;
         CK(cudaGetLastError());
     }
     return PS_OK;
@@ -582,9 +652,9 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
     Workspace &w = m->ws;
     const int kind = (sizeof(T) == 4 ? 0 : 1) + (jac ? 0 : 2);
     if (gi <= 0) {
-        const int batch = 16;
+        const int batch = 15;
         for (;;) {
-            RC(enqueue_cg_iters<T>(m, batch, s));
+            RC(enqueue_cg_iters<T>(m, batch, 0, s));
             CK(cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (w.h_st->done) return PS_OK;
@@ -597,7 +667,7 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
         const int64_t saved_launches = m->launches;
-        int rc = enqueue_cg_iters<T>(m, gi, w.cap_stream);
+        int rc = enqueue_cg_iters<T>(m, gi, 0, w.cap_stream);
         m->launches = saved_launches;
         cudaError_t e2 = cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, w.cap_stream);
         cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
@@ -613,7 +683,7 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
     }
     for (;;) {
         CK(cudaGraphLaunch(g->exec, s));
-        m->launches += 3 * (int64_t)gi;
+        m->launches += 2 * (int64_t)gi;
         CK(cudaStreamSynchronize(s));
         if (w.h_st->done) return PS_OK;
     }
@@ -711,9 +781,12 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
             ++outer;
             if (rr <= stop_abs2) { status = PS_OK; break; }
             if (used >= max_it || outer > max_restarts) { status = PS_ENOTCONV; break; }
-            k_cg_start<double><<<g3, kBlock, 0, s>>>(np, nullptr, 1.0, w.r64, nullptr, w.p64, m->dev.dinv64, w.st,
-                                                     w.dot2, stop_abs2, 0, max_it - used);
-            m->launches += 1;
+            {
+                Cg2Args<double> a = cg2_args<double>(m);
+                k_cg2_start<double><<<m->g3c, kBlock, 0, s>>>(m->dev, a, nullptr, 1.0, nullptr, stop_abs2, 0,
+                                                              max_it - used);
+                m->launches += 1;
+            }
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
             if ((rc = run_cg_until_done<double>(m, gi, jac, s)) != PS_OK) break;
             RC(read_state(m, s, &h));
@@ -730,9 +803,12 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
             if (rr <= stop_abs2) { status = PS_OK; break; }
             if (used >= max_it || outer > max_outer) { status = PS_ENOTCONV; break; }
             const double scale = 1.0 / std::sqrt(rr);
-            k_cg_start<float><<<g3, kBlock, 0, s>>>(np, w.r64, scale, w.r32, w.x32, w.p32, m->dev.dinv32, w.st,
-                                                    w.dot2, itol * itol, 1, max_it - used);
-            m->launches += 1;
+            {
+                Cg2Args<float> a = cg2_args<float>(m);
+                k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, itol * itol, 1,
+                                                             max_it - used);
+                m->launches += 1;
+            }
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
             if ((rc = run_cg_until_done<float>(m, gi, jac, s)) != PS_OK) break;
             RC(read_state(m, s, &h));
@@ -817,7 +893,7 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
     std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    if (o.mode == PS_MODE_MIXED && o.engine != PS_ENGINE_GRAPH && o.precond != PS_PRECOND_NONE) {
+    if (o.mode == PS_MODE_MIXED && o.engine == PS_ENGINE_PERSISTENT && o.precond != PS_PRECOND_NONE) {
         ps_mesh *one[1] = {m};
         const double *bb[1] = {b};
         double *xx[1] = {x};
@@ -912,20 +988,35 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
     auto one = [&]() {
         switch (which) {
             case 0: {
-                VecArgs<float> a = cg_args32(m);
-                if (d.dim == 2) k_chunks<2, float, kCG><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
-                else k_chunks<3, float, kCG><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                Cg2Args<float> a = cg2_args<float>(m);
+                if (m->pipe_grid > 0) {
+                    if (d.dim == 2)
+                        k_cg2_chunks_pipe<2><<<m->pipe_grid, kBlock, m->pipe_L0.total, s>>>(d, a, m->pipe_L0, m->pipe_L1);
+                    else
+                        k_cg2_chunks_pipe<3><<<m->pipe_grid, kBlock, m->pipe_L0.total, s>>>(d, a, m->pipe_L0, m->pipe_L1);
+                } else if (d.dim == 2) {
+                    k_cg2_chunks<2, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                } else {
+                    k_cg2_chunks<3, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                }
                 break;
             }
             case 1: {
-                VecArgs<float> a = cg_args32(m);
-                k_shared<float, kCG><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
+                Cg2Args<float> a = cg2_args<float>(m);
+                k_cg2_update<float><<<m->g3c, kBlock, 0, s>>>(d, a);
                 break;
             }
-            case 2:
-                k_cg_update<float><<<m->grid3, kBlock, 0, s>>>(d.n_pad, w.x32, w.r32, w.p32, w.q32, d.dinv32, w.st,
-                                                               w.dot2, nullptr);
+            case 2: {
+                VecArgs<float> a;
+                std::memset(&a, 0, sizeof(a));
+                a.x = w.p32;
+                a.y = w.q32;
+                a.partial = w.part32;
+                if (d.dim == 2) k_chunks<2, float, kApply><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                else k_chunks<3, float, kApply><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+                k_shared<float, kApply><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
                 break;
+            }
             case 3: {
                 VecArgs<double> a;
                 std::memset(&a, 0, sizeof(a));
@@ -940,9 +1031,9 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
                 break;
             }
             case 4: {
-                VecArgs<double> a = cg_args64(m);
-                if (d.dim == 2) k_chunks<2, double, kCG><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
-                else k_chunks<3, double, kCG><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                Cg2Args<double> a = cg2_args<double>(m);
+                if (d.dim == 2) k_cg2_chunks<2, double><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+                else k_cg2_chunks<3, double><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
                 break;
             }
         }

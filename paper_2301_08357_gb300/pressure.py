@@ -334,7 +334,7 @@ def ps_server_get_stats(srv):
     return s
 
 
-PS_KERNEL_CG_F32, PS_KERNEL_SHARED_F32, PS_KERNEL_UPDATE_F32, PS_KERNEL_RESID_F64, PS_KERNEL_CG_F64 = 0, 1, 2, 3, 4
+PS_KERNEL_CG_F32, PS_KERNEL_UPDATE_F32, PS_KERNEL_APPLY_F32, PS_KERNEL_RESID_F64, PS_KERNEL_CG_F64 = 0, 1, 2, 3, 4
 
 
 def ps_profile_kernel(mesh, which, reps=20, stream=None):

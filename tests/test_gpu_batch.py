@@ -64,7 +64,7 @@ def test_batch_matches_oracle_and_alone(env):
             assert inf1[0].iters_inner == infos[k].iters_inner
             bd = torch.as_tensor(rhs[k][0], device="cuda")
             xd = torch.as_tensor(rhs[k][1], device="cuda").clone()
-            st2, inf2 = P.ps_pressure_solve(meshes[k], bd, xd, P.make_opts(tol=1e-10))
+            st2, inf2 = P.ps_pressure_solve(meshes[k], bd, xd, P.make_opts(tol=1e-10, engine=P.PS_ENGINE_PERSISTENT))
             assert np.array_equal(xd.cpu().numpy(), xs[k])
         # another batch order gives the same per-mesh results
         order = [5, 2, 7, 0, 6, 1, 4, 3]

@@ -44,15 +44,15 @@ def ctx(P, torch_mod):
 
 
 def gpu_solve(P, torch, m, b, x0, **kw):
-    if "engine" not in kw and kw.get("mode") == "graph":
-        kw["mode"], kw["engine"] = 1, P.PS_ENGINE_GRAPH
+    if "engine" not in kw and kw.get("mode") == "persistent":
+        kw["mode"], kw["engine"] = 1, P.PS_ENGINE_PERSISTENT
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     xd = torch.as_tensor(x0, dtype=torch.float64, device="cuda").clone()
     st, info = P.ps_pressure_solve(m, bd, xd, P.make_opts(**kw))
     return st, info, xd.cpu().numpy()
 
 
-MODES = [(0, "fp64"), (1, "mixed"), ("graph", "mixed_graph")]
+MODES = [(0, "fp64"), (1, "mixed"), ("persistent", "mixed_persistent")]
 SMALL = [
     ("c1_64", lambda: S.make_c1(64), 0),
     ("c1_32_shuffled", lambda: S.shuffle_case(S.make_c1(32)), 41),
