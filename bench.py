@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
+    ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
@@ -66,6 +67,42 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def aggregate(total_ms, work, device=None):
+    """Whole-job numbers over ranks (replicas): the max time and the summed
+    work.  A no-op without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(work)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
+def parse_clocks(lines):
+    """nvidia-smi --query-gpu=<Clocks.Q> --format=csv,noheader,nounits lines ->
+    {sm_mhz (median), sm_max_mhz, reasons (throttle reasons seen active), samples}."""
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = max(mx, float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def workload_name(n):
@@ -112,25 +149,10 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = max(mx, float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        with open(self.path) as f:
+            out = parse_clocks(f.readlines())
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
 
 
 def cpu_baseline(case, seconds, steps=None):
@@ -194,7 +216,8 @@ def run_ours(args):
 
     case = S.make_c2(args.n)
     ctx = P.ps_ctx_create(local)
-    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk)
+    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
+                         pipeline=args.pipeline)
     P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()
@@ -241,15 +264,7 @@ def run_ours(args):
     clk = clocks.stop() if not args.no_clocks else None
     last_info = info
     dof_iters = case.n_free * iters
-    t_max = total_ms
-    tot_dof = dof_iters
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        d = torch.tensor([float(dof_iters)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(d)
-        tot_dof = float(d.item())
+    t_max, tot_dof = aggregate(total_ms, dof_iters, device="cuda")
     value = tot_dof / (t_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers (copies timed)

@@ -80,7 +80,9 @@ typedef int64_t ps_ticket;
 typedef struct {
     int32_t chunk_elems;     /* target elements per chunk (0 = auto by size)       */
     int32_t chunk_nodes_max; /* cap on distinct nodes per chunk (0 = auto)          */
-    int32_t reserved[6];
+    int32_t pipeline;        /* FP32 CG operator kernel: 0 = one block per chunk,  */
+                             /* 1 = persistent blocks with double-buffered staging */
+    int32_t reserved[5];
 } ps_mesh_opts;
 
 typedef struct {

@@ -308,33 +308,57 @@ template <int D, typename T, typename N4, bool DIAG>
 __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const T *__restrict__ s_val,
                                            const uint16_t *__restrict__ rec, const T *__restrict__ bdt2,
                                            T *__restrict__ out) {
-    const int pm = rec[0];
-    const int ia = rec[1];
+    // the 24-byte record as three 8-byte loads: [m, a, b, r0], [r1..r4], [r5, r6, -, -]
+    const ushort4 q0 = reinterpret_cast<const ushort4 *>(rec)[0];
+    const ushort4 q1 = reinterpret_cast<const ushort4 *>(rec)[1];
+    const ushort4 q2 = reinterpret_cast<const ushort4 *>(rec)[2];
+    const int pm = q0.x;
+    const int ring[7] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
+    // beta*dt^2 of the patch's elements: one vector load each, all up front
+    T bd[kPatchMax];
+    if (sizeof(T) == 4) {
+        const float2 *b2 = reinterpret_cast<const float2 *>(bdt2);
+#pragma unroll
+        for (int k = 0; k < kPatchMax / 2; ++k) {
+            const float2 v = __ldg(b2 + k);
+            bd[2 * k] = (T)v.x;
+            bd[2 * k + 1] = (T)v.y;
+        }
+    } else {
+        const double2 *b2 = reinterpret_cast<const double2 *>(bdt2);
+#pragma unroll
+        for (int k = 0; k < kPatchMax / 2; ++k) {
+            const double2 v = __ldg(b2 + k);
+            bd[2 * k] = (T)v.x;
+            bd[2 * k + 1] = (T)v.y;
+        }
+    }
+    const int ia = q0.y;
     const N4 A = s_node[ia];
     const T va = DIAG ? T(0) : s_val[ia];
     const T aa = fabs(A.w);
     T acc_a = T(0), acc_b = T(0);
     if (D == 3) {
-        const int ib = rec[2];
+        const int ib = q0.z;
         const N4 B = s_node[ib];
         const T vb = DIAG ? T(0) : s_val[ib];
         const T ab = fabs(B.w);
         const T e1x = B.x - A.x, e1y = B.y - A.y, e1z = B.z - A.z;
-        int i0 = rec[3];
-        N4 R0 = s_node[i0];
-        T v0 = DIAG ? T(0) : s_val[i0];
+        N4 R0 = s_node[ring[0]];
+        T v0 = DIAG ? T(0) : s_val[ring[0]];
         T d0x = R0.x - A.x, d0y = R0.y - A.y, d0z = R0.z - A.z;
         T w0x = e1y * d0z - e1z * d0y, w0y = e1z * d0x - e1x * d0z, w0z = e1x * d0y - e1y * d0x;
         T acc_c = T(0);
-        for (int j = 0; j < pm; ++j) {
-            const int i1 = rec[4 + j];
-            const N4 R1 = s_node[i1];
-            const T v1 = DIAG ? T(0) : s_val[i1];
+#pragma unroll
+        for (int j = 0; j < kPatchMax; ++j) {
+            if (j >= pm) break;
+            const N4 R1 = s_node[ring[j + 1]];
+            const T v1 = DIAG ? T(0) : s_val[ring[j + 1]];
             const T d1x = R1.x - A.x, d1y = R1.y - A.y, d1z = R1.z - A.z;
             const T w1x = e1y * d1z - e1z * d1y, w1y = e1z * d1x - e1x * d1z, w1z = e1x * d1y - e1y * d1x;
             const T c1x = d0y * d1z - d0z * d1y, c1y = d0z * d1x - d0x * d1z, c1z = d0x * d1y - d0y * d1x;
             const T ad = fabs(e1x * c1x + e1y * c1y + e1z * c1z);
-            const T kc = fdiv_fast(bdt2[j], T(6) * ad);
+            const T kc = fdiv_fast(bd[j], T(6) * ad);
             const T a2 = fabs(R0.w), a3 = fabs(R1.w);
             const T S = (aa + ab) + (a2 + a3);
             const T cm = ad * T(1.0 / 720.0);
@@ -376,20 +400,20 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
         out[0] = acc_a;
         out[1] = acc_b;
     } else {
-        int i0 = rec[3];
-        N4 R0 = s_node[i0];
-        T v0 = DIAG ? T(0) : s_val[i0];
+        N4 R0 = s_node[ring[0]];
+        T v0 = DIAG ? T(0) : s_val[ring[0]];
         T d0x = R0.x - A.x, d0y = R0.y - A.y;
         T acc_c = T(0);
-        for (int j = 0; j < pm; ++j) {
-            const int i1 = rec[4 + j];
-            const N4 R1 = s_node[i1];
-            const T v1 = DIAG ? T(0) : s_val[i1];
+#pragma unroll
+        for (int j = 0; j < kPatchMax; ++j) {
+            if (j >= pm) break;
+            const N4 R1 = s_node[ring[j + 1]];
+            const T v1 = DIAG ? T(0) : s_val[ring[j + 1]];
             const T d1x = R1.x - A.x, d1y = R1.y - A.y;
             // c1 = perp(d1) = (d1y, -d1x), c2 = -perp(d0) = (-d0y, d0x)
             const T c1x = d1y, c1y = -d1x, c2x = -d0y, c2y = d0x;
             const T ad = fabs(d0x * d1y - d0y * d1x);
-            const T kc = fdiv_fast(bdt2[j], T(2) * ad);
+            const T kc = fdiv_fast(bd[j], T(2) * ad);
             const T a1 = fabs(R0.w), a2 = fabs(R1.w);
             const T S = aa + a1 + a2;
             const T cm = ad * T(1.0 / 120.0);

@@ -85,6 +85,7 @@ struct ps_mesh {
     int grid2 = 1, grid3 = 1, g3c = 1;
     ps::SmemLayout pipe_L0, pipe_L1;   // two-stage layout of the pipelined CG kernel
     int pipe_grid = 0;                 // its persistent grid (0 = not used)
+    int pipeline = 0;                  // ps_mesh_opts::pipeline
     bool coeff_ok = false, alpha_set = false;
     double dt2 = 0.0;
     ps::Workspace ws;

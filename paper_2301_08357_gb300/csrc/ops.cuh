@@ -163,9 +163,17 @@ __device__ __forceinline__ void patches_eval(const MeshDev &m, const ChunkDesc &
 template <typename T>
 __device__ __forceinline__ T node_sum(const ChunkSmem<T> &S, int l) {
     const int b = S.incp[l], e = S.incp[l + 1];
-    T s = T(0);
-    for (int k = b; k < e; ++k) s += S.contrib[S.inc[k]];
-    return s;
+    // four independent partial sums (fixed pattern: deterministic)
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int k = b;
+    for (; k + 3 < e; k += 4) {
+        s0 += S.contrib[S.inc[k]];
+        s1 += S.contrib[S.inc[k + 1]];
+        s2 += S.contrib[S.inc[k + 2]];
+        s3 += S.contrib[S.inc[k + 3]];
+    }
+    for (; k < e; ++k) s0 += S.contrib[S.inc[k]];
+    return (s0 + s1) + (s2 + s3);
 }
 
 // Process chunk c.  Returns this thread's share of the mode's dot product

@@ -359,7 +359,7 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
                                                                                       kBlock, m->pipe_L0.total);
         if (oe != cudaSuccess || m->pipe_L0.total > 200 * 1024) per_sm = 0;
         cudaGetLastError();
-        m->pipe_grid = per_sm > 0 ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
+        m->pipe_grid = (per_sm > 0 && m->pipeline) ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
     }
     {
         int64_t g = (d.n_pad / 4 + kBlock - 1) / kBlock;
@@ -383,6 +383,7 @@ extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double 
     ps_mesh *m = new (std::nothrow) ps_mesh();
     if (!m) return PS_ENOMEM;
     m->ctx = c;
+    m->pipeline = opts ? opts->pipeline : 0;
     std::string err = prepare_mesh(dim, n_nodes, coords, n_elems, conn, dirichlet, po, m->prep);
     if (!err.empty()) {
         ps_set_last_error(err.c_str());

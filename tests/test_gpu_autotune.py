@@ -1,0 +1,35 @@
+"""The autotuner picks a layout and an inner tolerance by measurement through
+the C ABI; the parameters it returns give a correct solve."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_08357_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_returns_working_parameters():
+    import torch
+    from paper_2301_08357_gb300 import autotune, build
+    build.build()
+    from paper_2301_08357_gb300 import pressure as P
+    case = S.make_c2(14)
+    ctx = P.ps_ctx_create(0)
+    try:
+        res = autotune.tune(P, ctx, case, chunks=(256, 1024), pipelines=(0, 1), inner_tols=(1e-3, 1e-5),
+                            reps=5, solve_reps=1)
+        assert res["chunk_elems"] in (256, 1024) and res["pipeline"] in (0, 1)
+        assert res["inner_tol"] in (1e-3, 1e-5)
+        assert len(res["table"]) == 4 and all(r["op_ms"] > 0 for r in res["table"])
+        m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet,
+                             chunk_elems=res["chunk_elems"], pipeline=res["pipeline"])
+        P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+        b = torch.as_tensor(case.b, device="cuda")
+        x = torch.zeros_like(b)
+        st, info = P.ps_pressure_solve(m, b, x, P.make_opts(inner_tol=res["inner_tol"]))
+        A = oracle.PressureMatrix.from_case(case)
+        assert st == P.PS_OK and A.residual(case.b, x.cpu().numpy()) <= 1.05e-10
+        P.ps_mesh_free(m)
+    finally:
+        P.ps_ctx_destroy(ctx)
