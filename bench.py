@@ -36,6 +36,12 @@ if ROOT not in sys.path:
 METRIC = "pressure CG DOF-iters/s + HBM GB/s; solves/s, p50/p99 ms at 1e-10 rel residual"
 UNIT = "DOF-iter/s"
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the current kernel source (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (kernel, cells per side).  An entry is
+# removed whenever the kernel changes; missing means not captured (null).
+TRAFFIC = {}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -48,9 +54,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="c2 only: warm-up and timed solves alone (no e2e pass, no kernel timing, no CPU "
+                         "baseline), for a profiler's launch list; the line then has no roofline or e2e")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
-    ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "fused"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
                          "c4 = 256-mesh batch; c5 = served Poisson stream")
@@ -222,7 +231,8 @@ def run_ours(args):
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()
     mode = P.PS_MODE_MIXED if args.mode == "mixed" else P.PS_MODE_FP64
-    engine = {"auto": P.PS_ENGINE_AUTO, "graph": P.PS_ENGINE_GRAPH, "persistent": P.PS_ENGINE_PERSISTENT}[args.engine]
+    engine = {"auto": P.PS_ENGINE_AUTO, "graph": P.PS_ENGINE_GRAPH, "persistent": P.PS_ENGINE_PERSISTENT,
+              "fused": P.PS_ENGINE_FUSED}[args.engine]
     opts = P.make_opts(mode=mode, tol=1e-10, engine=engine)
     b = torch.as_tensor(case.b, device="cuda")
     x = torch.zeros_like(b)
@@ -266,6 +276,15 @@ def run_ours(args):
     dof_iters = case.n_free * iters
     t_max, tot_dof = aggregate(total_ms, dof_iters, device="cuda")
     value = tot_dof / (t_max / 1e3)
+    if args.launch_list:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                              "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+                              "config": {"workload": workload_name(args.n), "engine": args.engine},
+                              "gpu_launches": launches, "launch_list_run": True}))
+        P.ps_mesh_free(m)
+        P.ps_ctx_destroy(ctx)
+        return
 
     # ---- end to end through the C ABI with host buffers (copies timed)
     b_h = torch.as_tensor(case.b).pin_memory()
@@ -284,27 +303,38 @@ def run_ours(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = case.n_free * (info.iters_inner + info.iters_outer) * len(e2e_ms) / (np.sum(e2e_ms) / 1e3)
 
-    # ---- roofline of the dominant kernel: the FP32 CG operator pass (chunk kernel)
-    which = P.PS_KERNEL_CG_F32 if mode == P.PS_MODE_MIXED else P.PS_KERNEL_CG_F64
+    # ---- roofline of the dominant kernel
+    fused = mode == P.PS_MODE_MIXED and (args.engine == "fused" or (args.engine == "auto" and case.n_nodes <= 200000))
+    if fused:
+        which, kname = P.PS_KERNEL_CG1_F32, "k_cg1_chunks<3>"
+    elif mode == P.PS_MODE_MIXED:
+        which, kname = P.PS_KERNEL_CG_F32, "k_cg2_chunks<3,float>"
+    else:
+        which, kname = P.PS_KERNEL_CG_F64, "k_cg2_chunks<3,double>"
     kern_ms = P.ps_profile_kernel(m, which, reps=50, stream=stream)
     kern_other = {name: P.ps_profile_kernel(m, k, reps=50, stream=stream)
-                  for name, k in (("update_f32", P.PS_KERNEL_UPDATE_F32), ("apply_f32", P.PS_KERNEL_APPLY_F32),
-                                  ("resid_f64", P.PS_KERNEL_RESID_F64))}
+                  for name, k in (("cg1_f32_fused", P.PS_KERNEL_CG1_F32), ("update_f32", P.PS_KERNEL_UPDATE_F32),
+                                  ("apply_f32", P.PS_KERNEL_APPLY_F32), ("resid_f64", P.PS_KERNEL_RESID_F64))}
     E, N = stats.n_elems, stats.n_nodes
-    if mode == P.PS_MODE_MIXED:
-        # per element: 4 x u16 local vertex ids + 4 x u16 incidence entries + f32 beta*dt^2 = 20 B
-        # per node: f32 (x, y, z, alpha) 16 B + p_old, r, D^-1 in 12 B + p, q out 8 B = 36 B
+    # per element (all kernels): patch/connectivity + incidence ids and beta*dt^2 = 20 B
+    if fused:
+        # per node: record (x, y, z, alpha) 16 B + r, w, s, p, x, D^-1 read 24 B + r, s, p, x, w written 20 B
+        alg_bytes = 20 * E + 60 * N
+    elif mode == P.PS_MODE_MIXED:
+        # per node: record 16 B + p_old, r, D^-1 read 12 B + p, q written 8 B
         alg_bytes = 20 * E + 36 * N
     else:
         alg_bytes = 24 * E + 32 * 2 * N + 8 * 5 * N
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    traffic = TRAFFIC.get((kname, args.n))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_chunks<3,%s,kCG>" % ("float" if mode == P.PS_MODE_MIXED else "double"),
+            "traffic": traffic, "kernel": kname,
             "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
             "other_kernels_ms": kern_other, "chunks": stats.n_chunks,
             "shared_node_frac": stats.n_shared / stats.n_nodes,
-            "note": "64^3 working set (~%.0f MB/launch) is L2-resident" % (alg_bytes / 1e6)}
+            "note": "%d^3 working set (~%.0f MB/launch) %s L2-resident between iterations"
+                    % (args.n, alg_bytes / 1e6, "is" if alg_bytes < 100e6 else "is not")}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

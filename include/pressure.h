@@ -95,8 +95,14 @@ typedef struct {
     int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
     int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
                              /* negative = launch kernels directly, no graph)      */
-    int32_t engine;          /* single solves: PS_ENGINE_AUTO / PS_ENGINE_GRAPH run */
-                             /* the multi-kernel PCG captured in CUDA graphs;       */
+    int32_t engine;          /* single solves, captured in CUDA graphs:             */
+                             /* PS_ENGINE_GRAPH: two kernels per CG iteration;      */
+                             /* PS_ENGINE_FUSED (mixed mode): one fused kernel per  */
+                             /* inner iteration (one-reduction PCG): fewer launches */
+                             /* and reductions, more vector traffic per pass; FP64  */
+                             /* mode falls back to two kernels;                     */
+                             /* PS_ENGINE_AUTO: FUSED for meshes of at most 200,000 */
+                             /* nodes (where it measured faster), else GRAPH;       */
                              /* PS_ENGINE_PERSISTENT (mixed mode) runs the batched  */
                              /* persistent engine on a batch of one, which gives    */
                              /* bitwise the result the mesh gets in any batch       */
@@ -106,6 +112,7 @@ typedef struct {
 #define PS_ENGINE_AUTO        0
 #define PS_ENGINE_GRAPH       1
 #define PS_ENGINE_PERSISTENT  2
+#define PS_ENGINE_FUSED       3
 
 typedef struct {
     int32_t status;          /* PS_OK, PS_ENOTCONV, PS_EBREAKDOWN, ...             */
@@ -327,12 +334,16 @@ int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_e
  *   PS_KERNEL_APPLY_F32  FP32 operator apply alone (chunk kernel + shared-node sums)
  *   PS_KERNEL_RESID_F64  FP64 true-residual chunk kernel
  *   PS_KERNEL_CG_F64     FP64 CG operator kernel
+ *   PS_KERNEL_CG1_F32    FP32 fused one-reduction CG pass (node updates of x, r, s, p,
+ *                        u = D^-1 r, w = A u, gamma, delta, rho): the whole inner
+ *                        iteration of the default mixed-precision solve
  * Errors: PS_EINVAL, PS_ESTATE (coefficients not set). */
 #define PS_KERNEL_CG_F32     0
 #define PS_KERNEL_UPDATE_F32 1
 #define PS_KERNEL_APPLY_F32  2
 #define PS_KERNEL_RESID_F64  3
 #define PS_KERNEL_CG_F64     4
+#define PS_KERNEL_CG1_F32    5
 int ps_profile_kernel(ps_mesh *mesh, int which, int reps, void *stream, double *avg_ms);
 
 #ifdef __cplusplus

@@ -1,10 +1,12 @@
 """Autotuner for the solver's free parameters (chunk size, operator-kernel
-variant, inner tolerance of the mixed solver).
+variant, single-solve engine, inner tolerance of the mixed solver).
 
 It measures through the C ABI only: each candidate mesh layout is uploaded,
-the FP32 CG operator kernel and the update kernel are timed with
-ps_profile_kernel (CUDA events on the caller's stream), and for the best few
-layouts whole solves are timed with ps_pressure_solve.  The result is a plain
+the FP32 CG kernels are timed with ps_profile_kernel (CUDA events on the
+caller's stream): the operator and update kernels of the two-kernel
+iteration and the fused one-reduction pass; the cheaper iteration picks the
+engine.  On the best layout whole solves are timed with ps_pressure_solve to
+pick the inner tolerance.  The result is a plain
 dict that the caller passes back as ps_mesh_upload / ps_solve_opts
 arguments; nothing is cached behind the caller's back.
 """
@@ -21,7 +23,7 @@ INNER_TOLS = (1e-3, 1e-4, 1e-5)
 
 def tune(P, ctx, case, stream=None, chunks=CHUNKS, pipelines=PIPELINES, inner_tols=INNER_TOLS,
          reps=20, solve_reps=2):
-    """Return {'chunk_elems', 'pipeline', 'inner_tol', 'table': [...]} for `case`
+    """Return {'chunk_elems', 'pipeline', 'engine', 'inner_tol', 'table': [...]} for `case`
     (a synthetic.Case or any object with dim/coords/conn/dirichlet/alpha/beta/dt2/b).
 
     `P` is the pressure binding, `ctx` a ps_ctx.  Requires torch for device
@@ -45,8 +47,14 @@ def tune(P, ctx, case, stream=None, chunks=CHUNKS, pipelines=PIPELINES, inner_to
                 P.ps_pressure_solve(m, b, x, opts, stream)      # warm-up, fills the workspace
                 k1 = P.ps_profile_kernel(m, P.PS_KERNEL_CG_F32, reps, stream)
                 k2 = P.ps_profile_kernel(m, P.PS_KERNEL_UPDATE_F32, reps, stream)
-                table.append({"chunk_elems": ce, "pipeline": pl, "op_ms": k1, "update_ms": k2,
-                              "iter_ms": k1 + k2})
+                row = {"chunk_elems": ce, "pipeline": pl, "op_ms": k1, "update_ms": k2,
+                       "iter_ms": k1 + k2, "engine": P.PS_ENGINE_GRAPH}
+                if pl == 0:        # the fused pass does not use the pipelined kernel
+                    kf = P.ps_profile_kernel(m, P.PS_KERNEL_CG1_F32, reps, stream)
+                    row["fused_ms"] = kf
+                    if kf < row["iter_ms"]:
+                        row["iter_ms"], row["engine"] = kf, P.PS_ENGINE_FUSED
+                table.append(row)
             finally:
                 P.ps_mesh_free(m)
     if not table:
@@ -60,7 +68,7 @@ def tune(P, ctx, case, stream=None, chunks=CHUNKS, pipelines=PIPELINES, inner_to
     try:
         P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
         for it in inner_tols:
-            o = P.make_opts(tol=1e-10, inner_tol=it)
+            o = P.make_opts(tol=1e-10, inner_tol=it, engine=best["engine"])
             ts = []
             for _ in range(solve_reps + 1):
                 x.zero_()
@@ -75,5 +83,5 @@ def tune(P, ctx, case, stream=None, chunks=CHUNKS, pipelines=PIPELINES, inner_to
     finally:
         P.ps_mesh_free(m)
     solves.sort(key=lambda r: r["solve_ms"])
-    return {"chunk_elems": best["chunk_elems"], "pipeline": best["pipeline"],
+    return {"chunk_elems": best["chunk_elems"], "pipeline": best["pipeline"], "engine": best["engine"],
             "inner_tol": solves[0]["inner_tol"] if solves else 1e-4, "table": table, "solves": solves}

@@ -8,6 +8,7 @@
 
 #include "../../include/pressure.h"
 #include "batched.h"
+#include "cg1.cuh"
 
 namespace ps {
 
@@ -72,24 +73,8 @@ __device__ __forceinline__ float2 split_df(double v) {
     return make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
-// One-reduction PCG update of one node from its old values (shared by the
-// chunk pass, for every local node, and the shared-node pass):
-//   s' = w + beta s, r' = r - alpha s', u' = D^-1 r', p' = D^-1 r + beta p,
-//   x' = x + alpha p'.  Explicit roundings: the same inputs give bitwise the
-// same outputs wherever this is evaluated.
-struct NodeUpd {
-    float s, r, u, p, x;
-};
-__device__ __forceinline__ NodeUpd node_update(float r, float w, float s, float di, float p, float x, float alpha,
-                                               float beta) {
-    NodeUpd o;
-    o.s = __fmaf_rn(beta, s, w);
-    o.r = __fmaf_rn(-alpha, o.s, r);
-    o.u = __fmul_rn(di, o.r);
-    o.p = __fmaf_rn(beta, p, __fmul_rn(di, r));
-    o.x = __fmaf_rn(alpha, o.p, x);
-    return o;
-}
+// node_update (cg1.cuh): the one-reduction PCG update of one node from its
+// old values, shared by the chunk pass and the shared-node pass.
 
 // Phase 1 for one chunk of mesh M: node updates (written for interior nodes),
 // w' = A u' (interior rows written, shared rows as partial sums), and the

@@ -21,7 +21,7 @@ struct DevAlloc {
 };
 
 struct GraphRec {
-    int kind;    // precision (0 FP32, 1 FP64) + 2 * (no preconditioner)
+    int kind;    // precision (0 FP32, 1 FP64) + 2 * (no preconditioner) + 4 * (fused engine)
     int iters;
     cudaGraphExec_t exec;
 };
@@ -36,6 +36,11 @@ struct Workspace {
     double *part64 = nullptr;
     double *dot1 = nullptr, *dot2 = nullptr;
     double *pq2 = nullptr, *z3 = nullptr;   // two-kernel CG partials
+    // fused CG (FP32): second buffers of x, r, p, w (first: x32, r32, p32,
+    // q32), both buffers of s, second partial buffer, per-chunk dot triples
+    float *x32b = nullptr, *r32b = nullptr, *p32b = nullptr, *q32b = nullptr;
+    float *s32a = nullptr, *s32b = nullptr, *part32b = nullptr;
+    double *dots1 = nullptr;
     CgState *st = nullptr;
     CgState *h_st = nullptr;
     float *one32 = nullptr;

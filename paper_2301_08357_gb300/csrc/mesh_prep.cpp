@@ -268,6 +268,17 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         // aim for >= 4 chunks per SM of a 152-SM part, 96..1536 elements each
         int64_t t = n_elems / 608;
         t = std::max<int64_t>(96, std::min<int64_t>(1536, t));
+        if (dim == 3) {
+            // 6 * 2^k tets: on Kuhn-type meshes (6 tets per cube cell) such a
+            // chunk is a Morton block of cells, with the fewest shared nodes
+            int64_t b = 96;
+            while (b < t && b < 1536) b *= 2;
+            t = b;
+            // large meshes: 8^3-cell blocks; fewer shared nodes outweigh the
+            // lower occupancy of the larger shared-memory footprint once
+            // there are many waves of chunks (measured on 128^3: -14% per pass)
+            if (n_elems >= (int64_t)3072 * 152 * 8) t = 3072;
+        }
         ec = (int)round_up(t, 32);
     }
     ec = std::max(1, std::min(ec, kMaxChunkPatches));
@@ -475,6 +486,18 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     // partial sums are stored shared-node-major: chunk slot -> its position
     m.sh_dest.assign(m.sh_total, -1);
     for (size_t k = 0; k < m.shr_slot.size(); ++k) m.sh_dest[m.shr_slot[k]] = (int32_t)k;
+    // the first chunk holding a shared node owns it: that chunk alone stores
+    // the node's values in passes where every holder evaluates them
+    m.sh_info.assign(m.sh_total * 4, 0);
+    for (int64_t k = 0; k < m.sh_total; ++k) {
+        const int32_t g = m.sh_ids[k];
+        m.sh_info[4 * k] = g;
+        if (g < 0) continue;
+        const int64_t s = g - m.n_int;
+        m.sh_info[4 * k + 1] = m.shr_ptr[s];
+        m.sh_info[4 * k + 2] = m.shr_ptr[s + 1];
+        m.sh_info[4 * k + 3] = m.shr_slot[m.shr_ptr[s]] == k ? 1 : 0;
+    }
     return "";
 }
 
@@ -549,6 +572,21 @@ std::string validate_prep(const PrepMesh &m, const int32_t *conn) {
         }
     for (int64_t k = 0; k < m.sh_total; ++k)
         if ((m.sh_ids[k] >= 0) != (slot_hits[k] == 1)) return "partial slots not a bijection";
+    if ((int64_t)m.sh_info.size() != 4 * m.sh_total) return "slot info missing";
+    std::vector<int> owners(m.n_shared, 0);
+    for (int64_t k = 0; k < m.sh_total; ++k) {
+        const int32_t *si = &m.sh_info[4 * k];
+        if (si[0] != m.sh_ids[k]) return "slot info node mismatch";
+        if (si[0] < 0) {
+            if (si[1] || si[2] || si[3]) return "slot info on a pad slot";
+            continue;
+        }
+        const int64_t s = si[0] - m.n_int;
+        if (si[1] != m.shr_ptr[s] || si[2] != m.shr_ptr[s + 1]) return "slot info range mismatch";
+        if (si[3]) owners[s]++;
+    }
+    for (int64_t s = 0; s < m.n_shared; ++s)
+        if (owners[s] != 1) return "shared node without exactly one owner";
     return "";
 }
 

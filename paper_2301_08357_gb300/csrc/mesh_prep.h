@@ -42,6 +42,9 @@ struct PrepMesh {
     std::vector<int32_t> shr_ptr;                  // [n_shared + 1]
     std::vector<int32_t> shr_slot;                 // chunk-major slot of each shared-node-major partial
     std::vector<int32_t> sh_dest;                  // [sh_total] shared-node-major position of a chunk slot, -1 pad
+    // [sh_total * 4] per chunk slot: node id, begin and end of the node's
+    // partial-sum range, 1 on the owner slot (the node's first chunk); pads -1, 0, 0, 0
+    std::vector<int32_t> sh_info;
 };
 
 // Returns "" on success, else an error message (bad input).

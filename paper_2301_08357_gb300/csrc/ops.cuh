@@ -33,6 +33,7 @@ struct MeshDev {
     const uint16_t *pids;    // [patch_total * kPatchIds]
     const uint16_t *incp, *inc;
     const int32_t *sh_ids, *shr_ptr, *sh_dest;
+    const int4 *sh_info;     // [sh_total] node id, partial range [begin, end), owner flag
     const NodeF *node32;
     const NodeD *node64;
     const float *bdt2_32;
@@ -50,7 +51,9 @@ struct CgState {
     long long iters, max_iters;
     int done, status;
     unsigned int cnt_a, cnt_b;
-    int host_done_idx, pad;
+    int first, free_run;     // fused engine: first = the start pass is next;
+                             // free_run = never stop (kernel timing only)
+    double tol2;             // fused engine: relative stopping tolerance squared
 };
 
 enum CgStatus : int { kCgRunning = 0, kCgConverged = 1, kCgMaxIter = 2, kCgBreakdown = 3 };

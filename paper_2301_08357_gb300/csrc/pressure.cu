@@ -20,6 +20,7 @@
 
 #include "../../include/pressure.h"
 #include "internal.h"
+#include "cg1.cuh"
 #include "cg2.cuh"
 
 using namespace ps;
@@ -161,20 +162,23 @@ static cudaError_t set_max_dyn_smem(F *func) {
     return e;
 }
 
+// Every kernel launched with a chunk's shared-memory layout (which can pass
+// the 48 KB default for large chunks) gets the opt-in maximum.
 static int set_smem_attrs() {
-    const int lim = 227 * 1024;
-    CK(cudaFuncSetAttribute(k_chunks<2, float, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, float, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<2, double, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, double, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<2, float, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, float, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<2, double, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, double, kCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<2, double, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, double, kResid>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<2, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(k_chunks<3, double, kDiag>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(set_max_dyn_smem(k_chunks<2, float, kApply>));
+    CK(set_max_dyn_smem(k_chunks<3, float, kApply>));
+    CK(set_max_dyn_smem(k_chunks<2, double, kApply>));
+    CK(set_max_dyn_smem(k_chunks<3, double, kApply>));
+    CK(set_max_dyn_smem(k_chunks<2, float, kCG>));
+    CK(set_max_dyn_smem(k_chunks<3, float, kCG>));
+    CK(set_max_dyn_smem(k_chunks<2, double, kCG>));
+    CK(set_max_dyn_smem(k_chunks<3, double, kCG>));
+    CK(set_max_dyn_smem(k_chunks<2, double, kResid>));
+    CK(set_max_dyn_smem(k_chunks<3, double, kResid>));
+    CK(set_max_dyn_smem(k_chunks<2, double, kDiag>));
+    CK(set_max_dyn_smem(k_chunks<3, double, kDiag>));
+    CK(set_max_dyn_smem(k_cg1_chunks<2>));
+    CK(set_max_dyn_smem(k_cg1_chunks<3>));
     CK(set_max_dyn_smem(k_cg2_chunks<2, float>));
     CK(set_max_dyn_smem(k_cg2_chunks<3, float>));
     CK(set_max_dyn_smem(k_cg2_chunks<2, double>));
@@ -297,6 +301,9 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     d.shr_ptr = i32;
     RC(upload(c, m, &i32, pm.sh_dest.data(), pm.sh_dest.size() * 4));
     d.sh_dest = i32;
+    int4 *i4;
+    RC(upload(c, m, &i4, pm.sh_info.data(), pm.sh_info.size() * 4));
+    d.sh_info = i4;
     RC(upload(c, m, &m->d_loc_node, pm.loc_node.data(), pm.loc_node.size() * 4));
     RC(upload(c, m, &m->d_elem_src, pm.elem_src.data(), pm.elem_src.size() * 4));
     RC(upload(c, m, &m->d_old_of_new, pm.old_of_new.data(), pm.old_of_new.size() * 4));
@@ -583,6 +590,14 @@ int ensure_workspace(ps_mesh *m) {
     WA(st, CgState, 1);
     WA(pq2, double, m->dev.n_chunks + 8);
     WA(z3, double, 6 * m->g3c + 8);
+    WA(x32b, float, np);
+    WA(r32b, float, np);
+    WA(p32b, float, np);
+    WA(q32b, float, np);
+    WA(s32a, float, np);
+    WA(s32b, float, np);
+    WA(part32b, float, sh);
+    WA(dots1, double, 3 * m->dev.n_chunks + 8);
 #undef WA
     if (rc != PS_OK) {
         dfree_all(c, w.allocs);
@@ -621,9 +636,46 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
     return a;
 }
 
-// Enqueue `iters` CG iterations (no host sync) of precision T.
+static CG1Vec cg1_vec(ps_mesh *m) {
+    Workspace &w = m->ws;
+    CG1Vec v;
+    v.x[0] = w.x32;
+    v.x[1] = w.x32b;
+    v.r[0] = w.r32;
+    v.r[1] = w.r32b;
+    v.s[0] = w.s32a;
+    v.s[1] = w.s32b;
+    v.p[0] = w.p32;
+    v.p[1] = w.p32b;
+    v.w[0] = w.q32;
+    v.w[1] = w.q32b;
+    v.part[0] = w.part32;
+    v.part[1] = w.part32b;
+    v.dinv = m->dev.dinv32;
+    v.dots = reinterpret_cast<float2 *>(w.dots1);
+    return v;
+}
+
+static void launch_cg1(ps_mesh *m, const CG1Vec &v, cudaStream_t s) {
+    if (m->dev.dim == 2)
+        k_cg1_chunks<2><<<m->dev.n_chunks, kBlock, m->dev.sm32.total, s>>>(m->dev, v, m->ws.st);
+    else
+        k_cg1_chunks<3><<<m->dev.n_chunks, kBlock, m->dev.sm32.total, s>>>(m->dev, v, m->ws.st);
+}
+
+// Enqueue `iters` CG iterations (no host sync) of precision T; FP32 with
+// `fused` runs one fused pass per iteration.
 template <typename T>
-static int enqueue_cg_iters(ps_mesh *m, int iters, int, cudaStream_t s) {
+static int enqueue_cg_iters(ps_mesh *m, int iters, bool fused, cudaStream_t s) {
+    if (sizeof(T) == 4 && fused) {
+        const CG1Vec v = cg1_vec(m);
+        for (int k = 0; k < iters; ++k) {
+            launch_cg1(m, v, s);
+            m->launches += 1;
+            CK(cudaGetLastError());
+        }
+        return PS_OK;
+    }
     const Cg2Args<T> a = cg2_args<T>(m);
     const SmemLayout &L = sizeof(T) == 4 ? m->dev.sm32 : m->dev.sm64;
     for (int k = 0; k < iters; ++k) {
@@ -649,13 +701,15 @@ static int enqueue_cg_iters(ps_mesh *m, int iters, int, cudaStream_t s) {
 // Run CG iterations until the device state says done: graph batches of
 // `gi` iterations followed by a copy of the state to pinned host memory.
 template <typename T>
-static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
+static int run_cg_until_done(ps_mesh *m, int gi, bool jac, bool fused, cudaStream_t s) {
     Workspace &w = m->ws;
-    const int kind = (sizeof(T) == 4 ? 0 : 1) + (jac ? 0 : 2);
+    fused = fused && sizeof(T) == 4;
+    const int kind = (sizeof(T) == 4 ? 0 : 1) + (jac ? 0 : 2) + (fused ? 4 : 0);
+    const int per_iter = fused ? 1 : 2;
     if (gi <= 0) {
         const int batch = 15;
         for (;;) {
-            RC(enqueue_cg_iters<T>(m, batch, 0, s));
+            RC(enqueue_cg_iters<T>(m, batch, fused, s));
             CK(cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (w.h_st->done) return PS_OK;
@@ -668,7 +722,7 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
         const int64_t saved_launches = m->launches;
-        int rc = enqueue_cg_iters<T>(m, gi, 0, w.cap_stream);
+        int rc = enqueue_cg_iters<T>(m, gi, fused, w.cap_stream);
         m->launches = saved_launches;
         cudaError_t e2 = cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, w.cap_stream);
         cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
@@ -684,7 +738,7 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, cudaStream_t s) {
     }
     for (;;) {
         CK(cudaGraphLaunch(g->exec, s));
-        m->launches += 2 * (int64_t)gi;
+        m->launches += per_iter * (int64_t)gi;
         CK(cudaStreamSynchronize(s));
         if (w.h_st->done) return PS_OK;
     }
@@ -724,6 +778,8 @@ static int check_dev_err(ps_ctx *c) {
     }
     return PS_OK;
 }
+
+static constexpr int64_t kFusedMaxNodes = 200000;
 
 int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cudaStream_t s) {
     Workspace &w = m->ws;
@@ -789,7 +845,7 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
                 m->launches += 1;
             }
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
-            if ((rc = run_cg_until_done<double>(m, gi, jac, s)) != PS_OK) break;
+            if ((rc = run_cg_until_done<double>(m, gi, jac, false, s)) != PS_OK) break;
             RC(read_state(m, s, &h));
             used += h.iters;
             if (h.status == kCgBreakdown) { status = PS_EBREAKDOWN; rc = PS_OK; break; }
@@ -797,6 +853,12 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
     } else {
         const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-4;
         const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
+        // measured crossover of the per-iteration cost on GB300 (Kuhn cubes):
+        // the fused pass is ~30% faster at 35K nodes, equal near 250K, ~20%
+        // slower at 900K (its larger vector traffic sits in the latency-bound
+        // chunk pass)
+        const bool fused = o.engine == PS_ENGINE_FUSED ||
+                           (o.engine == PS_ENGINE_AUTO && m->dev.n_nodes <= kFusedMaxNodes);
         for (;;) {
             rc = true_residual(m, s, &rr);
             if (rc != PS_OK) break;
@@ -804,18 +866,26 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
             if (rr <= stop_abs2) { status = PS_OK; break; }
             if (used >= max_it || outer > max_outer) { status = PS_ENOTCONV; break; }
             const double scale = 1.0 / std::sqrt(rr);
-            {
+            if (fused) {
+                const CG1Vec v = cg1_vec(m);
+                k_cg1_init_state<<<1, 32, 0, s>>>(w.st, itol * itol, max_it - used);
+                k_cg1_start<<<g3, kBlock, 0, s>>>(np, m->prep.sh_total, v, w.r64, scale);
+                m->launches += 2;
+            } else {
                 Cg2Args<float> a = cg2_args<float>(m);
                 k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, itol * itol, 1,
                                                              max_it - used);
                 m->launches += 1;
             }
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
-            if ((rc = run_cg_until_done<float>(m, gi, jac, s)) != PS_OK) break;
+            if ((rc = run_cg_until_done<float>(m, gi, jac, fused, s)) != PS_OK) break;
             RC(read_state(m, s, &h));
             used += h.iters;
             if (h.status == kCgBreakdown) { status = PS_EBREAKDOWN; rc = PS_OK; break; }
-            k_correct<<<g3, kBlock, 0, s>>>(np, w.x64, w.x32, 1.0 / scale);
+            if (fused)
+                k_cg1_correct<<<g3, kBlock, 0, s>>>(np, w.x64, cg1_vec(m), w.st, 1.0 / scale);
+            else
+                k_correct<<<g3, kBlock, 0, s>>>(np, w.x64, w.x32, 1.0 / scale);
             m->launches += 1;
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
         }
@@ -887,6 +957,7 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
     ps_solve_opts o;
     if (opts) o = *opts; else ps_solve_opts_default(&o);
     if (o.mode != PS_MODE_FP64 && o.mode != PS_MODE_MIXED) return PS_EINVAL;
+    if (o.engine < PS_ENGINE_AUTO || o.engine > PS_ENGINE_FUSED) return PS_EINVAL;
     ps_solve_info local;
     ps_solve_info *inf = info ? info : &local;
     std::memset(inf, 0, sizeof(*inf));
@@ -966,7 +1037,7 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
 
 // ---------------------------------------------------------------- kernel timing
 extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, double *avg_ms) {
-    if (!m || !avg_ms || reps < 1 || which < 0 || which > 4) return PS_EINVAL;
+    if (!m || !avg_ms || reps < 1 || which < 0 || which > 5) return PS_EINVAL;
     if (!m->coeff_ok) return PS_ESTATE;
     std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
@@ -982,6 +1053,8 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
     hs.beta = 0.0;
     hs.max_iters = 1LL << 60;
     hs.stop_rr = -1.0;
+    hs.first = 1;
+    hs.free_run = 1;     // the fused pass never stops
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1037,6 +1110,9 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
                 else k_cg2_chunks<3, double><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
                 break;
             }
+            case 5:
+                launch_cg1(m, cg1_vec(m), s);
+                break;
         }
     };
     one();  // warm-up

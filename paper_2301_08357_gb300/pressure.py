@@ -25,7 +25,7 @@ PS_ETIMEOUT, PS_ECUDA, PS_ESTATE, PS_ENOTFOUND = -5, -6, -7, -8
 PS_F32, PS_F64 = 1, 2
 PS_MODE_FP64, PS_MODE_MIXED = 0, 1
 PS_PRECOND_NONE, PS_PRECOND_JACOBI = 0, 1
-PS_ENGINE_AUTO, PS_ENGINE_GRAPH, PS_ENGINE_PERSISTENT = 0, 1, 2
+PS_ENGINE_AUTO, PS_ENGINE_GRAPH, PS_ENGINE_PERSISTENT, PS_ENGINE_FUSED = 0, 1, 2, 3
 SOFT = {PS_OK, PS_PENDING, PS_ENOTCONV, PS_EBREAKDOWN}
 
 
@@ -336,6 +336,7 @@ def ps_server_get_stats(srv):
 
 
 PS_KERNEL_CG_F32, PS_KERNEL_UPDATE_F32, PS_KERNEL_APPLY_F32, PS_KERNEL_RESID_F64, PS_KERNEL_CG_F64 = 0, 1, 2, 3, 4
+PS_KERNEL_CG1_F32 = 5
 
 
 def ps_profile_kernel(mesh, which, reps=20, stream=None):

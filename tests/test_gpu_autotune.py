@@ -22,12 +22,14 @@ def test_autotune_returns_working_parameters():
         assert res["chunk_elems"] in (256, 1024) and res["pipeline"] in (0, 1)
         assert res["inner_tol"] in (1e-3, 1e-5)
         assert len(res["table"]) == 4 and all(r["op_ms"] > 0 for r in res["table"])
+        assert res["engine"] in (P.PS_ENGINE_GRAPH, P.PS_ENGINE_FUSED)
+        assert all(r["fused_ms"] > 0 for r in res["table"] if r["pipeline"] == 0)
         m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet,
                              chunk_elems=res["chunk_elems"], pipeline=res["pipeline"])
         P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
         b = torch.as_tensor(case.b, device="cuda")
         x = torch.zeros_like(b)
-        st, info = P.ps_pressure_solve(m, b, x, P.make_opts(inner_tol=res["inner_tol"]))
+        st, info = P.ps_pressure_solve(m, b, x, P.make_opts(inner_tol=res["inner_tol"], engine=res["engine"]))
         A = oracle.PressureMatrix.from_case(case)
         assert st == P.PS_OK and A.residual(case.b, x.cpu().numpy()) <= 1.05e-10
         P.ps_mesh_free(m)

@@ -44,21 +44,28 @@ def ctx(P, torch_mod):
 
 
 def gpu_solve(P, torch, m, b, x0, **kw):
-    if "engine" not in kw and kw.get("mode") == "persistent":
-        kw["mode"], kw["engine"] = 1, P.PS_ENGINE_PERSISTENT
+    engines = {"persistent": P.PS_ENGINE_PERSISTENT, "fused": P.PS_ENGINE_FUSED, "graph": P.PS_ENGINE_GRAPH}
+    if "engine" not in kw and kw.get("mode") in engines:
+        kw["mode"], kw["engine"] = 1, engines[kw["mode"]]
     bd = torch.as_tensor(b, dtype=torch.float64, device="cuda")
     xd = torch.as_tensor(x0, dtype=torch.float64, device="cuda").clone()
     st, info = P.ps_pressure_solve(m, bd, xd, P.make_opts(**kw))
     return st, info, xd.cpu().numpy()
 
 
-MODES = [(0, "fp64"), (1, "mixed"), ("persistent", "mixed_persistent")]
+# mixed: the default engine choice; graph: two kernels per inner iteration;
+# fused: one fused one-reduction pass per inner iteration; persistent: the
+# batched engine
+MODES = [(0, "fp64"), (1, "mixed"), ("graph", "mixed_graph"), ("fused", "mixed_fused"),
+         ("persistent", "mixed_persistent")]
 SMALL = [
     ("c1_64", lambda: S.make_c1(64), 0),
     ("c1_32_shuffled", lambda: S.shuffle_case(S.make_c1(32)), 41),
     ("c2_n12", lambda: S.make_c2(12), 0),
     ("c2_n10_shuffled", lambda: S.shuffle_case(S.make_c2(10), seed=5), 77),
     ("c3_n12_warm", lambda: S.make_c3(12), 0),
+    ("c2_n5_one_chunk", lambda: S.make_c2(5), 1000),
+    ("c2_n12_large_chunks", lambda: S.make_c2(12), 4096),    # > 48 KB of shared memory per block
     ("batch_mesh_3", lambda: S.make_batch_case(3, lo=2e3, hi=6e3), 0),
 ]
 
@@ -115,12 +122,19 @@ def test_solve_is_deterministic(P, torch_mod, ctx):
     case = S.make_c2(14)
     m = upload(P, ctx, case)
     try:
-        _, i1, x1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
-        _, i2, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1)
+        _, i1, x1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="graph")
+        _, i2, x2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="graph")
         assert np.array_equal(x1, x2)
         assert i1.iters_inner == i2.iters_inner
-        _, j1, y1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode=1, graph_iters=-1)
+        _, j1, y1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="graph", graph_iters=-1)
         assert np.array_equal(x1, y1)
+        # fused engine: graph batches of an odd length (the pass parity lives
+        # on the device) and direct launches give the same result
+        _, k1, z1 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="fused")
+        _, k2, z2 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="fused", graph_iters=7)
+        _, k3, z3 = gpu_solve(P, torch_mod, m, case.b, case.x0, mode="fused", graph_iters=-1)
+        assert np.array_equal(z1, z2) and np.array_equal(z1, z3)
+        assert k1.kernel_launches < i1.kernel_launches
     finally:
         P.ps_mesh_free(m)
 
