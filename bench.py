@@ -38,7 +38,7 @@ UNIT = "DOF-iter/s"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the current kernel source (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by (kernel, cells per side).  An entry is
+# dram__bytes_write.sum), keyed by (kernel, workload).  An entry is
 # removed whenever the kernel changes; missing means not captured (null).
 TRAFFIC = {}
 
@@ -204,6 +204,43 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def kernel_roofline(P, m, stats, mode, fused, stream, workload):
+    """Roofline entry of the solve's dominant kernel: algorithmic bytes per
+    launch over its CUDA-event time (ps_profile_kernel, back-to-back launches
+    on `stream`), against the measured HBM copy bandwidth."""
+    if fused:
+        which, kname = P.PS_KERNEL_CG1_F32, "k_cg1_chunks<%d>" % stats.dim
+    elif mode == P.PS_MODE_MIXED:
+        which, kname = P.PS_KERNEL_CG_F32, "k_cg2_chunks<%d,float>" % stats.dim
+    else:
+        which, kname = P.PS_KERNEL_CG_F64, "k_cg2_chunks<%d,double>" % stats.dim
+    kern_ms = P.ps_profile_kernel(m, which, reps=50, stream=stream)
+    kern_other = {name: P.ps_profile_kernel(m, k, reps=20, stream=stream)
+                  for name, k in (("cg1_f32_fused", P.PS_KERNEL_CG1_F32), ("cg_f32_two_pass", P.PS_KERNEL_CG_F32),
+                                  ("update_f32", P.PS_KERNEL_UPDATE_F32), ("apply_f32", P.PS_KERNEL_APPLY_F32),
+                                  ("resid_f64", P.PS_KERNEL_RESID_F64))}
+    E, N, d = stats.n_elems, stats.n_nodes, stats.dim
+    esz = 8 if mode == P.PS_MODE_FP64 else 4
+    # per element: d+1 vertex ids (i32) + beta*dt^2
+    elem_b = 4 * (d + 1) + esz
+    if fused:
+        # per node: coordinates + alpha, r w s p x D^-1 read, r s p x w written
+        node_b = esz * (d + 1) + 6 * esz + 5 * esz
+    else:
+        # per node: coordinates + alpha, p_old r D^-1 read, p q written
+        node_b = esz * (d + 1) + 3 * esz + 2 * esz
+    alg_bytes = elem_b * E + node_b * N
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get((kname, workload)), "kernel": kname,
+            "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+            "other_kernels_ms": kern_other, "chunks": stats.n_chunks,
+            "shared_node_frac": stats.n_shared / stats.n_nodes,
+            "note": "working set ~%.0f MB/launch: %s" % (
+                alg_bytes / 1e6, "L2-resident between iterations" if alg_bytes < 100e6 else "exceeds L2 (129 MB)")}
+
+
 def run_ours(args):
     import torch
 
@@ -305,36 +342,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel
     fused = mode == P.PS_MODE_MIXED and (args.engine == "fused" or (args.engine == "auto" and case.n_nodes <= 200000))
-    if fused:
-        which, kname = P.PS_KERNEL_CG1_F32, "k_cg1_chunks<3>"
-    elif mode == P.PS_MODE_MIXED:
-        which, kname = P.PS_KERNEL_CG_F32, "k_cg2_chunks<3,float>"
-    else:
-        which, kname = P.PS_KERNEL_CG_F64, "k_cg2_chunks<3,double>"
-    kern_ms = P.ps_profile_kernel(m, which, reps=50, stream=stream)
-    kern_other = {name: P.ps_profile_kernel(m, k, reps=50, stream=stream)
-                  for name, k in (("cg1_f32_fused", P.PS_KERNEL_CG1_F32), ("update_f32", P.PS_KERNEL_UPDATE_F32),
-                                  ("apply_f32", P.PS_KERNEL_APPLY_F32), ("resid_f64", P.PS_KERNEL_RESID_F64))}
-    E, N = stats.n_elems, stats.n_nodes
-    # per element (all kernels): patch/connectivity + incidence ids and beta*dt^2 = 20 B
-    if fused:
-        # per node: record (x, y, z, alpha) 16 B + r, w, s, p, x, D^-1 read 24 B + r, s, p, x, w written 20 B
-        alg_bytes = 20 * E + 60 * N
-    elif mode == P.PS_MODE_MIXED:
-        # per node: record 16 B + p_old, r, D^-1 read 12 B + p, q written 8 B
-        alg_bytes = 20 * E + 36 * N
-    else:
-        alg_bytes = 24 * E + 32 * 2 * N + 8 * 5 * N
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
-    traffic = TRAFFIC.get((kname, args.n))
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": kname,
-            "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
-            "other_kernels_ms": kern_other, "chunks": stats.n_chunks,
-            "shared_node_frac": stats.n_shared / stats.n_nodes,
-            "note": "%d^3 working set (~%.0f MB/launch) %s L2-resident between iterations"
-                    % (args.n, alg_bytes / 1e6, "is" if alg_bytes < 100e6 else "is not")}
+    roof = kernel_roofline(P, m, stats, mode, fused, stream, workload_name(args.n))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -345,7 +353,7 @@ def run_ours(args):
            "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if mode == P.PS_MODE_MIXED else "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args.n), "n_free": case.n_free, "n_elems": E,
+           "config": {"workload": workload_name(args.n), "n_free": case.n_free, "n_elems": case.n_elems,
                       "mode": args.mode, "precond": "jacobi", "tol": 1e-10,
                       "iters_per_solve": last_info.iters_inner + last_info.iters_outer,
                       "outer_per_solve": last_info.iters_outer, "rel_res": last_info.rel_res,
@@ -412,6 +420,8 @@ def run_single(args, which):
         times.append(e0.elapsed_time(e1))
         iters += info.iters_inner + info.iters_outer
         infos = info
+    stats = P.ps_mesh_get_stats(m)
+    roof = kernel_roofline(P, m, stats, mode, False, stream, case.name)
     err = None
     if which == "c3":
         xs_h = case.extra["xstar"]
@@ -426,7 +436,8 @@ def run_single(args, which):
                       "iters_per_solve": infos.iters_inner + infos.iters_outer, "outer_per_solve": infos.iters_outer,
                       "rel_res": infos.rel_res, "rel_err_vs_xstar": err,
                       "l2": "flushed between steps (256 MB write)"},
-           "solves_per_s": 1e3 * args.steps / tot, "p50_ms": _pctl(times, 50), "p99_ms": _pctl(times, 99)}
+           "solves_per_s": 1e3 * args.steps / tot, "p50_ms": _pctl(times, 50), "p99_ms": _pctl(times, 99),
+           "roofline": roof}
     print(json.dumps(out))
     P.ps_mesh_free(m)
     P.ps_ctx_destroy(ctx)

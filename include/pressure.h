@@ -82,7 +82,9 @@ typedef struct {
     int32_t chunk_nodes_max; /* cap on distinct nodes per chunk (0 = auto)          */
     int32_t pipeline;        /* FP32 CG operator kernel: 0 = one block per chunk,  */
                              /* 1 = persistent blocks with double-buffered staging */
-    int32_t reserved[5];
+    int32_t update_blocks_per_sm; /* grid of the CG update kernel in blocks per SM */
+                             /* (0 = auto)                                          */
+    int32_t reserved[4];
 } ps_mesh_opts;
 
 typedef struct {

@@ -91,6 +91,7 @@ struct ps_mesh {
     ps::SmemLayout pipe_L0, pipe_L1;   // two-stage layout of the pipelined CG kernel
     int pipe_grid = 0;                 // its persistent grid (0 = not used)
     int pipeline = 0;                  // ps_mesh_opts::pipeline
+    int update_bps = 0;                // ps_mesh_opts::update_blocks_per_sm
     bool coeff_ok = false, alpha_set = false;
     double dt2 = 0.0;
     ps::Workspace ws;

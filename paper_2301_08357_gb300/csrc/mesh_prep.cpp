@@ -231,19 +231,32 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     for (int c = 0; c < dim; ++c) ext = std::max(ext, hi[c] - lo[c]);
     if (!(ext > 0)) return "degenerate bounding box";
     const double vol_floor = std::pow(ext, dim) * 1e-30;
+    double det_sum = 0.0;
     for (int64_t e = 0; e < n_elems; ++e) {
         double d = simplex_det(dim, coords, conn + e * nv);
         if (!(std::fabs(d) > vol_floor)) return "element of zero volume";
+        det_sum += std::fabs(d);
         for (int a = 0; a < nv; ++a)
             for (int b = a + 1; b < nv; ++b)
                 if (conn[e * nv + a] == conn[e * nv + b]) return "repeated vertex in element";
     }
 
     // ---- Morton order of element centroids
+    // The quantum is a power-of-two fraction of the typical cell size
+    // h = (mean |det|)^(1/d) (the edge of the cube that d! mean elements
+    // fill), so that on structured (Kuhn-type) meshes every cell maps to one
+    // key prefix and aligned Morton blocks are blocks of whole cells, whatever
+    // the number of cells per side.
     std::vector<uint64_t> key(n_elems);
     std::vector<int32_t> order(n_elems);
     const int bits = dim == 3 ? 21 : 31;
-    const double scale = (double)((1ULL << bits) - 1) / ext;
+    const double qmax = (double)((1ULL << bits) - 1);
+    const double h = std::pow(det_sum / (double)n_elems, 1.0 / dim);
+    double scale = qmax / ext;
+    if (h > 0 && std::isfinite(h)) {
+        const int s = (int)std::floor(std::log2(qmax * h / ext));
+        if (s >= 0) scale = std::ldexp(1.0, s) / h;
+    }
     for (int64_t e = 0; e < n_elems; ++e) {
         double cen[3] = {0, 0, 0};
         for (int a = 0; a < nv; ++a)

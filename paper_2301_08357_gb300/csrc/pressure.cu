@@ -28,6 +28,7 @@ using namespace ps;
 namespace ps {
 
 const int kBlock = 256;
+static const int kUpdateBlocksPerSm = 2;   // update-kernel grid when occupancy is unknown
 
 static int sm_count_of(int dev) {
     int v = 0;
@@ -369,8 +370,20 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         m->pipe_grid = (per_sm > 0 && m->pipeline) ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
     }
     {
+        // auto: one full wave of the update kernel (its resident blocks per
+        // SM times the SMs); measured on 160^3: 33 us at 6 blocks/SM (one
+        // wave) against 59 us at 2 and 43 us at 8 (a partial second wave)
         int64_t g = (d.n_pad / 4 + kBlock - 1) / kBlock;
-        m->g3c = (int)std::max<int64_t>(1, std::min<int64_t>(g, 2 * (int64_t)c->sms));
+        int bps = m->update_bps;
+        if (bps <= 0) {
+            int of = 0, od = 0;
+            cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_cg2_update<float>, kBlock, 0);
+            cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&od, k_cg2_update<double>, kBlock, 0);
+            cudaGetLastError();
+            bps = (e1 == cudaSuccess && e2 == cudaSuccess) ? std::min(of, od) : 0;
+            if (bps <= 0) bps = kUpdateBlocksPerSm;
+        }
+        m->g3c = (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)bps * c->sms));
     }
     return PS_OK;
 }
@@ -391,6 +404,11 @@ extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double 
     if (!m) return PS_ENOMEM;
     m->ctx = c;
     m->pipeline = opts ? opts->pipeline : 0;
+    m->update_bps = opts ? opts->update_blocks_per_sm : 0;
+    if (m->update_bps < 0 || m->update_bps > 64) {
+        delete m;
+        return PS_EINVAL;
+    }
     std::string err = prepare_mesh(dim, n_nodes, coords, n_elems, conn, dirichlet, po, m->prep);
     if (!err.empty()) {
         ps_set_last_error(err.c_str());

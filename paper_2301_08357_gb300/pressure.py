@@ -44,7 +44,7 @@ class PressureError(RuntimeError):
 
 class ps_mesh_opts(C.Structure):
     _fields_ = [("chunk_elems", C.c_int32), ("chunk_nodes_max", C.c_int32), ("pipeline", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("update_blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class ps_solve_opts(C.Structure):
@@ -193,14 +193,15 @@ def ps_ctx_bytes_in_use(ctx):
     return int(_lib.ps_ctx_bytes_in_use(ctx))
 
 
-def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, pipeline=0):
+def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, pipeline=0,
+                   update_blocks_per_sm=0):
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
     n = coords.shape[0]
     pd = None
     if dirichlet is not None:
         dirichlet, pd = _host(dirichlet, np.uint8)
-    o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline)
+    o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline, update_blocks_per_sm)
     h = _vp()
     _check(_lib.ps_mesh_upload(ctx, int(dim), n, pc, conn.shape[0], pe, pd, C.byref(o), C.byref(h)),
            "ps_mesh_upload")
