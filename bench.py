@@ -40,7 +40,14 @@ UNIT = "DOF-iter/s"
 # capture of the current kernel source (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, workload).  An entry is
 # removed whenever the kernel changes; missing means not captured (null).
-TRAFFIC = {}
+TRAFFIC = {
+    # C2 capture (cold cache: ncu flushes the caches before it)
+    ("k_cg2_chunks<3,float>", "c2_3d_kuhn_64^3_tets1572864_nodes274625"): 33324544,
+    # C3 capture
+    ("k_cg2_chunks<3,float>", "c3_3d_160"): 513803776,
+    # 32^3 capture of the fused pass (cold cache)
+    ("k_cg1_chunks<3>", "c2_3d_kuhn_32^3_tets196608_nodes35937"): 5914624,
+}
 
 
 def parse():
@@ -55,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--launch-list", action="store_true",
-                    help="c2 only: warm-up and timed solves alone (no e2e pass, no kernel timing, no CPU "
+                    help="c1/c2/c3: warm-up and timed solves alone (no e2e pass, no kernel timing, no CPU "
                          "baseline), for a profiler's launch list; the line then has no roofline or e2e")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
@@ -420,6 +427,14 @@ def run_single(args, which):
         times.append(e0.elapsed_time(e1))
         iters += info.iters_inner + info.iters_outer
         infos = info
+    if args.launch_list:
+        tot = float(np.sum(times))
+        print(json.dumps({"metric": METRIC, "value": case.n_free * iters / (tot / 1e3), "unit": UNIT,
+                          "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps,
+                          "config": {"workload": case.name}, "launch_list_run": True}))
+        P.ps_mesh_free(m)
+        P.ps_ctx_destroy(ctx)
+        return
     stats = P.ps_mesh_get_stats(m)
     roof = kernel_roofline(P, m, stats, mode, False, stream, case.name)
     err = None
