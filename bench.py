@@ -472,7 +472,7 @@ def run_batch(args):
     t0 = time.perf_counter()
     for i in range(args.meshes):
         c = S.make_batch_case(i, lo=2e3 * args.size_scale, hi=2e5 * args.size_scale)
-        m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet)
+        m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=args.chunk)
         P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
         meshes.append(m)
         bs.append(torch.as_tensor(c.b, device="cuda"))
@@ -529,7 +529,7 @@ def run_served(args):
     cases, meshes = [], []
     for c in range(args.cases):
         cs = S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
-        m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet)
+        m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet, chunk_elems=args.chunk)
         P.ps_coeff_set(m, cs.alpha, cs.beta, cs.dt2)
         cases.append(cs)
         meshes.append(m)
@@ -585,10 +585,40 @@ def run_served(args):
                 "queue_p50_ms": 1e3 * _pctl(qwait, 50), "peak_in_flight": stats["peak_in_flight"],
                 "epochs": stats["epochs"]}
 
+    def single_run(mode):
+        """Requests of the same shape (every case, every step, its drift continuing
+        the case's seeded stream) solved one at a time through ps_pressure_solve
+        (plain FP64 PCG or the mixed single-solve engine), each case warm-starting
+        from its previous pressure; returns solves/s and latency percentiles."""
+        opts = P.make_opts(mode=mode, tol=1e-10)
+        lat, done_iters, worst = [], 0, 0.0
+        xs = [torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda") for c in cases]
+        state = [(c.beta.copy(), c.b.copy()) for c in cases]
+        t_start = time.perf_counter()
+        for k in range(args.case_steps):
+            for ci, c in enumerate(cases):
+                if k > 0:
+                    state[ci] = S.served_step_drift(c, *state[ci])
+                    P.ps_coeff_set_beta(meshes[ci], state[ci][0])
+                t0 = time.perf_counter()
+                b = torch.as_tensor(state[ci][1], device="cuda")
+                st, info = P.ps_pressure_solve(meshes[ci], b, xs[ci], opts)
+                torch.cuda.synchronize()
+                lat.append(time.perf_counter() - t0)
+                worst = max(worst, info.rel_res)
+                done_iters += c.n_free * (info.iters_inner + info.iters_outer)
+        wall = time.perf_counter() - t_start
+        for ci, c in enumerate(cases):          # restore the case coefficients
+            P.ps_coeff_set_beta(meshes[ci], c.beta)
+        return {"mode": "fp64" if mode == P.PS_MODE_FP64 else "mixed", "solves": len(lat), "wall_s": wall,
+                "solves_per_s": len(lat) / wall, "dof_iters_per_s": done_iters / wall,
+                "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99), "max_rel_res": worst}
+
     sat = one_run(None)
     runs = [sat]
     for f in [float(v) for v in args.rates.split(",") if v]:
         runs.append(dict(one_run(f * sat["solves_per_s"]), rate_x_sat=f))
+    singles = [single_run(P.PS_MODE_FP64), single_run(P.PS_MODE_MIXED)]
     out = {"metric": METRIC, "value": sat["dof_iters_per_s"], "unit": UNIT, "n_gpus": 1,
            "steps": args.case_steps, "warmup": 0, "ms_per_step": 1e3 / sat["solves_per_s"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
@@ -596,7 +626,8 @@ def run_served(args):
            "config": {"workload": "c5_served_%d_cases_x_%d_steps" % (args.cases, args.case_steps),
                       "nodes_total": nodes_total},
            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
-           "runs": runs}
+           "served_vs_fp64_single_solves_per_s": sat["solves_per_s"] / singles[0]["solves_per_s"],
+           "runs": runs, "single_solves": singles}
     print(json.dumps(out))
     for m in meshes:
         P.ps_mesh_free(m)

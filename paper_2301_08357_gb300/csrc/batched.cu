@@ -28,19 +28,24 @@ __device__ __forceinline__ int ld_acquire_i32(const int *p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] = arrival count, bar[32] = generation (separate 128-byte lines).
-// The wait is bounded: on timeout the error flag is set and false returned;
-// the caller then leaves the kernel (other blocks time out in turn).
-__device__ bool grid_barrier(unsigned int *bar, int *err) {
+// bar[0] = arrival count, bar[32] = generation, bar[64] = the stop word the
+// last arriver publishes (separate 128-byte lines).  The last block to arrive
+// has seen every block's work of the pass, so it reads the active-mesh count
+// then and publishes "stop" before releasing the generation: every block
+// takes the same decision.  The wait is bounded: on timeout the error flag is
+// set and false returned; the caller then leaves the kernel (other blocks
+// time out in turn).
+__device__ bool grid_barrier_stop(unsigned int *bar, int *err, const int *active_cnt, int *s_stop) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned int *count = bar, *gen = bar + 32;
+        unsigned int *count = bar, *gen = bar + 32, *stop = bar + 64;
         const unsigned int g = ld_acquire_u32(gen);
         const unsigned int arrived = atomic_add_acq_rel(count, 1u);
         int ok = 0;
         if (arrived == gridDim.x - 1) {
             *(volatile unsigned int *)count = 0u;
+            *(volatile unsigned int *)stop = ld_acquire_i32(active_cnt) <= 0 ? 1u : 0u;
             st_release_u32(gen, g + 1u);
             ok = 1;
         } else {
@@ -54,270 +59,101 @@ __device__ bool grid_barrier(unsigned int *bar, int *err) {
             if (!ok) atomicOr(err, kErrGridTimeout);
         }
         s_ok = ok;
+        *s_stop = ok ? (int)*(volatile unsigned int *)stop : 1;
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-// Block sum of three double-float accumulators; result in red[32..34].
-__device__ __forceinline__ void block_sum3(const DotF &a, const DotF &b, const DotF &c, double *red, double out[3]) {
-    out[0] = block_sum(a, red);
-    out[1] = block_sum(b, red);
-    out[2] = block_sum(c, red);
-}
-
-// A double as an unevaluated float pair (hi + lo), for partial sums that are
-// later reduced with FP32 error-free additions only.
-__device__ __forceinline__ float2 split_df(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(v - (double)hi));
-}
-
-// node_update (cg1.cuh): the one-reduction PCG update of one node from its
-// old values, shared by the chunk pass and the shared-node pass.
-
-// Phase 1 for one chunk of mesh M: node updates (written for interior nodes),
-// w' = A u' (interior rows written, shared rows as partial sums), and the
-// chunk's shares of gamma = r'.u', delta = w'.u', rho = r'.r'.
-__device__ void chunk_cg1(const BMesh &M, int c, const ChunkSmem<float> &S, uint32_t &phase, float alpha, float beta,
-                          DotF acc[3], bool &failed) {
-    const MeshDev &m = M.d;
-    const ChunkDesc cd = m.chunks[c];
-    const int n_loc = cd.n_loc, n_int = cd.n_int;
-    stage_issue<float>(m, cd, S);
-    if (!stage_wait<float>(m, S, phase)) {
-        failed = true;
-        return;
-    }
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        const bool interior = l < n_int;
-        const int g = interior ? cd.int_begin + l : S.shid[l - n_int];
-        // vectors written earlier in this launch by other blocks: read at L2 (.cg)
-        const float di = m.dinv32[g];
-        const float r = __ldcg(M.r + g), w = __ldcg(M.w + g), s = __ldcg(M.s + g);
-        const float p = interior ? __ldcg(M.p + g) : 0.f, x = interior ? __ldcg(M.x + g) : 0.f;
-        NodeUpd o = node_update(r, w, s, di, p, x, alpha, beta);
-        if (is_dirichlet(S.node[l].w)) {
-            o.u = 0.f;
-            o.r = 0.f;
-        }
-        S.val[l] = o.u;
-        S.aux[l] = o.r;
-        if (interior) {
-            M.s[g] = o.s;
-            M.r[g] = o.r;
-            M.p[g] = o.p;
-            M.x[g] = o.x;
-        }
-    }
-    __syncthreads();
-    if (m.dim == 3)
-        patches_eval<3, float, false>(m, cd, S);
-    else
-        patches_eval<2, float, false>(m, cd, S);
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        float wv = node_sum(S, l);
-        if (is_dirichlet(S.node[l].w)) wv = 0.f;
-        if (l < n_int) {
-            M.w[cd.int_begin + l] = wv;
-            const float u = S.val[l], r = S.aux[l];
-            acc[0].add_prod(r, u);
-            acc[1].add_prod(wv, u);
-            acc[2].add_prod(r, r);
-        } else {
-            M.part[m.sh_dest[cd.sh_off + (l - n_int)]] = wv;
-        }
-    }
-}
-
-// Reduce mesh M's per-task dot triplets (fixed order) and advance its
-// scalars.  Called by the last block to finish the mesh's phase-2 tasks.
-__device__ void mesh_scalars(const BMesh &M, double *red, int *active_cnt) {
-    const int n = M.d.n_chunks + M.n_segs;
-    DotF ag, ad, ar;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const float2 g2 = __ldcg(M.dots + 3 * k), d2 = __ldcg(M.dots + 3 * k + 1), r2 = __ldcg(M.dots + 3 * k + 2);
-        ag.merge(g2.x, g2.y);
-        ad.merge(d2.x, d2.y);
-        ar.merge(r2.x, r2.y);
-    }
-    double out[3];
-    block_sum3(ag, ad, ar, red, out);
-    const double g = out[0], d = out[1], rho = out[2];
-    if (threadIdx.x != 0) return;
-    BState *st = M.st;
-    st->cnt2 = 0;
-    int done = 0, status = 0;
-    if (st->first) {
-        st->first = 0;
-        st->rho0 = rho;
-        st->stop2 = st->inner_tol2 * rho;
-        if (!(rho > 0.0)) {
-            done = 1;
-            status = kCgConverged;
-        } else if (!(d > 0.0) || !isfinite(g) || !isfinite(d)) {
-            done = 1;
-            status = kCgBreakdown;
-        } else {
-            st->alpha = g / d;
-            st->beta = 0.0;
-        }
-    } else {
-        st->iters += 1;
-        st->iters_total += 1;
-        const double beta = g / st->gamma;
-        const double den = d - beta * g / st->alpha;
-        if (!isfinite(rho) || !isfinite(g) || !isfinite(d) || !(den > 0.0)) {
-            done = 1;
-            status = kCgBreakdown;
-        } else if (rho <= st->stop2) {
-            done = 1;
-            status = kCgConverged;
-        } else if (st->iters_total >= st->max_iters) {
-            done = 1;
-            status = kCgMaxIter;
-        } else {
-            st->beta = beta;
-            st->alpha = g / den;
-        }
-    }
-    st->gamma = g;
-    st->delta = d;
-    st->rho = rho;
-    if (done) {
-        st->status = status;
-        st->done = 1;
-        st->phase = kPhCorrect;
-        atomicSub(active_cnt, 1);
-    }
-}
-
-// Phase 2 for one segment of shared nodes of mesh M; the last block of the
-// mesh also advances its scalars.
-__device__ void seg_cg1(const BMesh &M, int seg, float alpha, float beta, double *red, int *active_cnt) {
-    const MeshDev &m = M.d;
-    const int64_t s0 = (int64_t)seg * kSegLen;
-    const int64_t s1 = s0 + kSegLen < m.n_shared ? s0 + kSegLen : m.n_shared;
-    DotF a0, a1, a2;
-    for (int64_t sidx = s0 + threadIdx.x; sidx < s1; sidx += blockDim.x) {
-        const int64_t g = m.n_int + sidx;
-        float wv = 0.f;
-        const int kb = m.shr_ptr[sidx], ke = m.shr_ptr[sidx + 1];
-        for (int k = kb; k < ke; ++k) wv += __ldcg(M.part + k);
-        NodeUpd o = node_update(__ldcg(M.r + g), __ldcg(M.w + g), __ldcg(M.s + g), m.dinv32[g], __ldcg(M.p + g),
-                                __ldcg(M.x + g), alpha, beta);
-        if (m.dirichlet[g]) {
-            o.u = 0.f;
-            o.r = 0.f;
-            wv = 0.f;
-        }
-        M.s[g] = o.s;
-        M.r[g] = o.r;
-        M.p[g] = o.p;
-        M.x[g] = o.x;
-        M.w[g] = wv;
-        a0.add_prod(o.r, o.u);
-        a1.add_prod(wv, o.u);
-        a2.add_prod(o.r, o.r);
-    }
-    double out[3];
-    block_sum3(a0, a1, a2, red, out);
-    __shared__ bool s_last;
-    if (threadIdx.x == 0) {
-        const int k = m.n_chunks + seg;
-        M.dots[3 * k] = split_df(out[0]);
-        M.dots[3 * k + 1] = split_df(out[1]);
-        M.dots[3 * k + 2] = split_df(out[2]);
-        const unsigned int t = atomic_add_acq_rel(&M.st->cnt2, 1u);
-        s_last = (t == (unsigned)M.n_segs - 1u);
-    }
-    __syncthreads();
-    if (s_last) mesh_scalars(M, red, active_cnt);
-    __syncthreads();
 }
 
 enum VecOp : int { kPrepare = 0, kInnerInit = 1, kCorrect = 2, kFinish = 3 };
 
 struct PcgArgs {
     const BMesh *meshes;
-    const int2 *t1, *t2;
-    int n_t1, n_t2;
+    const int2 *t1;                // (mesh, chunk) tasks, mesh-major
+    int n_t1, n_meshes;
     unsigned int *bar;
     int *active_cnt;
     int *err;
     int max_it;
-    SmemLayout L;
+    SmemLayout L;                  // chunk layout; the scalar cache follows at L.total
 };
 
-// (run, alpha, beta) of mesh `mi` for this block, read at L2 once per phase
-// and mesh (the cache is reset at every grid barrier).
-struct ScalarCache {
-    int mesh;
-    int run;
-    float alpha, beta;
-};
-__device__ __forceinline__ void task_scalars(const BMesh *meshes, int mi, ScalarCache *sc) {
-    if (sc->mesh == mi) return;     // block-uniform
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const BState *st = meshes[mi].st;
-        sc->run = (__ldcg(&st->phase) == kPhInner && !__ldcg(&st->done)) ? 1 : 0;
-        sc->alpha = (float)__ldcg(&st->alpha);
-        sc->beta = (float)__ldcg(&st->beta);
-        sc->mesh = mi;
+// The last chunk of mesh M to finish a pass: reduce the per-chunk triples and
+// advance the mesh's inner scalars; a finished inner solve moves the mesh to
+// the correction phase.
+__device__ void batch_mesh_scalars(const BMesh &M, double *red, int *active_cnt) {
+    double tot[3];
+    cg1_reduce(M.v.dots, M.d.n_chunks, red, tot);
+    if (threadIdx.x != 0) return;
+    BState *st = M.st;
+    st->in.cnt_a = 0;
+    const int was_first = st->in.first;
+    const int done = cg1_scalars(&st->in, tot[0], tot[1], tot[2]);
+    if (!was_first) st->iters_total += 1;
+    if (done) {
+        st->phase = kPhCorrect;
+        atomicSub(active_cnt, 1);
     }
-    __syncthreads();
 }
 
-// The persistent inner solver: up to max_it iterations of every active mesh.
+// The persistent inner solver: up to max_it fused passes of every mesh in the
+// inner phase, one grid barrier per pass.  At the start of a pass every block
+// reads each mesh's (run, parity, alpha, beta) into its shared-memory cache,
+// so a task costs no scalar round trip.
 __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const ChunkSmem<float> S = chunk_smem<float>(smem, A.L);
-    __shared__ ScalarCache sc;
-    __shared__ int s_act;
+    float2 *c_ab = reinterpret_cast<float2 *>(smem + A.L.total);          // [n_meshes]
+    int *c_par = reinterpret_cast<int *>(c_ab + A.n_meshes);               // [n_meshes], -1 = idle
+    __shared__ int s_stop;
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
         mbar_init(S.bar, 1);
         fence_mbar_init();
+        // no mesh leaves the inner phase before this launch's first pass, so
+        // every block reads the same count here; later decisions come from
+        // the grid barrier
+        s_stop = ld_acquire_i32(A.active_cnt) <= 0;
     }
     __syncthreads();
     uint32_t phase = 0;
     bool failed = false;
-    for (int it = 0; it < A.max_it; ++it) {
-        if (threadIdx.x == 0) {
-            s_act = ld_acquire_i32(A.active_cnt);
-            sc.mesh = -1;
+    for (int it = 0; it < A.max_it && !s_stop; ++it) {
+        for (int i = threadIdx.x; i < A.n_meshes; i += blockDim.x) {
+            const BState *st = A.meshes[i].st;
+            const bool run = __ldcg(&st->phase) == kPhInner && !__ldcg(&st->in.done);
+            c_par[i] = run ? cg1_parity(__ldcg(&st->in.first), __ldcg(&st->in.iters)) : -1;
+            c_ab[i] = make_float2((float)__ldcg(&st->in.alpha), (float)__ldcg(&st->in.beta));
         }
         __syncthreads();
-        if (s_act <= 0) break;
-        // ---- phase 1: chunks
         for (int t = blockIdx.x; t < A.n_t1; t += gridDim.x) {
             const int2 tk = A.t1[t];
+            const int par = c_par[tk.x];
+            if (par < 0) continue;                 // block-uniform
             const BMesh &M = A.meshes[tk.x];
-            task_scalars(A.meshes, tk.x, &sc);
-            if (!sc.run) continue;
+            const float2 ab = c_ab[tk.x];
             DotF acc[3];
-            chunk_cg1(M, tk.y, S, phase, sc.alpha, sc.beta, acc, failed);
+            if (M.d.dim == 3)
+                chunk_cg1f<3>(M.d, cg1_pass(M.v, par), M.v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
+            else
+                chunk_cg1f<2>(M.d, cg1_pass(M.v, par), M.v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
             if (failed) return;
             double out[3];
-            block_sum3(acc[0], acc[1], acc[2], S.red, out);
+            out[0] = block_sum(acc[0], S.red);
+            out[1] = block_sum(acc[1], S.red);
+            out[2] = block_sum(acc[2], S.red);
             if (threadIdx.x == 0) {
-                M.dots[3 * tk.y] = split_df(out[0]);
-                M.dots[3 * tk.y + 1] = split_df(out[1]);
-                M.dots[3 * tk.y + 2] = split_df(out[2]);
+                M.v.dots[3 * tk.y] = df_pack(out[0]);
+                M.v.dots[3 * tk.y + 1] = df_pack(out[1]);
+                M.v.dots[3 * tk.y + 2] = df_pack(out[2]);
+                const unsigned int k = atomic_add_acq_rel(&M.st->in.cnt_a, 1u);
+                s_last = (k == (unsigned)M.d.n_chunks - 1u);
             }
             __syncthreads();
+            if (s_last) batch_mesh_scalars(M, S.red, A.active_cnt);
+            __syncthreads();
         }
-        if (!grid_barrier(A.bar, A.err)) return;
-        // ---- phase 2: shared nodes, then per-mesh scalars
-        if (threadIdx.x == 0) sc.mesh = -1;
-        __syncthreads();
-        for (int t = blockIdx.x; t < A.n_t2; t += gridDim.x) {
-            const int2 tk = A.t2[t];
-            task_scalars(A.meshes, tk.x, &sc);
-            if (!sc.run) continue;
-            seg_cg1(A.meshes[tk.x], tk.y, sc.alpha, sc.beta, S.red, A.active_cnt);
-        }
-        if (!grid_barrier(A.bar, A.err)) return;
+        if (!grid_barrier_stop(A.bar, A.err, A.active_cnt, &s_stop)) return;
     }
 }
 
@@ -395,18 +231,21 @@ __global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int
         if (rr <= st->tol2 * bb) {
             st->converged = 1;
             st->phase = kPhOutput;
-        } else if (st->outer >= st->max_outer || st->iters_total >= st->max_iters || st->status == kCgBreakdown) {
+        } else if (st->outer >= st->max_outer || st->iters_total >= st->max_iters || st->in.status == kCgBreakdown) {
             st->phase = kPhOutput;
         } else {
             st->outer += 1;
             st->scale = 1.0 / sqrt(rr);
-            st->first = 1;
-            st->done = 0;
-            st->status = 0;
-            st->iters = 0;
-            st->alpha = 0.0;
-            st->beta = 0.0;
-            st->gamma = 0.0;
+            CgState &in = st->in;
+            in.rz = in.pq = in.alpha = in.beta = in.rr = in.rr0 = in.stop_rr = 0.0;
+            in.tol2 = st->inner_tol2;
+            in.iters = 0;
+            in.max_iters = st->max_iters - st->iters_total;
+            in.done = 0;
+            in.status = kCgRunning;
+            in.first = 1;
+            in.free_run = 0;
+            in.cnt_a = in.cnt_b = 0;
             st->phase = kPhInnerInit;
         }
     }
@@ -434,6 +273,7 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
     const int64_t i0 = (int64_t)tk.y * kVecLen;
     const int64_t i1 = i0 + kVecLen < m.n_pad ? i0 + kVecLen : m.n_pad;
     DotD acc;
+    // the tasks cover max(n_pad, partial slots); vector steps stop at n_pad
     if (OP == kPrepare) {
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             double bv = 0.0, xv = 0.0;
@@ -447,16 +287,25 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
             acc.add_prod(bv, bv);
         }
     } else if (OP == kInnerInit) {
+        // pass 0 reads buffer 0: r = r64 / ||r64||, x = p = s = w = 0 and
+        // the shared-node partial sums of w = 0
+        float *r = M.v.r[0], *x = M.v.x[0], *p = M.v.p[0], *sv = M.v.s[0], *w = M.v.w[0], *part = M.v.part[0];
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            M.r[i] = (float)(M.r64[i] * scale);
-            M.x[i] = 0.f;
-            M.p[i] = 0.f;
-            M.s[i] = 0.f;
-            M.w[i] = 0.f;
+            r[i] = (float)(M.r64[i] * scale);
+            x[i] = 0.f;
+            p[i] = 0.f;
+            sv[i] = 0.f;
+            w[i] = 0.f;
         }
+        const int64_t j1 = i0 + kVecLen < M.n_part ? i0 + kVecLen : M.n_part;
+        for (int64_t j = i0 + threadIdx.x; j < j1; j += blockDim.x) part[j] = 0.f;
     } else if (OP == kCorrect) {
         const double inv = 1.0 / scale;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) M.x64[i] += (double)M.x[i] * inv;
+        __shared__ int s_par;
+        if (threadIdx.x == 0) s_par = cg1_parity(M.st->in.first, M.st->in.iters);
+        __syncthreads();
+        const float *x = s_par ? M.v.x[1] : M.v.x[0];
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) M.x64[i] += (double)x[i] * inv;
     } else {  // kFinish
         for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x)
             if (j < m.n_nodes) M.x_user[j] = M.x64[M.new_of_old[j]];
@@ -526,19 +375,17 @@ static int ensure_batch_ws(ps_mesh *m) {
     if (rc != PS_OK) return rc;
     BatchMeshWs *w = new BatchMeshWs();
     const int64_t np = m->dev.n_pad;
+    const int64_t span = std::max<int64_t>(np, m->prep.sh_total);
     w->n_segs = (int)std::max<int64_t>(1, (m->prep.n_shared + kSegLen - 1) / kSegLen);
-    w->n_vt = (int)((np + kVecLen - 1) / kVecLen);
+    w->n_vt = (int)((span + kVecLen - 1) / kVecLen);
     void *p;
     auto A = [&](void **dst, size_t bytes) -> int {
         int r = dalloc(m->ctx, dst, bytes, w->allocs);
         if (r == PS_OK) cudaMemset(*dst, 0, bytes);
         return r;
     };
-    rc = A(&p, np * 4);
-    w->s32 = (float *)p;
-    if (rc == PS_OK) rc = A(&p, np * 4), w->w32 = (float *)p;
-    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 3 * sizeof(float2)), w->dots = (float2 *)p;
-    if (rc == PS_OK) rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 8), w->dots64 = (double *)p;
+    rc = A(&p, (size_t)(m->dev.n_chunks + w->n_segs) * 8);
+    w->dots64 = (double *)p;
     if (rc == PS_OK) rc = A(&p, (size_t)w->n_vt * 8), w->vdots = (double *)p;
     if (rc != PS_OK) {
         dfree_all(m->ctx, w->allocs);
@@ -550,9 +397,11 @@ static int ensure_batch_ws(ps_mesh *m) {
 }
 
 int64_t batch_ws_bytes(const ps_mesh *m) {
-    // vectors of ps_mesh::ws and BatchMeshWs (an estimate for admission)
+    // vectors of ps_mesh::ws and BatchMeshWs (an estimate for admission):
+    // FP64 x b r p q, FP32 x r p q (two buffers each), s (two), D^-1 copies
+    // of the unpreconditioned mode, partial sums, per-chunk dots
     const int64_t np = m->dev.n_pad, sh = m->prep.sh_total;
-    return np * (5 * 8 + 6 * 4) + sh * 12 + (int64_t)m->dev.n_chunks * 40;
+    return np * (5 * 8 + 12 * 4) + sh * 16 + (int64_t)m->dev.n_chunks * 48;
 }
 
 void batched_release_mesh(ps_mesh *m) {
@@ -586,6 +435,10 @@ static SmemLayout max_layout(const std::vector<ps_mesh *> &meshes, bool fp64) {
 
 int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, BatchPlan &plan) {
     batch_plan_free(plan);
+    if (n < 1 || n > kMaxBatch) {
+        ps_set_last_error("batch: between 1 and 4096 meshes per batch");
+        return PS_EINVAL;
+    }
     plan.ctx = ctx;
     plan.meshes.assign(meshes, meshes + n);
     plan.epoch_iters = epoch_iters > 0 ? epoch_iters : 256;
@@ -606,13 +459,22 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
         BMesh &B = plan.h_meshes[i];
         std::memset(&B, 0, sizeof(B));
         B.d = m->dev;
-        B.x = m->ws.x32;
-        B.r = m->ws.r32;
-        B.p = m->ws.p32;
-        B.s = w->s32;
-        B.w = w->w32;
-        B.part = m->ws.part32;
-        B.dots = w->dots;
+        const Workspace &ws = m->ws;
+        B.v.x[0] = ws.x32;
+        B.v.x[1] = ws.x32b;
+        B.v.r[0] = ws.r32;
+        B.v.r[1] = ws.r32b;
+        B.v.s[0] = ws.s32a;
+        B.v.s[1] = ws.s32b;
+        B.v.p[0] = ws.p32;
+        B.v.p[1] = ws.p32b;
+        B.v.w[0] = ws.q32;
+        B.v.w[1] = ws.q32b;
+        B.v.part[0] = ws.part32;
+        B.v.part[1] = ws.part32b;
+        B.v.dinv = m->dev.dinv32;
+        B.v.dots = reinterpret_cast<float2 *>(ws.dots1);
+        B.n_part = m->prep.sh_total;
         B.x64 = m->ws.x64;
         B.b64 = m->ws.b64;
         B.r64 = m->ws.r64;
@@ -645,8 +507,9 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
     std::memset(plan.h_st, 0, (size_t)n * sizeof(BState));
     plan.L32 = max_layout(plan.meshes, false);
     plan.L64 = max_layout(plan.meshes, true);
+    plan.pcg_smem = plan.L32.total + (uint32_t)n * (sizeof(float2) + sizeof(int));
     int per_sm = 0;
-    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, plan.L32.total));
+    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, plan.pcg_smem));
     if (rc != PS_OK) return rc;
     if (per_sm < 1) {
         ps_set_last_error("batch: shared-memory layout too large for the persistent kernel");
@@ -678,7 +541,7 @@ int batch_upload_states(BatchPlan &plan, cudaStream_t s) {
     const int n = (int)plan.meshes.size();
     // meshes carried over mid inner solve are counted as active
     int act = 0;
-    for (int i = 0; i < n; ++i) act += plan.h_st[i].phase == kPhInner && !plan.h_st[i].done;
+    for (int i = 0; i < n; ++i) act += plan.h_st[i].phase == kPhInner && !plan.h_st[i].in.done;
     plan.h_active = act;
     int *active = (int *)(plan_bar(plan) + 128);
     cudaError_t e = cudaMemcpyAsync(plan.d_meshes, plan.h_meshes.data(), n * sizeof(BMesh), cudaMemcpyHostToDevice, s);
@@ -703,9 +566,8 @@ static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
     PcgArgs A;
     A.meshes = plan.d_meshes;
     A.t1 = plan.d_t1;
-    A.t2 = plan.d_t2;
     A.n_t1 = plan.n_t1;
-    A.n_t2 = plan.n_t2;
+    A.n_meshes = n;
     A.bar = bar;
     A.active_cnt = active;
     A.err = plan.ctx->d_err;
@@ -716,7 +578,7 @@ static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(plan.grid_pcg);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = plan.L32.total;
+    cfg.dynamicSmemBytes = plan.pcg_smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -779,7 +641,7 @@ void batch_info(const BatchPlan &plan, int i, ps_solve_info *inf) {
     std::memset(inf, 0, sizeof(*inf));
     const double bb = st.bb > 0 ? st.bb : 1.0;
     inf->converged = st.converged;
-    inf->status = st.converged ? PS_OK : (st.status == kCgBreakdown ? PS_EBREAKDOWN : PS_ENOTCONV);
+    inf->status = st.converged ? PS_OK : (st.in.status == kCgBreakdown ? PS_EBREAKDOWN : PS_ENOTCONV);
     inf->iters_outer = st.outer + 1;
     inf->iters_inner = st.iters_total;
     inf->rel_res = std::sqrt(st.rr64 / bb);

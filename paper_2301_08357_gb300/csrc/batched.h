@@ -3,22 +3,25 @@
 //   * FP64 true residuals and node-range vector steps run as one launch over
 //     a task list covering every mesh of the batch;
 //   * the FP32 inner solves run in one cooperative persistent kernel whose
-//     blocks walk (mesh, chunk) and (mesh, shared-node segment) task lists
-//     with grid barriers between the two phases of each iteration.
-// The inner solver is preconditioned CG in the one-reduction form of
-// Chronopoulos and Gear (s = A p carried by recurrence, w = A u computed,
-// gamma = r.u, delta = w.u and rho = r.r reduced together once per
-// iteration).  Each mesh's arithmetic and reduction order depend only on that
-// mesh, so a mesh gives bitwise the same result alone and in any batch.
+//     blocks walk the (mesh, chunk) task list once per CG iteration, with one
+//     grid barrier per iteration.
+// The inner solver is the fused one-reduction PCG pass of cg1.cuh
+// (Chronopoulos and Gear): each chunk updates its nodes from the previous
+// pass's double-buffered vectors, applies A, and contributes its share of
+// gamma, delta and rho; the last chunk of a mesh to finish advances that
+// mesh's scalars.  Each mesh's arithmetic and reduction order depend only on
+// that mesh, so a mesh gives bitwise the same result alone and in any batch.
 #pragma once
 #include <vector>
 
 #include "internal.h"
+#include "cg1.cuh"
 
 namespace ps {
 
-constexpr int kSegLen = 256;    // shared nodes per phase-2 task (one per thread)
-constexpr int kVecLen = 8192;   // nodes per node-range task
+constexpr int kSegLen = 256;    // shared nodes per residual segment task (one per thread)
+constexpr int kVecLen = 8192;   // nodes (and partial slots) per node-range task
+constexpr int kMaxBatch = 4096; // meshes per plan (per-block scalar cache in shared memory)
 
 // Per-mesh phase of a batched solve; every kernel of an epoch acts only on the
 // meshes in its phase, and the last block to finish a mesh's part advances it.
@@ -34,21 +37,17 @@ enum BPhase : int {
 };
 
 struct BState {
-    // inner FP32 solve (one-reduction PCG)
-    double gamma, delta, rho, rho0, stop2, alpha, beta, inner_tol2;
+    CgState in;                    // inner FP32 solve (fused pass, cg1.cuh)
     // outer FP64 defect correction
-    double rr64, bb, scale, tol2;
-    long long iters, max_iters, iters_total;
-    int first, done, status, phase;
-    int outer, max_outer, converged, pad0;
-    unsigned int cnt2, cnt_r, cnt_v, pad1;
+    double rr64, bb, scale, tol2, inner_tol2;
+    long long iters_total, max_iters;
+    int phase, outer, max_outer, converged;
+    unsigned int cnt_r, cnt_v, pad0, pad1;
 };
 
 struct BMesh {
     MeshDev d;
-    float *x, *r, *p, *s, *w;      // FP32 inner vectors
-    float *part;                   // shared-node partial sums (FP32)
-    float2 *dots;                  // [(n_chunks + n_segs) * 3] double-float partials
+    CG1Vec v;                      // double-buffered FP32 inner vectors, per-chunk dots
     double *x64, *b64, *r64;
     double *part64;                // shared-node partial sums (FP64)
     double *dots64;                // [n_chunks + n_segs]
@@ -57,9 +56,9 @@ struct BMesh {
     double *x_user;
     const int32_t *old_of_new, *new_of_old;
     int n_segs, n_vt;
+    int64_t n_part;                // partial-sum slots (sh_total)
     BState *st;
 };
-
 
 // Host-side batch plan: device arrays of meshes and task lists, the per-mesh
 // states (device + pinned host mirror) and the captured epoch graph.
@@ -68,12 +67,13 @@ struct BatchPlan {
     std::vector<ps_mesh *> meshes;
     std::vector<DevAlloc> allocs;
     BMesh *d_meshes = nullptr;
-    int2 *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr;
+    int2 *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr;   // chunk, shared-segment, node-range tasks
     int n_t1 = 0, n_t2 = 0, n_t3 = 0;
     BState *d_st = nullptr;        // [n] contiguous device states
     BState *h_st = nullptr;        // [n] pinned host mirror (written by the epoch)
     std::vector<BMesh> h_meshes;
     SmemLayout L32, L64;
+    uint32_t pcg_smem = 0;         // L32 plus the per-block scalar cache
     int grid_pcg = 0;
     int epoch_iters = 256;
     int h_active = 0;
@@ -82,11 +82,9 @@ struct BatchPlan {
     bool graph_ok = true;
 };
 
-// Per-mesh batch workspace (extra FP32 vectors beyond ps_mesh::ws).
+// Per-mesh batch workspace beyond ps_mesh::ws (FP64 reduction partials).
 struct BatchMeshWs {
     std::vector<DevAlloc> allocs;
-    float *s32 = nullptr, *w32 = nullptr;
-    float2 *dots = nullptr;
     double *dots64 = nullptr, *vdots = nullptr;
     int n_segs = 0, n_vt = 0;
 };
