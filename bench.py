@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="c4/c5: library default chunks, no batch autotuning")
     ap.add_argument("--launch-list", action="store_true",
                     help="c1/c2/c3: warm-up and timed solves alone (no e2e pass, no kernel timing, no CPU "
                          "baseline), for a profiler's launch list; the line then has no roofline or e2e")
@@ -458,6 +459,16 @@ def run_single(args, which):
     P.ps_ctx_destroy(ctx)
 
 
+def batch_chunk(args, autotune, P, ctx, cases):
+    """Chunk size for the batched / served workloads: --chunk if given, else the
+    batch autotuner on every 8th case (outside any timed region)."""
+    if args.chunk or args.no_tune:
+        return args.chunk, None
+    sample = cases[::8]
+    res = autotune.tune_batch(P, ctx, sample)
+    return res["chunk_elems"], {"sample_meshes": len(sample), "table": res["table"]}
+
+
 def run_batch(args):
     """c4: 256 independent meshes (half 2D, half 3D, 2k-200k nodes) in one batched solve."""
     import contextlib
@@ -467,12 +478,14 @@ def run_batch(args):
         build()
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
+    from paper_2301_08357_gb300 import autotune
     ctx = P.ps_ctx_create(0)
     meshes, bs, xs, n_free = [], [], [], []
     t0 = time.perf_counter()
-    for i in range(args.meshes):
-        c = S.make_batch_case(i, lo=2e3 * args.size_scale, hi=2e5 * args.size_scale)
-        m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=args.chunk)
+    cases = [S.make_batch_case(i, lo=2e3 * args.size_scale, hi=2e5 * args.size_scale) for i in range(args.meshes)]
+    chunk, tune = batch_chunk(args, autotune, P, ctx, cases)
+    for c in cases:
+        m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=chunk)
         P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
         meshes.append(m)
         bs.append(torch.as_tensor(c.b, device="cuda"))
@@ -507,6 +520,8 @@ def run_batch(args):
            "config": {"workload": "c4_batch_%d_meshes" % args.meshes, "n_free_total": int(sum(n_free)),
                       "max_rel_res": max(inf.rel_res for inf in infos),
                       "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
+                      "iters_inner_max": int(max(inf.iters_inner for inf in infos)),
+                      "chunk_elems": chunk, "chunk_tuning": tune,
                       "setup_s": setup_s, "l2": "flushed between steps (256 MB write)"},
            "solves_per_s": 1e3 * args.meshes * args.steps / tot}
     print(json.dumps(out))
@@ -525,13 +540,15 @@ def run_served(args):
         build()
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
+    from paper_2301_08357_gb300 import autotune
     ctx = P.ps_ctx_create(0)
-    cases, meshes = [], []
-    for c in range(args.cases):
-        cs = S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
-        m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet, chunk_elems=args.chunk)
+    meshes = []
+    cases = [S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
+             for c in range(args.cases)]
+    chunk, tune = batch_chunk(args, autotune, P, ctx, cases)
+    for cs in cases:
+        m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet, chunk_elems=chunk)
         P.ps_coeff_set(m, cs.alpha, cs.beta, cs.dt2)
-        cases.append(cs)
         meshes.append(m)
     nodes_total = sum(c.n_nodes for c in cases)
 
@@ -624,7 +641,7 @@ def run_served(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
            "data": "synthetic",
            "config": {"workload": "c5_served_%d_cases_x_%d_steps" % (args.cases, args.case_steps),
-                      "nodes_total": nodes_total},
+                      "nodes_total": nodes_total, "chunk_elems": chunk, "chunk_tuning": tune},
            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
            "served_vs_fp64_single_solves_per_s": sat["solves_per_s"] / singles[0]["solves_per_s"],
            "runs": runs, "single_solves": singles}

@@ -1,5 +1,6 @@
 """Autotuner for the solver's free parameters (chunk size, operator-kernel
-variant, single-solve engine, inner tolerance of the mixed solver).
+variant, single-solve engine, inner tolerance of the mixed solver; chunk size
+of meshes solved in batches).
 
 It measures through the C ABI only: each candidate mesh layout is uploaded,
 the FP32 CG kernels are timed with ps_profile_kernel (CUDA events on the
@@ -85,3 +86,53 @@ def tune(P, ctx, case, stream=None, chunks=CHUNKS, pipelines=PIPELINES, inner_to
     solves.sort(key=lambda r: r["solve_ms"])
     return {"chunk_elems": best["chunk_elems"], "pipeline": best["pipeline"], "engine": best["engine"],
             "inner_tol": solves[0]["inner_tol"] if solves else 1e-4, "table": table, "solves": solves}
+
+
+BATCH_CHUNKS = (0, 768, 1536)
+
+
+def tune_batch(P, ctx, cases, stream=None, chunks=BATCH_CHUNKS, reps=2, opts=None):
+    """Chunk size for meshes that are solved together (ps_batch_solve or the
+    serving loop): there the other meshes fill the GPU, so larger chunks (fewer
+    shared nodes, less redundant work per pass) can beat the single-solve
+    default.  `cases` is a sample of the batch (synthetic.Case objects); each
+    candidate uploads the sample, warms up once and keeps the best of `reps`
+    timed batch solves.  Returns {'chunk_elems', 'table'}; 0 means the library
+    default.  Candidates whose layout does not fit are skipped."""
+    import torch
+
+    opts = opts if opts is not None else P.make_opts(tol=1e-10)
+    table = []
+    for ce in chunks:
+        meshes = []
+        try:
+            for c in cases:
+                m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=ce)
+                meshes.append(m)
+                P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
+        except P.PressureError:
+            for m in meshes:
+                P.ps_mesh_free(m)
+            continue
+        bs = [torch.as_tensor(c.b, device="cuda") for c in cases]
+        xs = [torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda") for c in cases]
+        ts = []
+        try:
+            for r in range(reps + 1):
+                for x in xs:
+                    x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, _ = P.ps_batch_solve(meshes, bs, xs, opts, stream)
+                torch.cuda.synchronize()
+                if st == P.PS_OK:
+                    ts.append(time.perf_counter() - t0)
+        finally:
+            for m in meshes:
+                P.ps_mesh_free(m)
+        if len(ts) > 1:
+            table.append({"chunk_elems": ce, "batch_ms": 1e3 * float(np.min(ts[1:]))})
+    if not table:
+        raise RuntimeError("autotune: no candidate chunk size could be measured")
+    table.sort(key=lambda r: r["batch_ms"])
+    return {"chunk_elems": table[0]["chunk_elems"], "table": table}

@@ -107,7 +107,14 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
     int *c_par = reinterpret_cast<int *>(c_ab + A.n_meshes);               // [n_meshes], -1 = idle
     __shared__ int s_stop;
     __shared__ bool s_last;
+    // the current task's mesh descriptor and buffers, copied into shared
+    // memory: read through a global reference, every pointer would be
+    // reloaded after each global store the pass makes (possible aliasing)
+    __shared__ __align__(16) MeshDev s_md;
+    __shared__ __align__(16) CG1Vec s_v;
+    __shared__ int s_mesh;
     if (threadIdx.x == 0) {
+        s_mesh = -1;
         mbar_init(S.bar, 1);
         fence_mbar_init();
         // no mesh leaves the inner phase before this launch's first pass, so
@@ -132,11 +139,24 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
             if (par < 0) continue;                 // block-uniform
             const BMesh &M = A.meshes[tk.x];
             const float2 ab = c_ab[tk.x];
+            if (s_mesh != tk.x) {                  // block-uniform
+                __syncthreads();                   // the previous task's readers are done
+                constexpr int nd = sizeof(MeshDev) / 4, nv = sizeof(CG1Vec) / 4;
+                static_assert(sizeof(MeshDev) % 4 == 0 && sizeof(CG1Vec) % 4 == 0, "word copy");
+                const uint32_t *src_d = reinterpret_cast<const uint32_t *>(&M.d);
+                const uint32_t *src_v = reinterpret_cast<const uint32_t *>(&M.v);
+                for (int k = threadIdx.x; k < nd + nv; k += blockDim.x) {
+                    if (k < nd) reinterpret_cast<uint32_t *>(&s_md)[k] = src_d[k];
+                    else reinterpret_cast<uint32_t *>(&s_v)[k - nd] = src_v[k - nd];
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) s_mesh = tk.x;
+            }
             DotF acc[3];
-            if (M.d.dim == 3)
-                chunk_cg1f<3>(M.d, cg1_pass(M.v, par), M.v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
+            if (s_md.dim == 3)
+                chunk_cg1f<3>(s_md, cg1_pass(s_v, par), s_v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
             else
-                chunk_cg1f<2>(M.d, cg1_pass(M.v, par), M.v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
+                chunk_cg1f<2>(s_md, cg1_pass(s_v, par), s_v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
             if (failed) return;
             double out[3];
             out[0] = block_sum(acc[0], S.red);

@@ -35,3 +35,33 @@ def test_autotune_returns_working_parameters():
         P.ps_mesh_free(m)
     finally:
         P.ps_ctx_destroy(ctx)
+
+
+def test_batch_autotune_picks_a_measured_chunk():
+    import torch
+    from paper_2301_08357_gb300 import autotune, build
+    build.build()
+    from paper_2301_08357_gb300 import pressure as P
+    cases = [S.make_batch_case(i, lo=2e3, hi=6e3) for i in range(4)]
+    ctx = P.ps_ctx_create(0)
+    try:
+        res = autotune.tune_batch(P, ctx, cases, chunks=(0, 768), reps=1)
+        assert res["chunk_elems"] in (0, 768)
+        assert {r["chunk_elems"] for r in res["table"]} == {0, 768}
+        assert all(r["batch_ms"] > 0 for r in res["table"])
+        # the chosen layout solves the batch to the gate
+        meshes = [P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=res["chunk_elems"])
+                  for c in cases]
+        for m, c in zip(meshes, cases):
+            P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
+        bs = [torch.as_tensor(c.b, device="cuda") for c in cases]
+        xs = [torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda") for c in cases]
+        st, infos = P.ps_batch_solve(meshes, bs, xs)
+        assert st == P.PS_OK
+        for c, x in zip(cases, xs):
+            A = oracle.PressureMatrix.from_case(c)
+            assert A.residual(c.b, x.cpu().numpy()) <= 1.05e-10
+        for m in meshes:
+            P.ps_mesh_free(m)
+    finally:
+        P.ps_ctx_destroy(ctx)
