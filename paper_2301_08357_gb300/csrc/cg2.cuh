@@ -61,8 +61,11 @@ struct Cg2Args {
     CgState *st;
 };
 
-// K1: one block per chunk.
-template <int D, typename T>
+// K1: one block per chunk.  PRE: fetch the element phase's beta*dt^2 and the
+// first shared nodes' partial-sum destinations into registers before the
+// staging wait (FP32; costs registers, so it is used where shared memory, not
+// registers, limits the blocks per SM).
+template <int D, typename T, bool PRE = false>
 __global__ void __launch_bounds__(256) k_cg2_chunks(MeshDev m, Cg2Args<T> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const SmemLayout &L = (sizeof(T) == 4) ? m.sm32 : m.sm64;
@@ -82,44 +85,76 @@ __global__ void __launch_bounds__(256) k_cg2_chunks(MeshDev m, Cg2Args<T> a) {
     stage_issue<T>(m, cd, S);
     const T beta = (T)s_beta;
     const int n_loc = cd.n_loc, n_int = cd.n_int;
-    T vin[4];
+    // Every gather runs while the bulk copies are in flight: shared-node ids
+    // come from sh_info in global memory (not from the staged copy) and S.val
+    // is not a staged region.  No Dirichlet mask is needed: D^-1 = 0 and
+    // r = 0 on Dirichlet nodes and p starts at 0, so p stays 0 there.  Loads
+    // of four nodes are issued before any store (the stores to p could alias
+    // them).
+    // The element phase's beta*dt^2 values and the partial-sum destinations
+    // of the thread's first shared nodes are fetched here as well.
+    BdPrefetch<T> bdp;
+    if constexpr (PRE) prefetch_bd<T>(m, cd, bdp);
+    int dst[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int l = threadIdx.x + k * blockDim.x;
-        vin[k] = T(0);
-        if (l < n_int) {
-            const int g = cd.int_begin + l;
-            vin[k] = cg_dir(a.dinv[g], a.r[g], beta, a.p[g]);
+        dst[k] = (PRE && l >= n_int && l < n_loc) ? m.sh_dest[cd.sh_off + (l - n_int)] : -1;
+    }
+    for (int l0 = threadIdx.x; l0 < n_loc; l0 += 4 * blockDim.x) {
+        int gg[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * blockDim.x;
+            gg[k] = l < n_int ? cd.int_begin + l : (l < n_loc ? m.sh_info[cd.sh_off + (l - n_int)].x : -1);
+        }
+        T dv[4], rv[4], pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dv[k] = rv[k] = pv[k] = T(0);
+            if (gg[k] >= 0) {
+                dv[k] = a.dinv[gg[k]];
+                rv[k] = a.r[gg[k]];
+                pv[k] = a.p[gg[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * blockDim.x;
+            if (gg[k] >= 0) {
+                const T v = cg_dir(dv[k], rv[k], beta, pv[k]);
+                S.val[l] = v;
+                if (l < n_int) a.p[gg[k]] = v;
+            }
         }
     }
     uint32_t ph = 0;
-    if (!stage_wait<T>(m, S, ph)) return;
-    auto finish = [&](int l, T v) {
-        if (is_dirichlet(S.node[l].w)) v = T(0);
-        if (l < n_int) a.p[cd.int_begin + l] = v;
-        S.val[l] = v;
-    };
-    auto fetch = [&](int l) -> T {
-        const int g = l < n_int ? cd.int_begin + l : S.shid[l - n_int];
-        return cg_dir(a.dinv[g], a.r[g], beta, a.p[g]);
-    };
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int l = threadIdx.x + k * blockDim.x;
-        if (l < n_loc) finish(l, l < n_int ? vin[k] : fetch(l));
-    }
-    for (int l = threadIdx.x + 4 * blockDim.x; l < n_loc; l += blockDim.x) finish(l, fetch(l));
-    __syncthreads();
-    patches_eval<D, T, false>(m, cd, S);
+    if (!stage_wait<T>(m, S, ph)) return;   // also the barrier for S.val
+    if constexpr (PRE)
+        patches_eval_pre<D, T>(m, cd, S, bdp);
+    else
+        patches_eval<D, T, false>(m, cd, S);
     typename DotOf<T>::type acc;
-    for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
+    auto emit = [&](int l, int d) {
         T s = node_sum(S, l);
         acc.add_prod(S.val[l], s);                 // element-wise p^T A_e p over the chunk
         if (is_dirichlet(S.node[l].w)) s = T(0);
         if (l < n_int)
             a.q[cd.int_begin + l] = s;
         else
-            a.partial[m.sh_dest[cd.sh_off + (l - n_int)]] = s;
+            a.partial[d] = s;
+    };
+    if constexpr (PRE) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = threadIdx.x + k * blockDim.x;
+            if (l < n_loc) emit(l, dst[k]);
+        }
+        for (int l = threadIdx.x + 4 * blockDim.x; l < n_loc; l += blockDim.x)
+            emit(l, l < n_int ? -1 : m.sh_dest[cd.sh_off + (l - n_int)]);
+    } else {
+        for (int l = threadIdx.x; l < n_loc; l += blockDim.x)
+            emit(l, l < n_int ? -1 : m.sh_dest[cd.sh_off + (l - n_int)]);
     }
     const double v = block_sum(acc, S.red);
     if (threadIdx.x == 0) {

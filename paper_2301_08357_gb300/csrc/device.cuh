@@ -304,18 +304,9 @@ __device__ __forceinline__ void elem_diag_2d(const N4 &p0, const N4 &p1, const N
 __device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }
 
-template <int D, typename T, typename N4, bool DIAG>
-__device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const T *__restrict__ s_val,
-                                           const uint16_t *__restrict__ rec, const T *__restrict__ bdt2,
-                                           T *__restrict__ out) {
-    // the 24-byte record as three 8-byte loads: [m, a, b, r0], [r1..r4], [r5, r6, -, -]
-    const ushort4 q0 = reinterpret_cast<const ushort4 *>(rec)[0];
-    const ushort4 q1 = reinterpret_cast<const ushort4 *>(rec)[1];
-    const ushort4 q2 = reinterpret_cast<const ushort4 *>(rec)[2];
-    const int pm = q0.x;
-    const int ring[7] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
-    // beta*dt^2 of the patch's elements: one vector load each, all up front
-    T bd[kPatchMax];
+// beta*dt^2 of a patch's elements: vector loads, all up front.
+template <typename T>
+__device__ __forceinline__ void load_bd(const T *__restrict__ bdt2, T (&bd)[kPatchMax]) {
     if (sizeof(T) == 4) {
         const float2 *b2 = reinterpret_cast<const float2 *>(bdt2);
 #pragma unroll
@@ -333,6 +324,18 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
             bd[2 * k + 1] = (T)v.y;
         }
     }
+}
+
+template <int D, typename T, typename N4, bool DIAG>
+__device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const T *__restrict__ s_val,
+                                           const uint16_t *__restrict__ rec, const T (&bd)[kPatchMax],
+                                           T *__restrict__ out) {
+    // the 24-byte record as three 8-byte loads: [m, a, b, r0], [r1..r4], [r5, r6, -, -]
+    const ushort4 q0 = reinterpret_cast<const ushort4 *>(rec)[0];
+    const ushort4 q1 = reinterpret_cast<const ushort4 *>(rec)[1];
+    const ushort4 q2 = reinterpret_cast<const ushort4 *>(rec)[2];
+    const int pm = q0.x;
+    const int ring[7] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
     const int ia = q0.y;
     const N4 A = s_node[ia];
     const T va = DIAG ? T(0) : s_val[ia];

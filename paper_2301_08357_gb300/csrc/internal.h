@@ -92,6 +92,7 @@ struct ps_mesh {
     int pipe_grid = 0;                 // its persistent grid (0 = not used)
     int pipeline = 0;                  // ps_mesh_opts::pipeline
     int update_bps = 0;                // ps_mesh_opts::update_blocks_per_sm
+    bool k1_pre = false;               // FP32 operator kernel variant (beta prefetch)
     bool coeff_ok = false, alpha_set = false;
     double dt2 = 0.0;
     ps::Workspace ws;

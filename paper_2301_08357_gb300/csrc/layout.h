@@ -27,6 +27,7 @@ constexpr int kIncPad = 8;       // incidence segments padded to 8 u16
 constexpr int kIncpPad = 8;      // incidence-pointer segments padded to 8 u16
 constexpr int kShPad = 4;        // shared-id segments padded to 4 int32
 constexpr int kMaxChunkPatches = 65535 / kPatchSlots;  // slot ids fit in u16
+constexpr int kChunkThreads = 256;  // threads of a block that processes a chunk
 
 // Elements of a chunk are grouped into "patches": the elements around one
 // pivot (an edge (a, b) in 3D, a vertex a in 2D), ordered so that element j of

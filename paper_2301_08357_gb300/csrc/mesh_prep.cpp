@@ -202,6 +202,19 @@ void build_patches(int dim, int n, const std::vector<std::array<int, 4>> &lc, st
 
 }  // namespace
 
+// Order the patches of a chunk for the kernels' assignment (patch q is
+// evaluated by thread q mod kChunkThreads, in round q / kChunkThreads): largest
+// patches first, every other round reversed, so that the element counts of
+// the threads of a block are close and the block waits less at the barrier
+// that ends the element phase.
+static void balance_patches(std::vector<PatchRec> &p) {
+    std::stable_sort(p.begin(), p.end(), [](const PatchRec &x, const PatchRec &y) { return x.m > y.m; });
+    for (size_t r = 1; r * kChunkThreads < p.size(); r += 2) {
+        const size_t b = r * kChunkThreads, e = std::min(p.size(), b + kChunkThreads);
+        std::reverse(p.begin() + b, p.begin() + e);
+    }
+}
+
 std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
                          const int32_t *conn, const uint8_t *dirichlet, const PrepOptions &opt,
                          PrepMesh &m) {
@@ -417,6 +430,7 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
             for (int a = 0; a < nv; ++a) lc[e][a] = loc_of_new[m.new_of_old[conn[(int64_t)src * nv + a]]];
         }
         build_patches(dim, n_el, lc, patches);
+        balance_patches(patches);
         const int np = (int)patches.size();
         if (np > kMaxChunkPatches) return "internal: too many patches in a chunk";
         cd.patch_off = (int32_t)patch_off;

@@ -156,9 +156,49 @@ __device__ __forceinline__ void patches_eval(const MeshDev &m, const ChunkDesc &
     using N4 = typename NodeOf<T>::type;
     const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
     const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
-    for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x)
-        patch_eval<D, T, N4, DIAG>(S.node, S.val, S.pids + q * kPatchIds, g_bdt2 + q * kPatchMax,
-                                   S.contrib + q * kPatchSlots);
+    for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
+        T bd[kPatchMax];
+        load_bd(g_bdt2 + q * kPatchMax, bd);
+        patch_eval<D, T, N4, DIAG>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+    }
+    __syncthreads();
+}
+
+// The same with beta*dt^2 of the thread's first R patches loaded earlier
+// (prefetch_bd, before the staging wait): the element phase then starts
+// without a global-memory round trip.
+constexpr int kBdRounds = 3;
+template <typename T>
+struct BdPrefetch {
+    T v[kBdRounds][kPatchMax];
+};
+template <typename T>
+__device__ __forceinline__ void prefetch_bd(const MeshDev &m, const ChunkDesc &cd, BdPrefetch<T> &P) {
+    const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
+    const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
+#pragma unroll
+    for (int k = 0; k < kBdRounds; ++k) {
+        const int q = threadIdx.x + k * blockDim.x;
+        if (q < cd.n_patch) load_bd(g_bdt2 + q * kPatchMax, P.v[k]);
+    }
+}
+template <int D, typename T>
+__device__ __forceinline__ void patches_eval_pre(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S,
+                                                 const BdPrefetch<T> &P) {
+    using N4 = typename NodeOf<T>::type;
+#pragma unroll
+    for (int k = 0; k < kBdRounds; ++k) {
+        const int q = threadIdx.x + k * blockDim.x;
+        if (q < cd.n_patch)
+            patch_eval<D, T, N4, false>(S.node, S.val, S.pids + q * kPatchIds, P.v[k], S.contrib + q * kPatchSlots);
+    }
+    const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
+    const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
+    for (int q = threadIdx.x + kBdRounds * blockDim.x; q < cd.n_patch; q += blockDim.x) {
+        T bd[kPatchMax];
+        load_bd(g_bdt2 + q * kPatchMax, bd);
+        patch_eval<D, T, N4, false>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+    }
     __syncthreads();
 }
 

@@ -27,7 +27,7 @@ using namespace ps;
 
 namespace ps {
 
-const int kBlock = 256;
+const int kBlock = kChunkThreads;   // threads per block of every kernel
 static const int kUpdateBlocksPerSm = 2;   // update-kernel grid when occupancy is unknown
 
 static int sm_count_of(int dev) {
@@ -182,6 +182,8 @@ static int set_smem_attrs() {
     CK(set_max_dyn_smem(k_cg1_chunks<3>));
     CK(set_max_dyn_smem(k_cg2_chunks<2, float>));
     CK(set_max_dyn_smem(k_cg2_chunks<3, float>));
+    CK(set_max_dyn_smem(k_cg2_chunks<2, float, true>));
+    CK(set_max_dyn_smem(k_cg2_chunks<3, float, true>));
     CK(set_max_dyn_smem(k_cg2_chunks<2, double>));
     CK(set_max_dyn_smem(k_cg2_chunks<3, double>));
     CK(set_max_dyn_smem(k_cg2_chunks_pipe<2>));
@@ -368,6 +370,17 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         if (oe != cudaSuccess || m->pipe_L0.total > 200 * 1024) per_sm = 0;
         cudaGetLastError();
         m->pipe_grid = (per_sm > 0 && m->pipeline) ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
+    }
+    {
+        // FP32 operator kernel: prefetch beta*dt^2 into registers when that
+        // costs no resident blocks (shared memory is the limit: large chunks)
+        int o0 = 0, o1 = 0;
+        cudaError_t e0 = pm.dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_cg2_chunks<2, float>, kBlock, d.sm32.total)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_cg2_chunks<3, float>, kBlock, d.sm32.total);
+        cudaError_t e1 = pm.dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_cg2_chunks<2, float, true>, kBlock, d.sm32.total)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_cg2_chunks<3, float, true>, kBlock, d.sm32.total);
+        cudaGetLastError();
+        m->k1_pre = e0 == cudaSuccess && e1 == cudaSuccess && o1 > 0 && o1 >= o0;
     }
     {
         // auto: one full wave of the update kernel (its resident blocks per
@@ -659,8 +672,13 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
 // 15-55% slower than 256-thread blocks capped at 64 registers.)
 static void launch_k1_f32(ps_mesh *m, const Cg2Args<float> &a, cudaStream_t s) {
     const MeshDev &d = m->dev;
-    if (d.dim == 2) k_cg2_chunks<2, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
-    else k_cg2_chunks<3, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+    if (m->k1_pre) {
+        if (d.dim == 2) k_cg2_chunks<2, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+        else k_cg2_chunks<3, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+    } else {
+        if (d.dim == 2) k_cg2_chunks<2, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+        else k_cg2_chunks<3, float><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
+    }
 }
 
 static CG1Vec cg1_vec(ps_mesh *m) {
