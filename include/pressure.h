@@ -239,6 +239,52 @@ int ps_pressure_solve(ps_mesh *mesh, const double *b_dev, double *x_dev,
 /* Fill opts with the defaults. */
 void ps_solve_opts_default(ps_solve_opts *opts);
 
+/* ---- projection stage of one time step (Sections 3.3-3.5) ----------------
+ * The pressure solve inside its Picard loop, for the ideal gas of Section 2:
+ * first guesses H^{n+1,1}_e = gamma/(gamma-1) mean_k(P^n_k) / rho_e and
+ * (rho K)^{n+1,1}_e = |W~~_u,e|^2 / (2 rho_e) (Section 3.3); then n_picard
+ * iterations (Section 3.4) of
+ *   beta = H^{n+1,k} (operator and Jacobi diagonal updated on the device),
+ *   b_i = int (W~_E - (rho K)^{n+1,k}) phi_i - int alpha_h P^n_h phi_i
+ *         + dt int H^{n+1,k} W~~_u . grad phi_i          (weak problem)
+ *   solve A dP = b (ps_pressure_solve with opts->solve; warm start: dp_dev,
+ *         then the previous Picard iterate),
+ *   P = P^n + dP,  W_u = W~~_u - dt grad dP_h,  H and rho K from them.
+ * alpha is the mesh's nodal coefficient from ps_coeff_set (1/(gamma-1) for
+ * the ideal gas); the mesh's dt2 becomes dt*dt and its beta the H of the last
+ * solve.  Readings: the boundary term of the weak problem is taken as zero
+ * (closed walls: W_u . eta = 0 on the Neumann boundary); element values of
+ * the enthalpy use the vertex mean of the nodal pressure.
+ * All arrays are device memory in the caller's numbering / element order:
+ *   rho_dev  [n_elems]        density rho^{n+1} per element (> 0)
+ *   wu_dev   [n_elems * dim]  intermediate momentum W~~_u per element
+ *   we_dev   [n_elems]        intermediate total energy density W~_E per element
+ *   pn_dev   [n_nodes]        pressure P^n
+ *   dp_dev   [n_nodes]        in: first guess of dP, out: dP^{n+1} (0 on Dirichlet nodes)
+ *   p_dev    [n_nodes]        out: P^{n+1} = P^n + dP
+ *   wun_dev  [n_elems * dim]  out: W_u^{n+1}
+ *   h_dev    [n_elems]        out: H from P^{n+1} (the next Picard guess)
+ *   rhok_dev [n_elems]        out: (rho K) from W_u^{n+1}
+ * info: the last solve's record, with iters_inner / iters_outer / seconds
+ * summed over the Picard iterations (may be NULL).  Errors: PS_EINVAL (bad
+ * argument, or an enthalpy that is not positive and finite), PS_ESTATE
+ * (coefficients not set), and the statuses of ps_pressure_solve.  Device
+ * data for the element passes (coordinates, connectivity, node-to-element
+ * lists) is allocated on the first call and counted in the context budget. */
+typedef struct {
+    double gamma;            /* ratio of specific heats, > 1                     */
+    double dt;               /* time step, > 0                                   */
+    int32_t n_picard;        /* Picard iterations, 1..64 (the paper uses 2)       */
+    int32_t reserved[7];
+    ps_solve_opts solve;     /* options of every pressure solve                  */
+} ps_projection_opts;
+
+void ps_projection_opts_default(ps_projection_opts *opts);
+int ps_projection_step(ps_mesh *mesh, const ps_projection_opts *opts, const double *rho_dev,
+                       const double *wu_dev, const double *we_dev, const double *pn_dev, double *dp_dev,
+                       double *p_dev, double *wun_dev, double *h_dev, double *rhok_dev,
+                       ps_solve_info *info, void *stream);
+
 /* ---- batched solve: many independent meshes in one persistent kernel ----
  *   meshes  [n] mesh handles of one context (distinct, coefficients set)
  *   b_dev   [n] device pointers, each [n_nodes_i] double, caller numbering

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libpressure.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["pressure.cu", "batched.cu", "apply_noalloc.cu", "server.cu", "mesh_prep.cpp"]
+SOURCES = ["pressure.cu", "batched.cu", "apply_noalloc.cu", "server.cu", "projection.cu", "mesh_prep.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -59,6 +59,11 @@ int ensure_workspace(ps_mesh *m);
 template <typename T, int MODE>
 int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 
+int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s);
+
+// projection.cu
+void projection_release(ps_mesh *m);
+
 // batched.cu
 int batched_set_attrs();
 void batched_release_mesh(ps_mesh *m);
@@ -97,6 +102,10 @@ struct ps_mesh {
     double dt2 = 0.0;
     ps::Workspace ws;
     void *batch_ws = nullptr;   // owned by batched.cu
+    void *proj = nullptr;       // owned by projection.cu
+    std::vector<double> coords_host;   // [n_nodes * dim], caller's numbering
+    std::vector<double> alpha_host;    // [n_nodes], caller's numbering (last ps_coeff_set)
+    int64_t alpha_version = 0;
     int64_t launches = 0;       // kernel launches of the current call
 };
 

@@ -434,7 +434,9 @@ extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double 
         delete m;
         return rc;
     }
-    // host copies that are no longer needed
+    // coordinates in the caller's numbering (the projection stage's element
+    // passes); host copies that are no longer needed are dropped
+    m->coords_host.assign(coords, coords + n_nodes * dim);
     m->prep.loc_rel.clear();
     m->prep.loc_rel.shrink_to_fit();
     c->meshes.insert(m);
@@ -463,6 +465,7 @@ extern "C" void ps_mesh_free(ps_mesh *m) {
     cudaDeviceSynchronize();
     free_workspace(m);
     batched_release_mesh(m);
+    projection_release(m);
     dfree_all(c, m->allocs);
     c->meshes.erase(m);
     delete m;
@@ -569,7 +572,11 @@ extern "C" int ps_coeff_set(ps_mesh *m, const double *alpha, const double *beta,
     std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
     int rc = coeff_upload(m, alpha, beta, dt2);
-    if (rc == PS_OK) m->alpha_set = true;
+    if (rc == PS_OK) {
+        m->alpha_set = true;
+        m->alpha_host.assign(alpha, alpha + p.n_nodes);
+        m->alpha_version += 1;
+    }
     return rc;
 }
 
@@ -586,6 +593,31 @@ extern "C" int ps_coeff_set_beta(ps_mesh *m, const double *beta) {
 
 // ---------------------------------------------------------------- workspace
 namespace ps {
+
+// beta (caller's element order, device) -> beta*dt^2 per patch slot and the
+// Jacobi diagonal, on stream s without allocating or synchronising (the
+// projection stage updates the operator between Picard iterations).  The
+// caller holds the context mutex.
+int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s) {
+    RC(ensure_workspace(m));
+    const PrepMesh &p = m->prep;
+    MeshDev &d = m->dev;
+    const int64_t nslots = p.patch_total * kPatchMax;
+    k_set_beta<<<grid_for(nslots, m->ctx->sms), kBlock, 0, s>>>(nslots, m->d_elem_src, beta_dev, dt2,
+                                                                 const_cast<float *>(d.bdt2_32),
+                                                                 const_cast<double *>(d.bdt2_64));
+    VecArgs<double> a;
+    std::memset(&a, 0, sizeof(a));
+    a.partial = m->ws.part64;
+    if (d.dim == 2)
+        k_chunks<2, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+    else
+        k_chunks<3, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
+    k_shared<double, kDiag><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
+    CK(cudaGetLastError());
+    m->dt2 = dt2;
+    return PS_OK;
+}
 
 int ensure_workspace(ps_mesh *m) {
     Workspace &w = m->ws;

@@ -53,6 +53,11 @@ class ps_solve_opts(C.Structure):
                 ("engine", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
+class ps_projection_opts(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("dt", C.c_double), ("n_picard", C.c_int32),
+                ("reserved", C.c_int32 * 7), ("solve", ps_solve_opts)]
+
+
 class ps_solve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("converged", C.c_int32), ("iters_outer", C.c_int64),
                 ("iters_inner", C.c_int64), ("rel_res", C.c_double), ("bnorm", C.c_double),
@@ -107,6 +112,9 @@ SIGNATURES = {
     "ps_pressure_apply": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ps_pressure_apply_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp]),
     "ps_pressure_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(ps_solve_opts), C.POINTER(ps_solve_info), _vp]),
+    "ps_projection_opts_default": (None, [C.POINTER(ps_projection_opts)]),
+    "ps_projection_step": (C.c_int, [_vp, C.POINTER(ps_projection_opts), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp, C.POINTER(ps_solve_info), _vp]),
     "ps_solve_opts_default": (None, [C.POINTER(ps_solve_opts)]),
     "ps_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                  C.POINTER(ps_solve_opts), C.POINTER(ps_solve_info), _vp]),
@@ -259,6 +267,28 @@ def ps_pressure_solve(mesh, b_dev, x_dev, opts=None, stream=None):
     o = C.byref(opts) if opts is not None else None
     st = _lib.ps_pressure_solve(mesh, _dev(b_dev), _dev(x_dev), o, C.byref(info), _stream(stream))
     return _check(st, "ps_pressure_solve"), info
+
+
+def ps_projection_opts_default():
+    o = ps_projection_opts()
+    _lib.ps_projection_opts_default(C.byref(o))
+    return o
+
+
+def ps_projection_step(mesh, rho, wu, we, pn, dp, p_out, wu_out, h_out, rhok_out, gamma=1.4, dt=None,
+                       n_picard=2, solve_opts=None, stream=None):
+    """One time step's projection stage (device arrays, caller's numbering /
+    element order; dp is the first guess in and dP out).  Returns (status, info)."""
+    o = ps_projection_opts_default()
+    o.gamma = float(gamma)
+    o.dt = float(dt) if dt is not None else 0.0
+    o.n_picard = int(n_picard)
+    if solve_opts is not None:
+        o.solve = solve_opts
+    info = ps_solve_info()
+    st = _lib.ps_projection_step(mesh, C.byref(o), _dev(rho), _dev(wu), _dev(we), _dev(pn), _dev(dp), _dev(p_out),
+                                 _dev(wu_out), _dev(h_out), _dev(rhok_out), C.byref(info), _stream(stream))
+    return _check(st, "ps_projection_step"), info
 
 
 def ps_batch_solve(meshes, b_devs, x_devs, opts=None, stream=None):

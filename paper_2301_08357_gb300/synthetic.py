@@ -324,6 +324,7 @@ def shuffle_case(case: Case, seed: int = 12345) -> Case:
              case.alpha[inv], case.beta[q], case.dt2, case.b[inv], case.x0[inv],
              n=case.n, seed=case.seed, extra=dict(case.extra))
     c.extra["node_new_of_old"] = p
+    c.extra["elem_old_of_new"] = q
     return c
 
 
@@ -335,3 +336,49 @@ def case_by_name(name: str, n: int | None = None) -> Case:
     if name == "c3":
         return make_c3(160 if n is None else n)
     raise ValueError(name)
+
+
+def make_projection_case(dim: int = 3, n: int = 64, seed: int = 0, gamma: float = 1.4) -> Case:
+    """One time step's projection stage on a jittered unit square / Kuhn cube
+    (Dirichlet x = 0): ideal gas, alpha = 1/(gamma - 1) at every node, and
+    seeded smooth primal-element fields in ``extra``:
+      rho  [E]     1 + 0.2 s1(centroid) with s a unit-amplitude product of sines,
+      wu   [E, d]  a divergence-free vortex (Taylor-Green-like) of amplitude 1
+                   plus 5 % N(0,1) noise,
+      pn   [N]     1 + 0.05 s2(node) + 0.01 N(0,1),
+      we   [E]     mean(pn)/(gamma - 1) + |wu|^2/(2 rho) + 0.01 N(0,1),
+      gamma, dt    dt = 0.5 h / max |wu| (a flow-speed CFL, Section 3).
+    beta is a placeholder (the step sets it to the enthalpy); dt2 = dt^2."""
+    rng = np.random.default_rng(7000 + seed)
+    if dim == 2:
+        coords, conn = square_mesh(n)
+        coords = jitter_nodes(coords, n, 0.2, rng)
+    else:
+        coords, conn = kuhn_cube_mesh(n)
+        coords = jitter_nodes(coords, n, 0.15, rng)
+    N, E = coords.shape[0], conn.shape[0]
+    cen = coords[conn].mean(axis=1)
+    two_pi = 2.0 * np.pi
+    ph = rng.uniform(0.0, two_pi, size=(2, dim))
+    s1 = np.prod(np.sin(two_pi * cen + ph[0]), axis=1)
+    rho = 1.0 + 0.2 * s1
+    wu = np.zeros((E, dim))
+    x, y = cen[:, 0], cen[:, 1]
+    if dim == 2:
+        wu[:, 0] = np.sin(np.pi * x) * np.cos(np.pi * y)
+        wu[:, 1] = -np.cos(np.pi * x) * np.sin(np.pi * y)
+    else:
+        z = cen[:, 2]
+        wu[:, 0] = np.sin(np.pi * x) * np.cos(np.pi * y) * np.cos(np.pi * z)
+        wu[:, 1] = -np.cos(np.pi * x) * np.sin(np.pi * y) * np.cos(np.pi * z)
+    wu += 0.05 * rng.standard_normal((E, dim))
+    s2 = np.prod(np.cos(two_pi * coords + ph[1]), axis=1)
+    pn = 1.0 + 0.05 * s2 + 0.01 * rng.standard_normal(N)
+    rhok = 0.5 * (wu * wu).sum(axis=1) / rho
+    we = pn[conn].mean(axis=1) / (gamma - 1.0) + rhok + 0.01 * rng.standard_normal(E)
+    dt = 0.5 / n / float(np.abs(wu).max())
+    dirichlet = _dirichlet_x0(coords)
+    alpha = np.full(N, 1.0 / (gamma - 1.0))
+    return Case("projection_%dd_%d" % (dim, n), dim, coords, conn, dirichlet, alpha, np.ones(E), dt * dt,
+                np.zeros(N), np.zeros(N), n=n, seed=seed,
+                extra={"rho": rho, "wu": wu, "we": we, "pn": pn, "gamma": gamma, "dt": dt})
