@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "fused"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "projection"],
                     help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
                          "c4 = 256-mesh batch; c5 = served Poisson stream")
     ap.add_argument("--meshes", type=int, default=256, help="c4: meshes in the batch")
@@ -651,6 +651,111 @@ def run_served(args):
     P.ps_ctx_destroy(ctx)
 
 
+def run_projection(args):
+    """One time step's projection stage (ps_projection_step) on the 3D Kuhn cube
+    n^3 with seeded flow fields: first guesses, 2 Picard iterations of [operator
+    update, right-hand side, mixed-precision solve to 1e-10, post-projection].
+    Every step starts from dP = 0 (the same work each step)."""
+    import contextlib
+    import torch
+    from __graft_entry__ import build
+    with contextlib.redirect_stdout(sys.stderr):
+        build()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    n_pic = 2
+    case = S.make_projection_case(3, args.n)
+    e = case.extra
+    ctx = P.ps_ctx_create(0)
+    m = P.ps_mesh_upload(ctx, 3, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk)
+    P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+    stream = torch.cuda.current_stream()
+    N, E = case.n_nodes, case.n_elems
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    ins = [dev(e["rho"]), dev(e["wu"]), dev(e["we"]), dev(e["pn"])]
+    dp = torch.zeros(N, dtype=torch.float64, device="cuda")
+    outs = [torch.empty(N, dtype=torch.float64, device="cuda"), torch.empty(E * 3, dtype=torch.float64, device="cuda"),
+            torch.empty(E, dtype=torch.float64, device="cuda"), torch.empty(E, dtype=torch.float64, device="cuda")]
+    opts = P.make_opts(tol=1e-10)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        dp.zero_()
+        return P.ps_projection_step(m, *ins, dp, *outs, gamma=e["gamma"], dt=e["dt"], n_picard=n_pic,
+                                    solve_opts=opts, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    clocks = Clocks(0)
+    if not args.no_clocks:
+        clocks.start()
+    times, iters, launches = [], 0, 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st != P.PS_OK:
+            raise RuntimeError("projection step failed: %s" % P.ps_status_str(st))
+        times.append(e0.elapsed_time(e1))
+        iters += info.iters_inner + info.iters_outer
+        # solve launches + per Picard iteration: check, beta, diagonal (2), right-hand side, post (2); + first guess
+        launches += info.kernel_launches + 6 * n_pic + 1
+    clk = clocks.stop() if not args.no_clocks else None
+    tot = float(np.sum(times))
+    # end to end: host inputs copied in, outputs copied back, inside the timed region
+    h_in = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+            for a in (e["rho"], e["wu"], e["we"], e["pn"])]
+    h_out = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in [dp] + outs]
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d_, h_ in zip(ins, h_in):
+            d_.copy_(h_, non_blocking=True)
+        step()
+        for h_, d_ in zip(h_out, [dp] + outs):
+            h_.copy_(d_, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    stats = P.ps_mesh_get_stats(m)
+    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream,
+                           "projection_3d_kuhn_%d" % args.n)
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import projection as PJ
+        t0 = time.perf_counter()
+        ref = PJ.projection_step(3, case.coords, case.conn, case.dirichlet, case.alpha, e["rho"], e["wu"], e["we"],
+                                 e["pn"], e["gamma"], e["dt"], n_pic, tol=1e-10)
+        t_cpu = time.perf_counter() - t0
+        it_cpu = sum(s_["iters"] for s_ in ref["solves"])
+        import oracle
+        cpu = {"value": case.n_free * it_cpu / t_cpu, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one full projection step (2 Picard iterations, NumPy right-hand side and updates, "
+                         "C Jacobi-PCG to 1e-10), %.1f s" % t_cpu}
+    bytes_in = 8 * (E * 5 + N)
+    bytes_out = 8 * (2 * N + 5 * E)
+    out = {"metric": METRIC, "value": case.n_free * iters / (tot / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": "projection_3d_kuhn_%d^3_picard%d" % (args.n, n_pic), "n_free": case.n_free,
+                      "n_elems": E, "iters_per_step": iters // max(args.steps, 1), "dt": e["dt"],
+                      "gamma": e["gamma"], "l2": "flushed between steps (256 MB write)"},
+           "steps_per_s": 1e3 * args.steps / tot, "p50_ms": _pctl(times, 50), "p99_ms": _pctl(times, 99),
+           "roofline": roof, "cpu_baseline": cpu,
+           "e2e": {"value": case.n_free * iters / (np.sum(e2e) / 1e3), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
+                   "d2h_bytes_per_step": bytes_out, "ms_per_step": float(np.mean(e2e))},
+           "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(out))
+    P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -661,6 +766,8 @@ def main():
         run_batch(args)
     elif args.workload == "c5":
         run_served(args)
+    elif args.workload == "projection":
+        run_projection(args)
     else:
         run_ours(args)
 
