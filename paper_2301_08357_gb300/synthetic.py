@@ -382,3 +382,42 @@ def make_projection_case(dim: int = 3, n: int = 64, seed: int = 0, gamma: float 
     return Case("projection_%dd_%d" % (dim, n), dim, coords, conn, dirichlet, alpha, np.ones(E), dt * dt,
                 np.zeros(N), np.zeros(N), n=n, seed=seed,
                 extra={"rho": rho, "wu": wu, "we": we, "pn": pn, "gamma": gamma, "dt": dt})
+
+
+def periodic_master(coords: np.ndarray, axes) -> np.ndarray:
+    """master[i] for a unit square / cube periodic along `axes`: a node with
+    coordinate 1 on a periodic axis is merged into the node at 0 there (all
+    periodic axes folded at once); every other node is its own master.
+    Boundary nodes are never jittered, so matching nodes have equal folded
+    coordinates."""
+    folded = coords.copy()
+    for a in axes:
+        folded[folded[:, a] == 1.0, a] = 0.0
+    index = {tuple(x): i for i, x in enumerate(coords)}
+    return np.array([index[tuple(x)] for x in folded], dtype=np.int32)
+
+
+def make_periodic_case(dim: int = 3, n: int = 16, seed: int = 0) -> Case:
+    """The C1 (2D) or C2 (3D) set-up made periodic in y (and z): Dirichlet on
+    x = 0, Neumann on x = 1, vertices on y = 1 (z = 1) merged into their
+    images on y = 0 (z = 0) (Section 3.6: periodic boundaries by vertex
+    merging).  alpha is sampled at each node's master, so it is periodic;
+    b ~ N(0,1) per node (slaves included: their loads add onto the merged
+    unknown).  ``extra['master']`` holds the merge map."""
+    rng = np.random.default_rng(9000 + seed)
+    if dim == 2:
+        coords, conn = square_mesh(n)
+        coords = jitter_nodes(coords, n, 0.2, rng)
+        axes = (1,)
+    else:
+        coords, conn = kuhn_cube_mesh(n)
+        coords = jitter_nodes(coords, n, 0.15, rng)
+        axes = (1, 2)
+    master = periodic_master(coords, axes)
+    alpha = alpha_fourier(coords, rng)[master]
+    beta = np.exp(0.5 * rng.standard_normal(conn.shape[0]))
+    dirichlet = _dirichlet_x0(coords)
+    b = _rhs(rng, dirichlet)
+    return Case("periodic_%dd_%d" % (dim, n), dim, coords, conn, dirichlet, alpha, beta,
+                1e-2 if dim == 3 else 1e-3, b, np.zeros(coords.shape[0]), n=n, seed=seed,
+                extra={"master": master})
