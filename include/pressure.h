@@ -189,6 +189,26 @@ void ps_mesh_free(ps_mesh *mesh);
 
 int ps_mesh_get_stats(const ps_mesh *mesh, ps_mesh_stats *out);
 
+/* ---- periodic boundaries (Section 3.6: the vertices of matching periodic
+ * boundary faces are merged, which reduces the unknowns of the pressure
+ * system).  As ps_mesh_upload, plus
+ *   periodic  host [n_nodes] int32: periodic[i] = the vertex whose unknown
+ *             vertex i shares (its master), periodic[i] = i for ordinary
+ *             vertices; a master is its own master; a vertex and its master
+ *             carry the same Dirichlet flag; no element may hold two vertices
+ *             of one unknown.
+ * Each element keeps its own vertex coordinates, so the merged vertices may
+ * lie on opposite sides of the domain.  Vectors still cross the ABI in the
+ * caller's numbering over all n_nodes vertices: on input, x and the apply's
+ * operand take each unknown's value from its master; a right-hand side is a
+ * load vector, so the loads of merged vertices are added onto their unknown;
+ * on output every vertex carries its unknown's value.  alpha is taken from
+ * the master.  Errors: PS_EINVAL for an inconsistent map (ps_last_error
+ * names the rule). */
+int ps_mesh_upload_periodic(ps_ctx *ctx, int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
+                            const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
+                            const ps_mesh_opts *opts, ps_mesh **out);
+
 /* ---- coefficients (Section 3.4: 1/(gamma-1), H^{n+1,k}, dt) -----------
  *   alpha_nodal  host [n_nodes] double, >= 0, finite
  *   beta_elem    host [n_elems] double, > 0, finite (element order of upload)
@@ -364,11 +384,12 @@ int ps_server_get_stats(ps_server *srv, ps_server_stats *out);
  * exactly once in its chunk's incidence lists, chunk-interior nodes belong to
  * one chunk, partial-sum slots of shared nodes form a bijection.  Same
  * arguments as ps_mesh_upload; stats filled (device_bytes = shared memory per
- * block of the FP64 operator pass).  PS_EINVAL for bad input, PS_ESTATE if an
- * invariant fails (ps_last_error names it). */
+ * block of the FP64 operator pass).  periodic as in ps_mesh_upload_periodic
+ * (may be NULL).  PS_EINVAL for bad input, PS_ESTATE if an invariant fails
+ * (ps_last_error names it). */
 int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
-                     const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
-                     ps_mesh_stats *stats);
+                     const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
+                     const ps_mesh_opts *opts, ps_mesh_stats *stats);
 
 /* ---- kernel timing (diagnostics for roofline reports) -------------------
  * Launch one internal kernel of the solver `reps` times back to back on

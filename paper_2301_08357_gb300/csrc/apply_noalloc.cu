@@ -87,8 +87,8 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
     void *yi = b + align256((size_t)np * esz);
     void *part = b + 2 * align256((size_t)np * esz);
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = m->dev.n_nodes;
-    const int g = grid_for(n, m->ctx->sms);
+    const int64_t n = m->dev.n_nodes, nu = m->prep.n_nodes;   // unknowns, caller's vertices
+    const int g = grid_for(n, m->ctx->sms), gu = grid_for(nu, m->ctx->sms);
     if (prec == PS_F32) {
         k_perm_in<float, float><<<g, 256, 0, s>>>(n, (const float *)x, (float *)xi, m->d_old_of_new, m->dev.dirichlet);
         VecArgs<float> a;
@@ -98,7 +98,7 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
         a.partial = (float *)part;
         rc = launch_pass<float, kApply>(m, a, s);
         if (rc != PS_OK) return rc;
-        k_perm_out<float, float><<<g, 256, 0, s>>>(n, (const float *)yi, (float *)y, m->d_new_of_old);
+        k_perm_out<float, float><<<gu, 256, 0, s>>>(nu, (const float *)yi, (float *)y, m->d_new_of_old);
     } else {
         k_perm_in<double, double><<<g, 256, 0, s>>>(n, (const double *)x, (double *)xi, m->d_old_of_new,
                                                     m->dev.dirichlet);
@@ -109,7 +109,7 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
         a.partial = (double *)part;
         rc = launch_pass<double, kApply>(m, a, s);
         if (rc != PS_OK) return rc;
-        k_perm_out<double, double><<<g, 256, 0, s>>>(n, (const double *)yi, (double *)y, m->d_new_of_old);
+        k_perm_out<double, double><<<gu, 256, 0, s>>>(nu, (const double *)yi, (double *)y, m->d_new_of_old);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {

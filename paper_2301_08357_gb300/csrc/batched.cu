@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
                 const int o = M.old_of_new[i];
                 bv = M.b_user[o];
                 xv = M.x_user[o];
+                if (M.slave_ptr)    // loads of merged periodic vertices add onto the unknown
+                    for (int k = M.slave_ptr[i]; k < M.slave_ptr[i + 1]; ++k) bv += M.b_user[M.slave[k]];
             }
             M.b64[i] = bv;
             M.x64[i] = xv;
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(256) k_b_vec(const BMesh *meshes, const int2 *
         const float *x = s_par ? M.v.x[1] : M.v.x[0];
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) M.x64[i] += (double)x[i] * inv;
     } else {  // kFinish
-        for (int64_t j = i0 + threadIdx.x; j < i1; j += blockDim.x)
-            if (j < m.n_nodes) M.x_user[j] = M.x64[M.new_of_old[j]];
+        const int64_t j1 = i0 + kVecLen < M.n_user ? i0 + kVecLen : M.n_user;
+        for (int64_t j = i0 + threadIdx.x; j < j1; j += blockDim.x) M.x_user[j] = M.x64[M.new_of_old[j]];
     }
     double v = 0.0;
     if (OP == kPrepare) v = block_sum(acc, red);
@@ -395,7 +397,7 @@ static int ensure_batch_ws(ps_mesh *m) {
     if (rc != PS_OK) return rc;
     BatchMeshWs *w = new BatchMeshWs();
     const int64_t np = m->dev.n_pad;
-    const int64_t span = std::max<int64_t>(np, m->prep.sh_total);
+    const int64_t span = std::max<int64_t>(std::max<int64_t>(np, m->prep.sh_total), m->prep.n_nodes);
     w->n_segs = (int)std::max<int64_t>(1, (m->prep.n_shared + kSegLen - 1) / kSegLen);
     w->n_vt = (int)((span + kVecLen - 1) / kVecLen);
     void *p;
@@ -503,6 +505,9 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
         B.vdots = w->vdots;
         B.old_of_new = m->d_old_of_new;
         B.new_of_old = m->d_new_of_old;
+        B.slave_ptr = m->d_slave_ptr;
+        B.slave = m->d_slave;
+        B.n_user = m->prep.n_nodes;
         B.n_segs = w->n_segs;
         B.n_vt = w->n_vt;
         B.st = plan.d_st + i;

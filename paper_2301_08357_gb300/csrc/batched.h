@@ -55,6 +55,8 @@ struct BMesh {
     const double *b_user;
     double *x_user;
     const int32_t *old_of_new, *new_of_old;
+    const int32_t *slave_ptr, *slave;   // merged periodic vertices (null: none)
+    int64_t n_user;                // caller's vertices (>= unknowns with merging)
     int n_segs, n_vt;
     int64_t n_part;                // partial-sum slots (sh_total)
     BState *st;

@@ -92,6 +92,7 @@ struct ps_mesh {
     std::vector<ps::DevAlloc> allocs;
     int32_t *d_loc_node = nullptr, *d_elem_src = nullptr;
     int32_t *d_old_of_new = nullptr, *d_new_of_old = nullptr;
+    int32_t *d_slave_ptr = nullptr, *d_slave = nullptr;   // merged periodic vertices (null: none)
     int grid2 = 1, grid3 = 1, g3c = 1;
     ps::SmemLayout pipe_L0, pipe_L1;   // two-stage layout of the pipelined CG kernel
     int pipe_grid = 0;                 // its persistent grid (0 = not used)

@@ -233,6 +233,24 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         if (!std::isfinite(coords[i])) return "non-finite coordinate";
     for (int64_t i = 0; i < n_elems * nv; ++i)
         if (conn[i] < 0 || conn[i] >= n_nodes) return "vertex id out of range";
+    // periodic merging: every vertex's master (itself without merging)
+    std::vector<int32_t> master(n_nodes);
+    for (int64_t i = 0; i < n_nodes; ++i) master[i] = (int32_t)i;
+    if (opt.periodic) {
+        for (int64_t i = 0; i < n_nodes; ++i) {
+            const int32_t mi = opt.periodic[i];
+            if (mi < 0 || mi >= n_nodes) return "periodic master out of range";
+            if (opt.periodic[mi] != mi) return "periodic master is itself merged into another vertex";
+            if (dirichlet && (dirichlet[i] != 0) != (dirichlet[mi] != 0))
+                return "periodic vertex and its master differ in the Dirichlet flag";
+            master[i] = mi;
+        }
+        for (int64_t e = 0; e < n_elems; ++e)
+            for (int a = 0; a < nv; ++a)
+                for (int b = a + 1; b < nv; ++b)
+                    if (master[conn[e * nv + a]] == master[conn[e * nv + b]])
+                        return "element with two vertices merged into one unknown";
+    }
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int c = 0; c < dim; ++c) lo[c] = hi[c] = coords[c];
     for (int64_t i = 0; i < n_nodes; ++i)
@@ -340,24 +358,31 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     const int nc = (int)chunk_begin.size() - 1;
     m.n_chunks = nc;
 
-    // ---- classify nodes: interior (one chunk) or shared
+    // ---- classify unknowns (by master vertex): interior = one vertex, touched
+    // by one chunk; shared = touched by several chunks, or carrying merged
+    // periodic vertices (each vertex keeps its own coordinates, so a merged
+    // unknown gets one local node per vertex, summed like partials)
     std::vector<int32_t> last(n_nodes, -1);
-    std::vector<uint8_t> shared(n_nodes, 0);
+    std::vector<uint8_t> shared(n_nodes, 0), used(n_nodes, 0);
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (master[i] != i) shared[master[i]] = 1;
     for (int c = 0; c < nc; ++c)
         for (int64_t k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) {
             const int32_t *v = conn + (int64_t)order[k] * nv;
             for (int a = 0; a < nv; ++a) {
-                if (last[v[a]] != c) {
-                    if (last[v[a]] != -1) shared[v[a]] = 1;
-                    last[v[a]] = c;
+                used[v[a]] = 1;
+                const int32_t d = master[v[a]];
+                if (last[d] != c) {
+                    if (last[d] != -1) shared[d] = 1;
+                    last[d] = c;
                 }
             }
         }
     for (int64_t i = 0; i < n_nodes; ++i)
-        if (last[i] == -1) return "node not used by any element";
+        if (!used[i]) return "node not used by any element";
 
-    // ---- renumber: interior nodes per chunk, then shared nodes
-    m.new_of_old.assign(n_nodes, -1);
+    // ---- renumber unknowns: interior per chunk, then shared
+    std::vector<int32_t> dof(n_nodes, -1);   // new id of each master vertex
     m.chunks.resize(nc);
     int32_t next = 0;
     for (int c = 0; c < nc; ++c) {
@@ -366,8 +391,10 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         cd.int_begin = next;
         for (int64_t k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) {
             const int32_t *v = conn + (int64_t)order[k] * nv;
-            for (int a = 0; a < nv; ++a)
-                if (!shared[v[a]] && m.new_of_old[v[a]] < 0) m.new_of_old[v[a]] = next++;
+            for (int a = 0; a < nv; ++a) {
+                const int32_t d = master[v[a]];
+                if (!shared[d] && dof[d] < 0) dof[d] = next++;
+            }
         }
         cd.n_int = next - cd.int_begin;
     }
@@ -375,23 +402,40 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     for (int c = 0; c < nc; ++c)
         for (int64_t k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) {
             const int32_t *v = conn + (int64_t)order[k] * nv;
-            for (int a = 0; a < nv; ++a)
-                if (shared[v[a]] && m.new_of_old[v[a]] < 0) m.new_of_old[v[a]] = next++;
+            for (int a = 0; a < nv; ++a) {
+                const int32_t d = master[v[a]];
+                if (shared[d] && dof[d] < 0) dof[d] = next++;
+            }
         }
     m.n_shared = next - m.n_int;
-    m.old_of_new.assign(n_nodes, 0);
-    m.dirichlet_new.assign(n_nodes, 0);
-    for (int64_t i = 0; i < n_nodes; ++i) {
-        m.old_of_new[m.new_of_old[i]] = (int32_t)i;
-        m.dirichlet_new[m.new_of_old[i]] = dirichlet ? (dirichlet[i] != 0) : 0;
-    }
+    m.n_dofs = next;
+    m.new_of_old.assign(n_nodes, -1);
+    for (int64_t i = 0; i < n_nodes; ++i) m.new_of_old[i] = dof[master[i]];
+    m.old_of_new.assign(m.n_dofs, 0);
+    m.dirichlet_new.assign(m.n_dofs, 0);
+    for (int64_t i = 0; i < n_nodes; ++i)
+        if (master[i] == i) {
+            m.old_of_new[dof[i]] = (int32_t)i;
+            m.dirichlet_new[dof[i]] = dirichlet ? (dirichlet[i] != 0) : 0;
+        }
     m.n_free = 0;
-    for (int64_t i = 0; i < n_nodes; ++i) m.n_free += m.dirichlet_new[i] == 0;
+    for (int64_t g = 0; g < m.n_dofs; ++g) m.n_free += m.dirichlet_new[g] == 0;
+    if (opt.periodic) {
+        // merged vertices of every unknown, ascending vertex id
+        m.slave_ptr.assign(m.n_dofs + 1, 0);
+        for (int64_t i = 0; i < n_nodes; ++i)
+            if (master[i] != i) m.slave_ptr[dof[master[i]] + 1]++;
+        for (int64_t g = 0; g < m.n_dofs; ++g) m.slave_ptr[g + 1] += m.slave_ptr[g];
+        m.slave.assign(m.slave_ptr.back(), 0);
+        std::vector<int32_t> fill(m.slave_ptr.begin(), m.slave_ptr.end() - 1);
+        for (int64_t i = 0; i < n_nodes; ++i)
+            if (master[i] != i) m.slave[fill[dof[master[i]]]++] = (int32_t)i;
+    }
 
     // ---- per-chunk local structure
     int64_t patch_off = 0, node_off = 0, sh_off = 0, incp_off = 0, inc_off = 0;
-    std::vector<int32_t> loc_of_new(n_nodes, -1);
-    std::vector<int32_t> shl;
+    std::vector<int32_t> loc_of_vtx(n_nodes, -1);   // local node of a vertex in the current chunk
+    std::vector<int32_t> shl;                        // the chunk's shared local vertices
     std::vector<int32_t> shr_cnt(m.n_shared + 1, 0);
     std::vector<std::array<int, 4>> lc;
     std::vector<PatchRec> patches;
@@ -399,26 +443,31 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         ChunkDesc &cd = m.chunks[c];
         const int n_el = (int)(chunk_begin[c + 1] - chunk_begin[c]);
         cd.n_elem = n_el;
-        // shared local nodes, ascending new id
+        // shared local nodes: one per vertex whose unknown is shared,
+        // ascending (unknown, vertex)
         shl.clear();
         for (int64_t k = chunk_begin[c]; k < chunk_begin[c + 1]; ++k) {
             const int32_t *v = conn + (int64_t)order[k] * nv;
             for (int a = 0; a < nv; ++a) {
-                int32_t g = m.new_of_old[v[a]];
-                if (g >= m.n_int && loc_of_new[g] != -2) { loc_of_new[g] = -2; shl.push_back(g); }
+                const int32_t g = m.new_of_old[v[a]];
+                if (g >= m.n_int && loc_of_vtx[v[a]] != -2) { loc_of_vtx[v[a]] = -2; shl.push_back(v[a]); }
             }
         }
-        std::sort(shl.begin(), shl.end());
+        std::sort(shl.begin(), shl.end(), [&](int32_t x, int32_t y) {
+            const int32_t gx = m.new_of_old[x], gy = m.new_of_old[y];
+            return gx != gy ? gx < gy : x < y;
+        });
         cd.n_sh = (int32_t)shl.size();
         cd.n_loc = cd.n_int + cd.n_sh;
         cd.node_off = (int32_t)node_off;
         cd.sh_off = (int32_t)sh_off;
         cd.incp_off = (int32_t)incp_off;
-        for (int32_t l = 0; l < cd.n_int; ++l) loc_of_new[cd.int_begin + l] = l;
+        for (int32_t l = 0; l < cd.n_int; ++l) loc_of_vtx[m.old_of_new[cd.int_begin + l]] = l;
         for (int32_t j = 0; j < cd.n_sh; ++j) {
-            loc_of_new[shl[j]] = cd.n_int + j;
-            m.sh_ids.push_back(shl[j]);
-            shr_cnt[shl[j] - m.n_int + 1]++;
+            const int32_t g = m.new_of_old[shl[j]];
+            loc_of_vtx[shl[j]] = cd.n_int + j;
+            m.sh_ids.push_back(g);
+            shr_cnt[g - m.n_int + 1]++;
         }
         for (int64_t j = cd.n_sh; j < round_up(cd.n_sh, kShPad); ++j) m.sh_ids.push_back(-1);
         sh_off += round_up(cd.n_sh, kShPad);
@@ -427,7 +476,7 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         lc.assign(n_el, std::array<int, 4>{0, 0, 0, 0});
         for (int e = 0; e < n_el; ++e) {
             int32_t src = order[chunk_begin[c] + e];
-            for (int a = 0; a < nv; ++a) lc[e][a] = loc_of_new[m.new_of_old[conn[(int64_t)src * nv + a]]];
+            for (int a = 0; a < nv; ++a) lc[e][a] = loc_of_vtx[conn[(int64_t)src * nv + a]];
         }
         build_patches(dim, n_el, lc, patches);
         balance_patches(patches);
@@ -473,17 +522,19 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         inc_off += round_up(n_inc, kIncPad);
         patch_off += np_pad;
         m.n_patches += np;
-        // node block bookkeeping (coordinates relative to the chunk origin)
-        int32_t origin_new = cd.n_int > 0 ? cd.int_begin : shl[0];
-        const double *o = coords + (int64_t)m.old_of_new[origin_new] * dim;
+        // node block bookkeeping (coordinates of each local node's own
+        // vertex, relative to the chunk origin)
+        const int32_t origin_vtx = cd.n_int > 0 ? m.old_of_new[cd.int_begin] : shl[0];
+        const double *o = coords + (int64_t)origin_vtx * dim;
         for (int32_t l = 0; l < cd.n_loc; ++l) {
-            int32_t g = l < cd.n_int ? cd.int_begin + l : shl[l - cd.n_int];
-            m.loc_node.push_back(g);
-            const double *p = coords + (int64_t)m.old_of_new[g] * dim;
+            const int32_t vtx = l < cd.n_int ? m.old_of_new[cd.int_begin + l] : shl[l - cd.n_int];
+            m.loc_node.push_back(m.new_of_old[vtx]);
+            m.loc_orig.push_back(vtx);
+            const double *p = coords + (int64_t)vtx * dim;
             for (int k = 0; k < dim; ++k) m.loc_rel.push_back(p[k] - o[k]);
         }
-        for (int32_t l = 0; l < cd.n_int; ++l) loc_of_new[cd.int_begin + l] = -1;
-        for (int32_t j = 0; j < cd.n_sh; ++j) loc_of_new[shl[j]] = -1;
+        for (int32_t l = 0; l < cd.n_int; ++l) loc_of_vtx[m.old_of_new[cd.int_begin + l]] = -1;
+        for (int32_t j = 0; j < cd.n_sh; ++j) loc_of_vtx[shl[j]] = -1;
         m.max_patch = std::max(m.max_patch, np);
         m.max_elem = std::max(m.max_elem, n_el);
         m.max_loc = std::max(m.max_loc, cd.n_loc);
@@ -531,14 +582,16 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
 std::string validate_prep(const PrepMesh &m, const int32_t *conn) {
     const int nv = m.nv;
     std::vector<int> seen_elem(m.n_elems, 0);
-    std::vector<int32_t> owner(m.n_nodes, -1);
+    std::vector<int32_t> owner(m.n_dofs, -1);
     for (int c = 0; c < m.n_chunks; ++c) {
         const ChunkDesc &cd = m.chunks[c];
         if (cd.patch_off % kPatchPad || cd.sh_off % kShPad || cd.incp_off % kIncpPad || cd.inc_off % kIncPad)
             return "segment not aligned";
-        auto global_of = [&](int l) -> int32_t {
-            return l < cd.n_int ? cd.int_begin + l : m.sh_ids[cd.sh_off + l - cd.n_int];
-        };
+        for (int32_t l = 0; l < cd.n_loc; ++l) {
+            const int32_t want_g = l < cd.n_int ? cd.int_begin + l : m.sh_ids[cd.sh_off + l - cd.n_int];
+            if (m.loc_node[cd.node_off + l] != want_g) return "local node maps to the wrong unknown";
+            if (m.new_of_old[m.loc_orig[cd.node_off + l]] != want_g) return "local vertex maps to the wrong unknown";
+        }
         std::vector<int> hits((size_t)cd.n_patch * kPatchSlots, 0);
         std::vector<int> slot_node((size_t)cd.n_patch * kPatchSlots, -1);
         int n_el = 0;
@@ -556,10 +609,10 @@ std::string validate_prep(const PrepMesh &m, const int32_t *conn) {
                 ++n_el;
                 std::vector<int32_t> want, have;
                 for (int a = 0; a < nv; ++a) want.push_back(conn[(int64_t)src * nv + a]);
-                have.push_back(m.old_of_new[global_of(rec[1])]);
-                if (m.dim == 3) have.push_back(m.old_of_new[global_of(rec[2])]);
-                have.push_back(m.old_of_new[global_of(rec[3 + j])]);
-                have.push_back(m.old_of_new[global_of(rec[3 + j + 1])]);
+                have.push_back(m.loc_orig[cd.node_off + rec[1]]);
+                if (m.dim == 3) have.push_back(m.loc_orig[cd.node_off + rec[2]]);
+                have.push_back(m.loc_orig[cd.node_off + rec[3 + j]]);
+                have.push_back(m.loc_orig[cd.node_off + rec[3 + j + 1]]);
                 std::sort(want.begin(), want.end());
                 std::sort(have.begin(), have.end());
                 if (want != have) return "patch element does not match the mesh";

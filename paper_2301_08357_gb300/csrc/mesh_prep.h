@@ -13,11 +13,16 @@ namespace ps {
 struct PrepOptions {
     int chunk_elems = 0;      // 0 = auto
     int chunk_nodes_max = 0;  // 0 = auto
+    // periodic boundaries by vertex merging (Section 3.6): master[i] is the
+    // vertex whose unknown vertex i shares (master[master[i]] == master[i]);
+    // nullptr = no merging
+    const int32_t *periodic = nullptr;
 };
 
 struct PrepMesh {
     int dim = 0, nv = 0;
     int64_t n_nodes = 0, n_elems = 0, n_free = 0;
+    int64_t n_dofs = 0;       // unknowns: n_nodes minus merged periodic vertices
     int n_chunks = 0;
     int64_t n_int = 0;        // interior nodes (new ids 0..n_int-1)
     int64_t n_shared = 0;     // shared nodes (new ids n_int..n_nodes-1)
@@ -29,15 +34,18 @@ struct PrepMesh {
     int64_t sh_total = 0;     // padded shared-id slots (= partial slots)
     int max_patch = 0, max_loc = 0, max_sh = 0, max_inc = 0, max_elem = 0;
 
-    std::vector<int32_t> new_of_old, old_of_new;   // [n_nodes]
-    std::vector<uint8_t> dirichlet_new;            // [n_nodes]
+    std::vector<int32_t> new_of_old;               // [n_nodes] unknown of each vertex
+    std::vector<int32_t> old_of_new;               // [n_dofs] master vertex of each unknown
+    std::vector<uint8_t> dirichlet_new;            // [n_dofs]
+    std::vector<int32_t> slave_ptr, slave;         // [n_dofs + 1], merged vertices per unknown (empty: no merging)
     std::vector<ChunkDesc> chunks;                 // [n_chunks]
     std::vector<uint16_t> pids;                    // [patch_total * kPatchIds]
     std::vector<int32_t> elem_src;                 // [patch_total * kPatchMax] original element, -1 unused
     std::vector<uint16_t> incp;                    // [incp_total]
     std::vector<uint16_t> inc;                     // [inc_total] patch * kPatchSlots + slot
     std::vector<int32_t> sh_ids;                   // [sh_total], -1 pad
-    std::vector<int32_t> loc_node;                 // [loc_total] new id of each local node
+    std::vector<int32_t> loc_node;                 // [loc_total] unknown (new id) of each local node
+    std::vector<int32_t> loc_orig;                 // [loc_total] vertex (caller's id) of each local node
     std::vector<double> loc_rel;                   // [loc_total * dim] coords - chunk origin
     std::vector<int32_t> shr_ptr;                  // [n_shared + 1]
     std::vector<int32_t> shr_slot;                 // chunk-major slot of each shared-node-major partial

@@ -529,6 +529,18 @@ __global__ void k_perm_in(int64_t n, const TI *__restrict__ in, TO *__restrict__
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = dirichlet[i] ? TO(0) : (TO)in[old_of_new[i]];
 }
+// Merged periodic vertices: out[g] += sum of in[v] over the vertices merged
+// into unknown g (ascending vertex id; 0 stays on Dirichlet unknowns).
+static __global__ void k_add_slaves(int64_t n, const int32_t *__restrict__ ptr, const int32_t *__restrict__ slave,
+                                    const double *__restrict__ in, double *__restrict__ out,
+                                    const uint8_t *__restrict__ dirichlet) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        if (dirichlet[g] || ptr[g] == ptr[g + 1]) continue;
+        double v = out[g];
+        for (int k = ptr[g]; k < ptr[g + 1]; ++k) v += in[slave[k]];
+        out[g] = v;
+    }
+}
 // out_old[j] = in_new[new_of_old[j]]
 template <typename TI, typename TO>
 __global__ void k_perm_out(int64_t n, const TI *__restrict__ in, TO *__restrict__ out, const int32_t *__restrict__ new_of_old) {

@@ -283,10 +283,10 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     std::memset(&d, 0, sizeof(d));
     d.dim = pm.dim;
     d.n_chunks = pm.n_chunks;
-    d.n_nodes = pm.n_nodes;
+    d.n_nodes = pm.n_dofs;             // internal vectors are per unknown
     d.n_int = pm.n_int;
     d.n_shared = pm.n_shared;
-    d.n_pad = round_up(pm.n_nodes, 4);
+    d.n_pad = round_up(pm.n_dofs, 4);
     ChunkDesc *ch;
     RC(upload(c, m, &ch, pm.chunks.data(), pm.chunks.size() * sizeof(ChunkDesc)));
     d.chunks = ch;
@@ -311,9 +311,13 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     RC(upload(c, m, &m->d_elem_src, pm.elem_src.data(), pm.elem_src.size() * 4));
     RC(upload(c, m, &m->d_old_of_new, pm.old_of_new.data(), pm.old_of_new.size() * 4));
     RC(upload(c, m, &m->d_new_of_old, pm.new_of_old.data(), pm.new_of_old.size() * 4));
+    if (!pm.slave.empty()) {
+        RC(upload(c, m, &m->d_slave_ptr, pm.slave_ptr.data(), pm.slave_ptr.size() * 4));
+        RC(upload(c, m, &m->d_slave, pm.slave.data(), pm.slave.size() * 4));
+    }
     // Dirichlet flags, padded to n_pad with 1 so padding rows stay zero
     std::vector<uint8_t> dir(d.n_pad, 1);
-    std::memcpy(dir.data(), pm.dirichlet_new.data(), pm.n_nodes);
+    std::memcpy(dir.data(), pm.dirichlet_new.data(), pm.n_dofs);
     uint8_t *du;
     RC(upload(c, m, &du, dir.data(), dir.size()));
     d.dirichlet = du;
@@ -404,6 +408,12 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
 extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
                               const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
                               ps_mesh **out) {
+    return ps_mesh_upload_periodic(c, dim, n_nodes, coords, n_elems, conn, dirichlet, nullptr, opts, out);
+}
+
+extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
+                                       const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
+                                       const ps_mesh_opts *opts, ps_mesh **out) {
     if (!c || !out || !coords || !conn) return PS_EINVAL;
     *out = nullptr;
     std::lock_guard<std::mutex> lk(c->mu);
@@ -413,6 +423,7 @@ extern "C" int ps_mesh_upload(ps_ctx *c, int dim, int64_t n_nodes, const double 
         po.chunk_elems = opts->chunk_elems;
         po.chunk_nodes_max = opts->chunk_nodes_max;
     }
+    po.periodic = periodic;
     ps_mesh *m = new (std::nothrow) ps_mesh();
     if (!m) return PS_ENOMEM;
     m->ctx = c;
@@ -510,15 +521,15 @@ static int coeff_upload(ps_mesh *m, const double *alpha, const double *beta, dou
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && alpha) {
-        std::vector<double> an(p.n_nodes);
-        for (int64_t i = 0; i < p.n_nodes; ++i) an[p.new_of_old[i]] = alpha[i];
+        std::vector<double> an(p.n_dofs);   // the master vertex's alpha per unknown
+        for (int64_t g = 0; g < p.n_dofs; ++g) an[g] = alpha[p.old_of_new[g]];
         void *dal = nullptr;
-        rc = dalloc(c, &dal, p.n_nodes * 8, tmp);
+        rc = dalloc(c, &dal, p.n_dofs * 8, tmp);
         if (rc != PS_OK) {
             dfree_all(c, tmp);
             return rc;
         }
-        e = cudaMemcpy(dal, an.data(), p.n_nodes * 8, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(dal, an.data(), p.n_dofs * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) {
             k_set_alpha<<<grid_for(p.loc_total, c->sms), kBlock>>>(p.loc_total, m->d_loc_node, (const double *)dal,
                                                                     d.dirichlet, const_cast<NodeF *>(d.node32),
@@ -892,7 +903,7 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
             std::vector<float> f(np);
             std::vector<double> d(np);
             std::vector<uint8_t> dir(np, 1);
-            for (int64_t i = 0; i < m->prep.n_nodes; ++i) dir[i] = m->prep.dirichlet_new[i];
+            for (int64_t i = 0; i < m->prep.n_dofs; ++i) dir[i] = m->prep.dirichlet_new[i];
             for (int64_t i = 0; i < np; ++i) {
                 f[i] = dir[i] ? 0.f : 1.f;
                 d[i] = dir[i] ? 0.0 : 1.0;
@@ -991,8 +1002,8 @@ extern "C" int ps_pressure_apply(ps_mesh *m, const void *x, void *y, int prec, v
     RC(ensure_workspace(m));
     cudaStream_t s = (cudaStream_t)stream;
     Workspace &w = m->ws;
-    const int64_t n = m->dev.n_nodes;
-    const int g = grid_for(n, m->ctx->sms);
+    const int64_t n = m->dev.n_nodes, nu = m->prep.n_nodes;   // unknowns, caller's vertices
+    const int g = grid_for(n, m->ctx->sms), gu = grid_for(nu, m->ctx->sms);
     if (prec == PS_F32) {
         k_perm_in<float, float><<<g, kBlock, 0, s>>>(n, (const float *)x, w.r32, m->d_old_of_new, m->dev.dirichlet);
         VecArgs<float> a;
@@ -1001,7 +1012,7 @@ extern "C" int ps_pressure_apply(ps_mesh *m, const void *x, void *y, int prec, v
         a.y = w.q32;
         a.partial = w.part32;
         RC((launch_pass<float, kApply>(m, a, s)));
-        k_perm_out<float, float><<<g, kBlock, 0, s>>>(n, w.q32, (float *)y, m->d_new_of_old);
+        k_perm_out<float, float><<<gu, kBlock, 0, s>>>(nu, w.q32, (float *)y, m->d_new_of_old);
     } else {
         k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, (const double *)x, w.r64, m->d_old_of_new, m->dev.dirichlet);
         VecArgs<double> a;
@@ -1010,7 +1021,7 @@ extern "C" int ps_pressure_apply(ps_mesh *m, const void *x, void *y, int prec, v
         a.y = w.q64;
         a.partial = w.part64;
         RC((launch_pass<double, kApply>(m, a, s)));
-        k_perm_out<double, double><<<g, kBlock, 0, s>>>(n, w.q64, (double *)y, m->d_new_of_old);
+        k_perm_out<double, double><<<gu, kBlock, 0, s>>>(nu, w.q64, (double *)y, m->d_new_of_old);
     }
     CK(cudaGetLastError());
     return PS_OK;
@@ -1054,16 +1065,20 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
     }
     RC(ensure_workspace(m));
     Workspace &w = m->ws;
-    const int64_t n = m->dev.n_nodes;
-    const int g = grid_for(n, m->ctx->sms);
+    const int64_t n = m->dev.n_nodes, nu = m->prep.n_nodes;   // unknowns, caller's vertices
+    const int g = grid_for(n, m->ctx->sms), gu = grid_for(nu, m->ctx->sms);
     m->launches = 0;
     k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, b, w.b64, m->d_old_of_new, m->dev.dirichlet);
     k_perm_in<double, double><<<g, kBlock, 0, s>>>(n, x, w.x64, m->d_old_of_new, m->dev.dirichlet);
     m->launches += 2;
+    if (m->d_slave) {        // merged periodic vertices: their loads add onto the unknown
+        k_add_slaves<<<g, kBlock, 0, s>>>(n, m->d_slave_ptr, m->d_slave, b, w.b64, m->dev.dirichlet);
+        m->launches += 1;
+    }
     CK(cudaGetLastError());
     int rc = solve_internal(m, o, inf, s);
     if (rc == PS_OK || rc == PS_ENOTCONV || rc == PS_EBREAKDOWN) {
-        k_perm_out<double, double><<<g, kBlock, 0, s>>>(n, w.x64, x, m->d_new_of_old);
+        k_perm_out<double, double><<<gu, kBlock, 0, s>>>(nu, w.x64, x, m->d_new_of_old);
         m->launches += 1;
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
@@ -1075,14 +1090,15 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
 
 // ---------------------------------------------------------------- debug hooks (host only)
 extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
-                                const int32_t *conn, const uint8_t *dirichlet, const ps_mesh_opts *opts,
-                                ps_mesh_stats *stats) {
+                                const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
+                                const ps_mesh_opts *opts, ps_mesh_stats *stats) {
     if (!coords || !conn) return PS_EINVAL;
     PrepOptions po;
     if (opts) {
         po.chunk_elems = opts->chunk_elems;
         po.chunk_nodes_max = opts->chunk_nodes_max;
     }
+    po.periodic = periodic;
     PrepMesh pm;
     std::string err = prepare_mesh(dim, n_nodes, coords, n_elems, conn, dirichlet, po, pm);
     if (!err.empty()) {

@@ -237,7 +237,7 @@ int ensure_proj(ps_mesh *m) {
                     loc[nl++] = rec[3 + j];
                     loc[nl++] = rec[3 + j + 1];
                     for (int a = 0; a < nv; ++a)
-                        conn[(size_t)src * nv + a] = pm.old_of_new[pm.loc_node[cd.node_off + loc[a]]];
+                        conn[(size_t)src * nv + a] = pm.loc_orig[cd.node_off + loc[a]];
                 }
             }
         }

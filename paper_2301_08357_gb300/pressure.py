@@ -105,6 +105,8 @@ SIGNATURES = {
     "ps_ctx_bytes_in_use": (_i64, [_vp]),
     "ps_mesh_upload": (C.c_int, [_vp, C.c_int, _i64, _vp, _i64, _vp, _vp, C.POINTER(ps_mesh_opts),
                                  C.POINTER(_vp)]),
+    "ps_mesh_upload_periodic": (C.c_int, [_vp, C.c_int, _i64, _vp, _i64, _vp, _vp, _vp, C.POINTER(ps_mesh_opts),
+                                 C.POINTER(_vp)]),
     "ps_mesh_free": (None, [_vp]),
     "ps_mesh_get_stats": (C.c_int, [_vp, C.POINTER(ps_mesh_stats)]),
     "ps_coeff_set": (C.c_int, [_vp, _vp, _vp, C.c_double]),
@@ -127,7 +129,7 @@ SIGNATURES = {
     "ps_server_release": (C.c_int, [_vp, _i64]),
     "ps_server_get_stats": (C.c_int, [_vp, C.POINTER(ps_server_stats)]),
     "ps_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double)]),
-    "ps_debug_prepare": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, C.POINTER(ps_mesh_opts),
+    "ps_debug_prepare": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, _vp, C.POINTER(ps_mesh_opts),
                                    C.POINTER(ps_mesh_stats)]),
 }
 
@@ -202,7 +204,8 @@ def ps_ctx_bytes_in_use(ctx):
 
 
 def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, pipeline=0,
-                   update_blocks_per_sm=0):
+                   update_blocks_per_sm=0, periodic=None):
+    """periodic: optional [n_nodes] master map (ps_mesh_upload_periodic)."""
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
     n = coords.shape[0]
@@ -211,8 +214,13 @@ def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_
         dirichlet, pd = _host(dirichlet, np.uint8)
     o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline, update_blocks_per_sm)
     h = _vp()
-    _check(_lib.ps_mesh_upload(ctx, int(dim), n, pc, conn.shape[0], pe, pd, C.byref(o), C.byref(h)),
-           "ps_mesh_upload")
+    if periodic is None:
+        _check(_lib.ps_mesh_upload(ctx, int(dim), n, pc, conn.shape[0], pe, pd, C.byref(o), C.byref(h)),
+               "ps_mesh_upload")
+    else:
+        periodic, pp = _host(periodic, np.int32)
+        _check(_lib.ps_mesh_upload_periodic(ctx, int(dim), n, pc, conn.shape[0], pe, pd, pp, C.byref(o),
+                                            C.byref(h)), "ps_mesh_upload_periodic")
     return h
 
 
@@ -377,15 +385,18 @@ def ps_profile_kernel(mesh, which, reps=20, stream=None):
     return float(ms.value)
 
 
-def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0):
+def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, periodic=None):
     """Host-only: run the mesh preprocessing and its invariant checks."""
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
     pd = None
     if dirichlet is not None:
         dirichlet, pd = _host(dirichlet, np.uint8)
+    pp = None
+    if periodic is not None:
+        periodic, pp = _host(periodic, np.int32)
     o = ps_mesh_opts(chunk_elems, chunk_nodes_max)
     s = ps_mesh_stats()
-    _check(_lib.ps_debug_prepare(int(dim), coords.shape[0], pc, conn.shape[0], pe, pd, C.byref(o), C.byref(s)),
-           "ps_debug_prepare")
+    _check(_lib.ps_debug_prepare(int(dim), coords.shape[0], pc, conn.shape[0], pe, pd, pp, C.byref(o),
+                                 C.byref(s)), "ps_debug_prepare")
     return s

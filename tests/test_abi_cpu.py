@@ -92,3 +92,41 @@ def test_prepare_rejects_bad_input(P):
         P.ps_debug_prepare(2, nanc, case.conn, case.dirichlet)
     with pytest.raises(P.PressureError):
         P.ps_debug_prepare(4, case.coords, case.conn, case.dirichlet)
+
+
+@pytest.mark.parametrize("dim,n,chunk", [(2, 8, 0), (2, 9, 40), (3, 4, 0), (3, 5, 60)])
+def test_prepare_periodic_invariants(P, dim, n, chunk):
+    from oracle.periodic import PeriodicMatrix
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_periodic_case(dim, n)
+    master = case.extra["master"]
+    s = P.ps_debug_prepare(dim, case.coords, case.conn, case.dirichlet, chunk_elems=chunk, periodic=master)
+    A = PeriodicMatrix(dim, case.coords, case.conn, case.dirichlet, master, case.alpha, case.beta, case.dt2)
+    assert s.n_nodes == case.n_nodes
+    assert s.n_free == int(A.free.sum())
+    # identity map = no merging
+    s0 = P.ps_debug_prepare(dim, case.coords, case.conn, case.dirichlet, chunk_elems=chunk,
+                            periodic=np.arange(case.n_nodes, dtype=np.int32))
+    assert s0.n_free == case.n_free
+
+
+def test_prepare_rejects_bad_periodic_maps(P):
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_periodic_case(2, 4)
+    master = case.extra["master"]
+    chained = master.copy()
+    j = int(np.flatnonzero(master != np.arange(case.n_nodes))[0])    # a merged vertex
+    i = int(np.flatnonzero(master == np.arange(case.n_nodes))[-1])   # some master
+    chained[i] = j                                                  # master mapped onto a merged vertex
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, case.coords, case.conn, case.dirichlet, periodic=chained)
+    mixed = case.dirichlet.copy()
+    x0_merged = np.flatnonzero((master != np.arange(case.n_nodes)) & (case.dirichlet == 1))[0]
+    mixed[x0_merged] = 0                                            # slave free, master Dirichlet
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, case.coords, case.conn, mixed, periodic=master)
+    # one cell across the period: an element would hold two vertices of one unknown
+    coords, conn = S.square_mesh(1)
+    thin = S.periodic_master(coords, (1,))
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(2, coords, conn, None, periodic=thin)
