@@ -384,6 +384,26 @@ def make_projection_case(dim: int = 3, n: int = 64, seed: int = 0, gamma: float 
                 extra={"rho": rho, "wu": wu, "we": we, "pn": pn, "gamma": gamma, "dt": dt})
 
 
+def make_eos_case(dim: int = 3, n: int = 64, seed: int = 0, eos_a: float = 2.5, eos_b: float = 0.5) -> Case:
+    """The projection-stage fields of make_projection_case for a gas whose
+    internal energy density is rho e = eos_a P + eos_b P^2 / rho (a thermally
+    perfect gas with c_v linear in the temperature; eos_b = 0 is the ideal
+    gas of make_projection_case with eos_a = 1/(gamma - 1)):
+      we [E]  eos_a Pbar + eos_b Pbar^2 / rho + |wu|^2 / (2 rho) + 0.01 N(0,1),
+    Pbar the vertex mean of pn; ``extra`` gains eos_a and eos_b, and alpha is
+    eos_a at every node (a placeholder: the Newton iteration sets it)."""
+    case = make_projection_case(dim, n, seed=seed, gamma=1.0 + 1.0 / eos_a)
+    e = case.extra
+    rng = np.random.default_rng(9100 + seed)
+    pbar = e["pn"][case.conn].mean(axis=1)
+    rhok = 0.5 * (e["wu"] * e["wu"]).sum(axis=1) / e["rho"]
+    we = eos_a * pbar + eos_b * pbar * pbar / e["rho"] + rhok + 0.01 * rng.standard_normal(case.n_elems)
+    extra = dict(e, we=we, eos_a=float(eos_a), eos_b=float(eos_b))
+    return Case("eos_%dd_%d" % (dim, n), dim, case.coords, case.conn, case.dirichlet,
+                np.full(case.n_nodes, float(eos_a)), case.beta, case.dt2, case.b, case.x0, n=n, seed=seed,
+                extra=extra)
+
+
 def periodic_master(coords: np.ndarray, axes) -> np.ndarray:
     """master[i] for a unit square / cube periodic along `axes`: a node with
     coordinate 1 on a periodic axis is merged into the node at 0 there (all
