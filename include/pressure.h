@@ -71,6 +71,10 @@ extern "C" {
 #define PS_PRECOND_NONE   0
 #define PS_PRECOND_JACOBI 1
 
+/* ---- mass form of the operator (ps_mesh_set_mass) -------------------- */
+#define PS_MASS_CONSISTENT 0  /* int alpha_h phi_i phi_j (Section 3.4; default)   */
+#define PS_MASS_LUMPED     1  /* vertex quadrature: diagonal (Section 3, general EOS) */
+
 typedef struct ps_ctx ps_ctx;
 typedef struct ps_mesh ps_mesh;
 typedef struct ps_server ps_server;
@@ -221,6 +225,19 @@ int ps_coeff_set(ps_mesh *mesh, const double *alpha_nodal, const double *beta_el
 /* Only beta changes (alpha and dt2 kept): same checks and effect. */
 int ps_coeff_set_beta(ps_mesh *mesh, const double *beta_elem);
 
+/* ---- mass form (Section 3, the general equation of state: with mass
+ * lumping the pressure system becomes mildly nonlinear and Newton-type
+ * methods solve it) -------------------------------------------------------
+ *   mass  PS_MASS_CONSISTENT (the form of Section 3.4) or PS_MASS_LUMPED:
+ *         the alpha-weighted mass integral by vertex quadrature on every
+ *         element, (M_alpha)_ij = delta_ij alpha_i m_i with
+ *         m_i = int phi_i = sum over the elements e around i of |T_e|/(d+1).
+ * Every apply and solve of the mesh (single, batched, served) uses the form
+ * set last; the Jacobi diagonal is rebuilt if coefficients are set.  A server
+ * reads the form when it admits a request: change it only while no request
+ * of the mesh is in flight.  Errors: PS_EINVAL (unknown form). */
+int ps_mesh_set_mass(ps_mesh *mesh, int mass);
+
 /* ---- operator apply: y = A x (Dirichlet rows/cols removed) ---------------
  *   x_dev, y_dev  device [n_nodes] float (PS_F32) or double (PS_F64), caller
  *                 numbering; must not alias.
@@ -304,6 +321,52 @@ int ps_projection_step(ps_mesh *mesh, const ps_projection_opts *opts, const doub
                        const double *wu_dev, const double *we_dev, const double *pn_dev, double *dp_dev,
                        double *p_dev, double *wun_dev, double *h_dev, double *rhok_dev,
                        ps_solve_info *info, void *stream);
+
+/* ---- projection stage with a general equation of state (Section 3: the
+ * energy equation with W_E(P, rho) in place of the ideal gas; with lumped
+ * mass the pressure system is mildly nonlinear, solved by Newton's method)
+ * The internal energy density is
+ *     rho e(P, rho) = eos_a P + eos_b P^2 / rho,
+ * the caloric equation of a thermally perfect gas whose c_v is linear in the
+ * temperature (eos_b = 0: the ideal gas, eos_a = 1/(gamma-1)).  Enthalpy per
+ * element H_e = (rho e(Pbar, rho_e) + Pbar) / rho_e, Pbar the vertex mean.
+ * Per Picard iteration k (H^{n+1,k}, (rho K)^{n+1,k} frozen, as in
+ * ps_projection_step), with w_ei = |T_e|/(d+1) and dP on the free nodes:
+ *   F_i(dP) = sum_e w_ei rho e(P^n_i + dP_i, rho_e) + dt^2 (K_H dP)_i - c_i,
+ *   c_i = int (W~_E - rho K) phi_i + dt int H W~~_u . grad phi_i;
+ * Newton from the current dP: J = diag(Q'_i) + dt^2 K_H, Q'_i the derivative
+ * of the mass sum, set as the mesh's alpha_i = Q'_i / m_i (lumped operator),
+ * then J dP_new = J dP - F(dP) solved by ps_pressure_solve (opts->solve,
+ * warm start dP).  The step stops when ||F||_2 <= newton_tol ||c||_2 over
+ * the free nodes (checked before each solve and after the last) or after
+ * max_newton solves.  Then the post-projection of ps_projection_step with
+ * the EOS enthalpy.
+ *   requires ps_mesh_set_mass(mesh, PS_MASS_LUMPED); not for periodic meshes.
+ *   Arrays and outputs: as ps_projection_step.  newton_res_host: NULL or host
+ *   [n_picard * (max_newton + 1)] doubles, ||F||/||c|| at each check (-1
+ *   where no check ran).  After the call the mesh's alpha is the last
+ *   Jacobian's, beta the last H, dt2 = dt^2 (ps_projection_step then needs a
+ *   new ps_coeff_set).  Errors: PS_EINVAL (bad argument, periodic mesh, an
+ *   enthalpy or Jacobian entry Q'_i that is not positive and finite),
+ *   PS_ESTATE (consistent mass), PS_ENOTCONV (newton_tol > 0 not reached in
+ *   the last Picard iteration; outputs written), solve statuses. */
+typedef struct {
+    double eos_a;            /* > 0                                               */
+    double eos_b;            /* >= 0                                              */
+    double dt;               /* time step, > 0                                    */
+    int32_t n_picard;        /* Picard iterations, 1..64                          */
+    int32_t max_newton;      /* Newton solves per Picard iteration, 1..64          */
+    double newton_tol;       /* relative nonlinear residual; <= 0: always          */
+                             /* max_newton solves, no check (default 1e-8)         */
+    double reserved[4];
+    ps_solve_opts solve;     /* options of every linear solve                      */
+} ps_eos_opts;
+
+void ps_eos_opts_default(ps_eos_opts *opts);
+int ps_projection_step_eos(ps_mesh *mesh, const ps_eos_opts *opts, const double *rho_dev,
+                           const double *wu_dev, const double *we_dev, const double *pn_dev, double *dp_dev,
+                           double *p_dev, double *wun_dev, double *h_dev, double *rhok_dev,
+                           double *newton_res_host, ps_solve_info *info, void *stream);
 
 /* ---- batched solve: many independent meshes in one persistent kernel ----
  *   meshes  [n] mesh handles of one context (distinct, coefficients set)

@@ -326,10 +326,14 @@ __device__ __forceinline__ void load_bd(const T *__restrict__ bdt2, T (&bd)[kPat
     }
 }
 
-template <int D, typename T, typename N4, bool DIAG>
+// lumped: the mass term by vertex quadrature (int alpha_h phi_i phi_j ~
+// delta_ij alpha_i |T| / (d+1) per element: the mass-lumped variant), else
+// the consistent form above.
+template <int D, typename T, typename N4, bool DIAG, bool LUMP = false>
 __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const T *__restrict__ s_val,
                                            const uint16_t *__restrict__ rec, const T (&bd)[kPatchMax],
                                            T *__restrict__ out) {
+    constexpr bool lumped = LUMP;
     // the 24-byte record as three 8-byte loads: [m, a, b, r0], [r1..r4], [r5, r6, -, -]
     const ushort4 q0 = reinterpret_cast<const ushort4 *>(rec)[0];
     const ushort4 q1 = reinterpret_cast<const ushort4 *>(rec)[1];
@@ -368,10 +372,11 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
             T o0, o1, o2, o3;
             if (DIAG) {
                 const T c0x = -(c1x - w1x + w0x), c0y = -(c1y - w1y + w0y), c0z = -(c1z - w1z + w0z);
-                o0 = cm * (T(2) * S + T(4) * aa) + kc * (c0x * c0x + c0y * c0y + c0z * c0z);
-                o1 = cm * (T(2) * S + T(4) * ab) + kc * (c1x * c1x + c1y * c1y + c1z * c1z);
-                o2 = cm * (T(2) * S + T(4) * a2) + kc * (w1x * w1x + w1y * w1y + w1z * w1z);
-                o3 = cm * (T(2) * S + T(4) * a3) + kc * (w0x * w0x + w0y * w0y + w0z * w0z);
+                const T cl = ad * T(1.0 / 24.0);
+                o0 = (lumped ? cl * aa : cm * (T(2) * S + T(4) * aa)) + kc * (c0x * c0x + c0y * c0y + c0z * c0z);
+                o1 = (lumped ? cl * ab : cm * (T(2) * S + T(4) * ab)) + kc * (c1x * c1x + c1y * c1y + c1z * c1z);
+                o2 = (lumped ? cl * a2 : cm * (T(2) * S + T(4) * a2)) + kc * (w1x * w1x + w1y * w1y + w1z * w1z);
+                o3 = (lumped ? cl * a3 : cm * (T(2) * S + T(4) * a3)) + kc * (w0x * w0x + w0y * w0y + w0z * w0z);
             } else {
                 // g = (vb - va) c1 + (v0 - va) c2 + (v1 - va) c3, c2 = -w1, c3 = w0
                 const T t1 = vb - va, t2 = v0 - va, t3 = v1 - va;
@@ -382,13 +387,21 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
                 const T k2 = -kc * (w1x * gx + w1y * gy + w1z * gz);
                 const T k3 = kc * (w0x * gx + w0y * gy + w0z * gz);
                 const T k0 = -(k1 + k2 + k3);
-                const T X = (va + vb) + (v0 + v1);
-                const T Q = (aa * va + ab * vb) + (a2 * v0 + a3 * v1);
-                const T base = S * X + Q;
-                o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
-                o1 = cm * (base + S * vb + ab * (X + T(2) * vb)) + k1;
-                o2 = cm * (base + S * v0 + a2 * (X + T(2) * v0)) + k2;
-                o3 = cm * (base + S * v1 + a3 * (X + T(2) * v1)) + k3;
+                if constexpr (lumped) {
+                    const T cl = ad * T(1.0 / 24.0);
+                    o0 = cl * aa * va + k0;
+                    o1 = cl * ab * vb + k1;
+                    o2 = cl * a2 * v0 + k2;
+                    o3 = cl * a3 * v1 + k3;
+                } else {
+                    const T X = (va + vb) + (v0 + v1);
+                    const T Q = (aa * va + ab * vb) + (a2 * v0 + a3 * v1);
+                    const T base = S * X + Q;
+                    o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
+                    o1 = cm * (base + S * vb + ab * (X + T(2) * vb)) + k1;
+                    o2 = cm * (base + S * v0 + a2 * (X + T(2) * v0)) + k2;
+                    o3 = cm * (base + S * v1 + a3 * (X + T(2) * v1)) + k3;
+                }
             }
             acc_a += o0;
             acc_b += o1;
@@ -423,20 +436,28 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
             T o0, o1, o2;
             if (DIAG) {
                 const T c0x = -(c1x + c2x), c0y = -(c1y + c2y);
-                o0 = cm * (T(2) * S + T(4) * aa) + kc * (c0x * c0x + c0y * c0y);
-                o1 = cm * (T(2) * S + T(4) * a1) + kc * (c1x * c1x + c1y * c1y);
-                o2 = cm * (T(2) * S + T(4) * a2) + kc * (c2x * c2x + c2y * c2y);
+                const T cl = ad * T(1.0 / 6.0);
+                o0 = (lumped ? cl * aa : cm * (T(2) * S + T(4) * aa)) + kc * (c0x * c0x + c0y * c0y);
+                o1 = (lumped ? cl * a1 : cm * (T(2) * S + T(4) * a1)) + kc * (c1x * c1x + c1y * c1y);
+                o2 = (lumped ? cl * a2 : cm * (T(2) * S + T(4) * a2)) + kc * (c2x * c2x + c2y * c2y);
             } else {
                 const T t1 = v0 - va, t2 = v1 - va;
                 const T gx = t1 * c1x + t2 * c2x, gy = t1 * c1y + t2 * c2y;
                 const T k1 = kc * (c1x * gx + c1y * gy);
                 const T k2 = kc * (c2x * gx + c2y * gy);
                 const T k0 = -(k1 + k2);
-                const T X = va + v0 + v1, Q = aa * va + a1 * v0 + a2 * v1;
-                const T base = S * X + Q;
-                o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
-                o1 = cm * (base + S * v0 + a1 * (X + T(2) * v0)) + k1;
-                o2 = cm * (base + S * v1 + a2 * (X + T(2) * v1)) + k2;
+                if constexpr (lumped) {
+                    const T cl = ad * T(1.0 / 6.0);
+                    o0 = cl * aa * va + k0;
+                    o1 = cl * a1 * v0 + k1;
+                    o2 = cl * a2 * v1 + k2;
+                } else {
+                    const T X = va + v0 + v1, Q = aa * va + a1 * v0 + a2 * v1;
+                    const T base = S * X + Q;
+                    o0 = cm * (base + S * va + aa * (X + T(2) * va)) + k0;
+                    o1 = cm * (base + S * v0 + a1 * (X + T(2) * v0)) + k1;
+                    o2 = cm * (base + S * v1 + a2 * (X + T(2) * v1)) + k2;
+                }
             }
             acc_a += o0;
             out[2 + j] = acc_c + o1;

@@ -59,7 +59,8 @@ int ensure_workspace(ps_mesh *m);
 template <typename T, int MODE>
 int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 
-int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s);
+int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s, bool diag = true);
+int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s);
 
 // projection.cu
 void projection_release(ps_mesh *m);
@@ -100,6 +101,7 @@ struct ps_mesh {
     int update_bps = 0;                // ps_mesh_opts::update_blocks_per_sm
     bool k1_pre = false;               // FP32 operator kernel variant (beta prefetch)
     bool coeff_ok = false, alpha_set = false;
+    bool alpha_newton = false;         // alpha last set by the general-EOS Newton iteration
     double dt2 = 0.0;
     ps::Workspace ws;
     void *batch_ws = nullptr;   // owned by batched.cu

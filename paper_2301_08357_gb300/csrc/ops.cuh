@@ -42,6 +42,7 @@ struct MeshDev {
     const double *dinv64;
     const uint8_t *dirichlet;
     int *err;
+    int lumped;              // 1: mass term by vertex quadrature (mass-lumped variant)
     SmemLayout sm32, sm64;
 };
 
@@ -150,16 +151,26 @@ __device__ __forceinline__ bool stage_wait(const MeshDev &m, const ChunkSmem<T> 
     return ok;
 }
 
-// Element contributions of every star patch of the chunk into S.contrib.
+// Element contributions of every star patch of the chunk into S.contrib
+// (the mesh's mass form chosen once per chunk, so each variant of the loop
+// is compiled on its own).
 template <int D, typename T, bool DIAG>
 __device__ __forceinline__ void patches_eval(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S) {
     using N4 = typename NodeOf<T>::type;
     const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
     const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
-    for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
-        T bd[kPatchMax];
-        load_bd(g_bdt2 + q * kPatchMax, bd);
-        patch_eval<D, T, N4, DIAG>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+    if (m.lumped) {
+        for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
+            T bd[kPatchMax];
+            load_bd(g_bdt2 + q * kPatchMax, bd);
+            patch_eval<D, T, N4, DIAG, true>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+        }
+    } else {
+        for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
+            T bd[kPatchMax];
+            load_bd(g_bdt2 + q * kPatchMax, bd);
+            patch_eval<D, T, N4, DIAG>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+        }
     }
     __syncthreads();
 }
@@ -182,23 +193,32 @@ __device__ __forceinline__ void prefetch_bd(const MeshDev &m, const ChunkDesc &c
         if (q < cd.n_patch) load_bd(g_bdt2 + q * kPatchMax, P.v[k]);
     }
 }
-template <int D, typename T>
-__device__ __forceinline__ void patches_eval_pre(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S,
-                                                 const BdPrefetch<T> &P) {
+template <int D, typename T, bool LUMP>
+__device__ __forceinline__ void patches_eval_pre_v(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S,
+                                                   const BdPrefetch<T> &P) {
     using N4 = typename NodeOf<T>::type;
 #pragma unroll
     for (int k = 0; k < kBdRounds; ++k) {
         const int q = threadIdx.x + k * blockDim.x;
         if (q < cd.n_patch)
-            patch_eval<D, T, N4, false>(S.node, S.val, S.pids + q * kPatchIds, P.v[k], S.contrib + q * kPatchSlots);
+            patch_eval<D, T, N4, false, LUMP>(S.node, S.val, S.pids + q * kPatchIds, P.v[k],
+                                              S.contrib + q * kPatchSlots);
     }
     const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
     const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
     for (int q = threadIdx.x + kBdRounds * blockDim.x; q < cd.n_patch; q += blockDim.x) {
         T bd[kPatchMax];
         load_bd(g_bdt2 + q * kPatchMax, bd);
-        patch_eval<D, T, N4, false>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
+        patch_eval<D, T, N4, false, LUMP>(S.node, S.val, S.pids + q * kPatchIds, bd, S.contrib + q * kPatchSlots);
     }
+}
+template <int D, typename T>
+__device__ __forceinline__ void patches_eval_pre(const MeshDev &m, const ChunkDesc &cd, const ChunkSmem<T> &S,
+                                                 const BdPrefetch<T> &P) {
+    if (m.lumped)
+        patches_eval_pre_v<D, T, true>(m, cd, S, P);
+    else
+        patches_eval_pre_v<D, T, false>(m, cd, S, P);
     __syncthreads();
 }
 
@@ -555,6 +575,25 @@ static __global__ void k_set_alpha(int64_t n_loc, const int32_t *__restrict__ lo
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_loc; k += (int64_t)gridDim.x * blockDim.x) {
         const int g = loc_node[k];
         const double a = alpha_new[g];
+        double w64 = a;
+        float w32 = (float)a;
+        if (dirichlet[g]) {
+            w64 = __longlong_as_double(__double_as_longlong(w64) | (long long)0x8000000000000000ULL);
+            w32 = __int_as_float(__float_as_int(w32) | (int)0x80000000u);
+        }
+        node64[k].w = w64;
+        node32[k].w = w32;
+    }
+}
+
+// The same from caller-numbered alpha: unknown g takes alpha of its master
+// vertex old_of_new[g].
+static __global__ void k_set_alpha_user(int64_t n_loc, const int32_t *__restrict__ loc_node,
+                                        const int32_t *__restrict__ old_of_new, const double *__restrict__ alpha_user,
+                                        const uint8_t *__restrict__ dirichlet, NodeF *node32, NodeD *node64) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_loc; k += (int64_t)gridDim.x * blockDim.x) {
+        const int g = loc_node[k];
+        const double a = alpha_user[old_of_new[g]];
         double w64 = a;
         float w32 = (float)a;
         if (dirichlet[g]) {

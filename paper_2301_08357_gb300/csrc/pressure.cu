@@ -455,11 +455,15 @@ extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, cons
     return PS_OK;
 }
 
+static void free_graphs(ps_mesh *m) {
+    for (auto &g : m->ws.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    m->ws.graphs.clear();
+}
+
 static void free_workspace(ps_mesh *m) {
     Workspace &w = m->ws;
-    for (auto &g : w.graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-    w.graphs.clear();
+    free_graphs(m);
     if (w.cap_stream) cudaStreamDestroy(w.cap_stream);
     w.cap_stream = nullptr;
     if (w.h_st) cudaFreeHost(w.h_st);
@@ -585,6 +589,7 @@ extern "C" int ps_coeff_set(ps_mesh *m, const double *alpha, const double *beta,
     int rc = coeff_upload(m, alpha, beta, dt2);
     if (rc == PS_OK) {
         m->alpha_set = true;
+        m->alpha_newton = false;
         m->alpha_host.assign(alpha, alpha + p.n_nodes);
         m->alpha_version += 1;
     }
@@ -605,18 +610,11 @@ extern "C" int ps_coeff_set_beta(ps_mesh *m, const double *beta) {
 // ---------------------------------------------------------------- workspace
 namespace ps {
 
-// beta (caller's element order, device) -> beta*dt^2 per patch slot and the
-// Jacobi diagonal, on stream s without allocating or synchronising (the
-// projection stage updates the operator between Picard iterations).  The
-// caller holds the context mutex.
-int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s) {
-    RC(ensure_workspace(m));
-    const PrepMesh &p = m->prep;
+// Jacobi diagonal from the mesh's current alpha, beta*dt^2 and mass form, on
+// stream s (FP64 element arithmetic, both precisions stored).  The caller
+// holds the context mutex and the workspace exists.
+static int diag_update_device(ps_mesh *m, cudaStream_t s) {
     MeshDev &d = m->dev;
-    const int64_t nslots = p.patch_total * kPatchMax;
-    k_set_beta<<<grid_for(nslots, m->ctx->sms), kBlock, 0, s>>>(nslots, m->d_elem_src, beta_dev, dt2,
-                                                                 const_cast<float *>(d.bdt2_32),
-                                                                 const_cast<double *>(d.bdt2_64));
     VecArgs<double> a;
     std::memset(&a, 0, sizeof(a));
     a.partial = m->ws.part64;
@@ -626,8 +624,39 @@ int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStrea
         k_chunks<3, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
     k_shared<double, kDiag><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
     CK(cudaGetLastError());
-    m->dt2 = dt2;
     return PS_OK;
+}
+
+// beta (caller's element order, device) -> beta*dt^2 per patch slot and the
+// Jacobi diagonal, on stream s without allocating or synchronising (the
+// projection stage updates the operator between Picard iterations).  The
+// caller holds the context mutex.
+int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s, bool diag) {
+    RC(ensure_workspace(m));
+    const PrepMesh &p = m->prep;
+    MeshDev &d = m->dev;
+    const int64_t nslots = p.patch_total * kPatchMax;
+    k_set_beta<<<grid_for(nslots, m->ctx->sms), kBlock, 0, s>>>(nslots, m->d_elem_src, beta_dev, dt2,
+                                                                 const_cast<float *>(d.bdt2_32),
+                                                                 const_cast<double *>(d.bdt2_64));
+    CK(cudaGetLastError());
+    m->dt2 = dt2;
+    return diag ? diag_update_device(m, s) : PS_OK;
+}
+
+// Nodal alpha (caller's numbering, device; each unknown takes its master
+// vertex's value) into both node records, then the Jacobi diagonal; on
+// stream s without allocating or synchronising.  The caller holds the
+// context mutex.
+int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s) {
+    RC(ensure_workspace(m));
+    const PrepMesh &p = m->prep;
+    MeshDev &d = m->dev;
+    k_set_alpha_user<<<grid_for(p.loc_total, m->ctx->sms), kBlock, 0, s>>>(
+        p.loc_total, m->d_loc_node, m->d_old_of_new, alpha_dev, d.dirichlet, const_cast<NodeF *>(d.node32),
+        const_cast<NodeD *>(d.node64));
+    CK(cudaGetLastError());
+    return diag_update_device(m, s);
 }
 
 int ensure_workspace(ps_mesh *m) {
@@ -1225,4 +1254,21 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return check_dev_err(m->ctx);
+}
+
+// ---------------------------------------------------------------- ABI: mass form
+extern "C" int ps_mesh_set_mass(ps_mesh *m, int mass) {
+    if (!m || (mass != PS_MASS_CONSISTENT && mass != PS_MASS_LUMPED)) return PS_EINVAL;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    const int lumped = mass == PS_MASS_LUMPED ? 1 : 0;
+    if (m->dev.lumped == lumped) return PS_OK;
+    m->dev.lumped = lumped;
+    // captured solve graphs hold the mesh descriptor by value
+    free_graphs(m);
+    if (!m->coeff_ok) return PS_OK;
+    RC(ensure_workspace(m));
+    RC(ps::diag_update_device(m, nullptr));
+    CK(cudaDeviceSynchronize());
+    return PS_OK;
 }

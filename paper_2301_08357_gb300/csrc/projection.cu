@@ -23,6 +23,7 @@ namespace ps {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kRedBlocks = 256;   // fixed grid of the norm pass (deterministic order)
 
 // Device data of the element passes (caller's numbering), built on first use.
 struct ProjData {
@@ -36,6 +37,15 @@ struct ProjData {
     double *b = nullptr;          // [n_nodes] right-hand side
     int *flag = nullptr;          // enthalpy check
     int64_t alpha_version = -1;
+    // general-EOS Newton iteration (allocated on its first call)
+    std::vector<DevAlloc> eos_allocs;
+    double *mi = nullptr;         // [n_nodes] m_i = sum_e |T_e| / (d+1)
+    double *si = nullptr;         // [n_nodes] s_i = sum_e |T_e| / ((d+1) rho_e)
+    double *c = nullptr;          // [n_nodes] right-hand side without the mass term
+    double *r = nullptr;          // [n_nodes] Newton right-hand side J dP - F(dP)
+    double *au = nullptr;         // [n_nodes] alpha_i = Q'_i / m_i
+    double *y = nullptr;          // [n_nodes] J dP
+    double *red = nullptr;        // [2 * kRedBlocks] partial sums of ||F||^2, ||c||^2
 };
 
 int cuda_rc(cudaError_t e) {
@@ -75,17 +85,25 @@ __device__ __forceinline__ double cofactors(const double (&v)[D + 1][D], double 
     }
 }
 
-// First guesses: H_e = g1 mean_k(P_k) / rho_e, (rho K)_e = |W~~_u,e|^2 / (2 rho_e).
+// Element enthalpy from the vertex mean Pbar of the pressure:
+// H_e = (h1 Pbar + hb Pbar^2 / rho_e) / rho_e, i.e. (rho e(Pbar) + Pbar) / rho_e
+// for rho e = a P + b P^2 / rho (h1 = a + 1, hb = b; the ideal gas passes
+// h1 = gamma / (gamma - 1), hb = 0).
+__device__ __forceinline__ double enthalpy(double pbar, double rho, double h1, double hb) {
+    return (h1 * pbar + hb * pbar * pbar / rho) / rho;
+}
+
+// First guesses: H_e from P^n, (rho K)_e = |W~~_u,e|^2 / (2 rho_e).
 template <int D>
 __global__ void __launch_bounds__(kT) k_pj_first(int64_t n_el, const int32_t *__restrict__ conn,
                                                  const double *__restrict__ p, const double *__restrict__ rho,
-                                                 const double *__restrict__ wu, double g1, double *__restrict__ H,
-                                                 double *__restrict__ rhok) {
+                                                 const double *__restrict__ wu, double h1, double hb,
+                                                 double *__restrict__ H, double *__restrict__ rhok) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
         double pb = 0.0, u2 = 0.0;
         for (int k = 0; k <= D; ++k) pb += p[conn[e * (D + 1) + k]];
         for (int a = 0; a < D; ++a) u2 += wu[e * D + a] * wu[e * D + a];
-        H[e] = g1 * (pb / (D + 1)) / rho[e];
+        H[e] = enthalpy(pb / (D + 1), rho[e], h1, hb);
         rhok[e] = 0.5 * u2 / rho[e];
     }
 }
@@ -101,7 +119,8 @@ __global__ void __launch_bounds__(kT) k_pj_check(int64_t n, const double *__rest
 // + dt H_e |T| W~~_u,e . grad lambda_k                 divergence term
 // - (M^e_alpha P^n)_k = cm (S X + Q + S P_k + alpha_k (X + 2 P_k))
 // with k the local index of i in e, S = sum alpha, X = sum P, Q = sum alpha P
-// over the element's vertices and cm = |T| d! / (d+3)!.
+// over the element's vertices and cm = |T| d! / (d+3)!.  alpha == nullptr
+// drops the mass term (the general-EOS residual carries it itself).
 template <int D>
 __global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *__restrict__ n2e_ptr,
                                                const int32_t *__restrict__ n2e, const int32_t *__restrict__ conn,
@@ -127,8 +146,8 @@ __global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *_
             for (int q = 0; q <= D; ++q) {
                 const int64_t g = conn[e * (D + 1) + q];
                 for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
-                al[q] = alpha[g];
-                pv[q] = p[g];
+                al[q] = alpha ? alpha[g] : 0.0;
+                pv[q] = alpha ? p[g] : 0.0;
             }
             const double det = cofactors<D>(v, c);
             const double adet = fabs(det);
@@ -143,7 +162,7 @@ __global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *_
                 Q += al[q] * pv[q];
             }
             const double cm = adet / cmden;
-            const double mass = cm * (S * X + Q + S * pv[k] + al[k] * (X + 2.0 * pv[k]));
+            const double mass = alpha ? cm * (S * X + Q + S * pv[k] + al[k] * (X + 2.0 * pv[k])) : 0.0;
             acc += (we[e] - rhok[e]) * vol / (D + 1) + dt * H[e] * sgn * cw / fact - mass;
         }
         b[i] = acc;
@@ -151,12 +170,12 @@ __global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *_
 }
 
 // Post-projection: W_u = W~~_u - dt grad dP_h, P = P^n + dP (vertex mean for
-// H), H = g1 mean(P) / rho, rho K = |W_u|^2 / (2 rho).
+// H), H from it (enthalpy above), rho K = |W_u|^2 / (2 rho).
 template <int D>
 __global__ void __launch_bounds__(kT) k_pj_post(int64_t n_el, const int32_t *__restrict__ conn,
                                                 const double *__restrict__ x, const double *__restrict__ pn,
                                                 const double *__restrict__ dp, const double *__restrict__ wu_tt,
-                                                const double *__restrict__ rho, double g1, double dt,
+                                                const double *__restrict__ rho, double h1, double hb, double dt,
                                                 double *__restrict__ wu_new, double *__restrict__ H,
                                                 double *__restrict__ rhok) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
@@ -177,7 +196,7 @@ __global__ void __launch_bounds__(kT) k_pj_post(int64_t n_el, const int32_t *__r
             wu_new[e * D + a] = u;
             u2 += u * u;
         }
-        H[e] = g1 * (pb / (D + 1)) / rho[e];
+        H[e] = enthalpy(pb / (D + 1), rho[e], h1, hb);
         rhok[e] = 0.5 * u2 / rho[e];
     }
 }
@@ -186,6 +205,87 @@ __global__ void __launch_bounds__(kT) k_pj_add(int64_t n, const double *__restri
                                                double *__restrict__ y) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a[i] + b[i];
+}
+
+// Lumped nodal weights of the general-EOS mass sum, gathered per node over
+// its elements in ascending order: m_i = sum_e w_ei, s_i = sum_e w_ei / rho_e,
+// w_ei = |T_e| / (d+1) (vertex quadrature).
+template <int D>
+__global__ void __launch_bounds__(kT) k_nt_weights(int64_t n_nodes, const int64_t *__restrict__ n2e_ptr,
+                                                   const int32_t *__restrict__ n2e, const int32_t *__restrict__ conn,
+                                                   const double *__restrict__ x, const double *__restrict__ rho,
+                                                   double *__restrict__ mi, double *__restrict__ si) {
+    constexpr double fact = D == 3 ? 6.0 : 2.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0, sr = 0.0;
+        for (int64_t t = n2e_ptr[i]; t < n2e_ptr[i + 1]; ++t) {
+            const int64_t e = n2e[t] >> 2;
+            double v[D + 1][D], c[D + 1][D];
+            for (int q = 0; q <= D; ++q) {
+                const int64_t g = conn[e * (D + 1) + q];
+                for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
+            }
+            const double w = fabs(cofactors<D>(v, c)) / fact / (D + 1);
+            m += w;
+            sr += w / rho[e];
+        }
+        mi[i] = m;
+        si[i] = sr;
+    }
+}
+
+// One Newton linearisation at dP (rho e = a P + b P^2 / rho, P = P^n + dP):
+//   Q_i = sum_e w_ei rho e(P_i, rho_e) = P_i (a m_i + b s_i P_i)
+//   Q'_i = a m_i + 2 b s_i P_i,   alpha_i = Q'_i / m_i
+//   r_i = c_i - Q_i + Q'_i dP_i   (J dP - F(dP); 0 on Dirichlet nodes)
+// flag: a free node whose Q'_i is not positive and finite.
+__global__ void __launch_bounds__(kT) k_nt_linearise(int64_t n, const uint8_t *__restrict__ dir,
+                                                     const double *__restrict__ pn, const double *__restrict__ dp,
+                                                     const double *__restrict__ mi, const double *__restrict__ si,
+                                                     const double *__restrict__ c, double a, double b,
+                                                     double *__restrict__ alpha, double *__restrict__ r, int *flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double P = pn[i] + dp[i];
+        const double m = mi[i], sw = si[i];
+        const double q = P * (a * m + b * sw * P);
+        const double qp = a * m + 2.0 * b * sw * P;
+        alpha[i] = m > 0.0 ? qp / m : a;
+        if (dir[i]) {
+            r[i] = 0.0;
+            continue;
+        }
+        if (!(qp > 0.0) || !isfinite(qp)) atomicOr(flag, 1);
+        r[i] = c[i] - q + qp * dp[i];
+    }
+}
+
+// Partial sums over free nodes of |J dP - r|^2 = |F(dP)|^2 and |c|^2, one per
+// block of a fixed grid (kRedBlocks); the host adds them in block order.
+__global__ void __launch_bounds__(kT) k_nt_norms(int64_t n, const uint8_t *__restrict__ dir,
+                                                 const double *__restrict__ y, const double *__restrict__ r,
+                                                 const double *__restrict__ c, double *__restrict__ red) {
+    __shared__ double sf[kT], sc[kT];
+    double f = 0.0, cc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (dir[i]) continue;
+        const double d = y[i] - r[i];
+        f += d * d;
+        cc += c[i] * c[i];
+    }
+    sf[threadIdx.x] = f;
+    sc[threadIdx.x] = cc;
+    __syncthreads();
+    for (int w = kT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sf[threadIdx.x] += sf[threadIdx.x + w];
+            sc[threadIdx.x] += sc[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        red[blockIdx.x] = sf[0];
+        red[kRedBlocks + blockIdx.x] = sc[0];
+    }
 }
 
 int grid(int64_t n, int sms) {
@@ -263,11 +363,39 @@ int ensure_proj(ps_mesh *m) {
         }
         m->proj = P;
     }
-    if (P->alpha_version != m->alpha_version) {
+    if (P->alpha_version != m->alpha_version && (int64_t)m->alpha_host.size() == N) {
         cudaError_t er = cudaMemcpy(P->alpha, m->alpha_host.data(), (size_t)N * 8, cudaMemcpyHostToDevice);
         if (er != cudaSuccess) return cuda_rc(er);
         P->alpha_version = m->alpha_version;
     }
+    return PS_OK;
+}
+
+// Device arrays of the general-EOS Newton iteration.  The caller holds the
+// context mutex.
+int ensure_eos(ps_mesh *m) {
+    ProjData *P = static_cast<ProjData *>(m->proj);
+    if (P->mi) return PS_OK;
+    const int64_t N = m->prep.n_nodes;
+    double **dst[] = {&P->mi, &P->si, &P->c, &P->r, &P->au, &P->y};
+    for (double **d : dst) {
+        void *q = nullptr;
+        int rc = dalloc(m->ctx, &q, (size_t)N * 8, P->eos_allocs);
+        if (rc == PS_OK) *d = (double *)q;
+        else {
+            dfree_all(m->ctx, P->eos_allocs);
+            for (double **e : dst) *e = nullptr;
+            return rc;
+        }
+    }
+    void *q = nullptr;
+    int rc = dalloc(m->ctx, &q, 2 * kRedBlocks * 8, P->eos_allocs);
+    if (rc != PS_OK) {
+        dfree_all(m->ctx, P->eos_allocs);
+        for (double **e : dst) *e = nullptr;
+        return rc;
+    }
+    P->red = (double *)q;
     return PS_OK;
 }
 
@@ -293,6 +421,7 @@ int check_positive(ps_mesh *m, const double *H, cudaStream_t s) {
 void projection_release(ps_mesh *m) {
     if (!m->proj) return;
     ProjData *P = static_cast<ProjData *>(m->proj);
+    dfree_all(m->ctx, P->eos_allocs);
     dfree_all(m->ctx, P->allocs);
     delete P;
     m->proj = nullptr;
@@ -317,7 +446,7 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
     if (!m || !o || !rho || !wu || !we || !pn || !dp || !p_out || !wu_out || !h_out || !rhok_out) return PS_EINVAL;
     if (!(o->gamma > 1.0) || !std::isfinite(o->gamma) || !(o->dt > 0.0) || !std::isfinite(o->dt)) return PS_EINVAL;
     if (o->n_picard < 1 || o->n_picard > 64) return PS_EINVAL;
-    if (!m->coeff_ok || !m->alpha_set) return PS_ESTATE;
+    if (!m->coeff_ok || !m->alpha_set || m->alpha_newton) return PS_ESTATE;
     if (m->prep.n_elems >= ((int64_t)1 << 29)) return PS_EINVAL;   // element * 4 + vertex fits in int32
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
@@ -335,8 +464,8 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
         if (rc != PS_OK) return rc;
         ProjData *P = static_cast<ProjData *>(m->proj);
         const int g = grid(E, m->ctx->sms);
-        if (dim == 3) k_pj_first<3><<<g, kT, 0, s>>>(E, P->conn, pn, rho, wu, g1, h_out, rhok_out);
-        else k_pj_first<2><<<g, kT, 0, s>>>(E, P->conn, pn, rho, wu, g1, h_out, rhok_out);
+        if (dim == 3) k_pj_first<3><<<g, kT, 0, s>>>(E, P->conn, pn, rho, wu, g1, 0.0, h_out, rhok_out);
+        else k_pj_first<2><<<g, kT, 0, s>>>(E, P->conn, pn, rho, wu, g1, 0.0, h_out, rhok_out);
         rc = cuda_rc(cudaGetLastError());
         if (rc != PS_OK) return rc;
     }
@@ -371,9 +500,9 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
             ProjData *P = static_cast<ProjData *>(m->proj);
             const int g = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, dt, wu_out, h_out, rhok_out);
+                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
             else
-                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, dt, wu_out, h_out, rhok_out);
+                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
             k_pj_add<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, pn, dp, p_out);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
@@ -382,5 +511,184 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
     if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
     acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = acc;
+    return rc;
+}
+
+// ---------------------------------------------------------------- general EOS
+extern "C" void ps_eos_opts_default(ps_eos_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->eos_a = 2.5;
+    o->eos_b = 0.0;
+    o->dt = 0.0;
+    o->n_picard = 2;
+    o->max_newton = 8;
+    o->newton_tol = 1e-8;
+    ps_solve_opts_default(&o->solve);
+}
+
+namespace {
+
+void add_solve(ps_solve_info &acc, const ps_solve_info &inf) {
+    const int64_t it_in = acc.iters_inner + inf.iters_inner, it_out = acc.iters_outer + inf.iters_outer;
+    const int64_t launches = acc.kernel_launches + inf.kernel_launches;
+    acc = inf;
+    acc.iters_inner = it_in;
+    acc.iters_outer = it_out;
+    acc.kernel_launches = launches;
+}
+
+// ||F(dP)|| / ||c|| over the free nodes, F = J dP - r with J the lumped
+// operator now on the mesh (FP64 apply); deterministic (fixed-order sums).
+int newton_residual(ps_mesh *m, const double *dp, cudaStream_t s, double *res) {
+    ProjData *P = static_cast<ProjData *>(m->proj);
+    int rc = ps_pressure_apply(m, dp, P->y, PS_F64, s);
+    if (rc != PS_OK) return rc;
+    std::vector<double> red(2 * kRedBlocks);
+    {
+        std::lock_guard<std::mutex> lk(m->ctx->mu);
+        k_nt_norms<<<kRedBlocks, kT, 0, s>>>(m->prep.n_nodes, P->dir, P->y, P->r, P->c, P->red);
+        rc = cuda_rc(cudaGetLastError());
+        if (rc == PS_OK)
+            rc = cuda_rc(cudaMemcpyAsync(red.data(), P->red, red.size() * 8, cudaMemcpyDeviceToHost, s));
+        if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+        if (rc != PS_OK) return rc;
+    }
+    double ff = 0.0, cc = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) {
+        ff += red[b];
+        cc += red[kRedBlocks + b];
+    }
+    *res = std::sqrt(ff) / (cc > 0.0 ? std::sqrt(cc) : 1.0);
+    return PS_OK;
+}
+
+}  // namespace
+
+extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const double *rho, const double *wu,
+                                      const double *we, const double *pn, double *dp, double *p_out,
+                                      double *wu_out, double *h_out, double *rhok_out, double *res_host,
+                                      ps_solve_info *info, void *stream) {
+    if (!m || !o || !rho || !wu || !we || !pn || !dp || !p_out || !wu_out || !h_out || !rhok_out) return PS_EINVAL;
+    if (!(o->eos_a > 0.0) || !std::isfinite(o->eos_a) || !(o->eos_b >= 0.0) || !std::isfinite(o->eos_b))
+        return PS_EINVAL;
+    if (!(o->dt > 0.0) || !std::isfinite(o->dt) || std::isnan(o->newton_tol)) return PS_EINVAL;
+    if (o->n_picard < 1 || o->n_picard > 64 || o->max_newton < 1 || o->max_newton > 64) return PS_EINVAL;
+    if (m->d_slave_ptr) {
+        ps_set_last_error("general-EOS projection: periodic meshes are not supported");
+        return PS_EINVAL;
+    }
+    if (!m->dev.lumped) {
+        ps_set_last_error("general-EOS projection: the mesh needs lumped mass (ps_mesh_set_mass)");
+        return PS_ESTATE;
+    }
+    if (m->prep.n_elems >= ((int64_t)1 << 29)) return PS_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int dim = m->prep.dim;
+    const int64_t N = m->prep.n_nodes, E = m->prep.n_elems;
+    const double a = o->eos_a, b = o->eos_b, dt = o->dt;
+    const double h1 = a + 1.0, hb = b;
+    const double tol = o->newton_tol;
+    const bool check = tol > 0.0 || res_host;
+    const int stride = o->max_newton + 1;
+    if (res_host)
+        for (int k = 0; k < o->n_picard * stride; ++k) res_host[k] = -1.0;
+    ps_solve_info acc;
+    std::memset(&acc, 0, sizeof(acc));
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(m->ctx->mu);
+        rc = cuda_rc(cudaSetDevice(m->ctx->device));
+        if (rc == PS_OK) rc = ensure_proj(m);
+        if (rc == PS_OK) rc = ensure_eos(m);
+        if (rc != PS_OK) return rc;
+        ProjData *P = static_cast<ProjData *>(m->proj);
+        const int ge = grid(E, m->ctx->sms), gn = grid(N, m->ctx->sms);
+        if (dim == 3) {
+            k_pj_first<3><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
+            k_nt_weights<3><<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, rho, P->mi, P->si);
+        } else {
+            k_pj_first<2><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
+            k_nt_weights<2><<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, rho, P->mi, P->si);
+        }
+        rc = cuda_rc(cudaGetLastError());
+        if (rc != PS_OK) return rc;
+    }
+    bool converged = true;
+    for (int k = 0; k < o->n_picard && rc == PS_OK; ++k) {
+        {
+            std::lock_guard<std::mutex> lk(m->ctx->mu);
+            ProjData *P = static_cast<ProjData *>(m->proj);
+            rc = check_positive(m, h_out, s);
+            if (rc == PS_OK) rc = beta_update_device(m, h_out, dt * dt, s, false);
+            if (rc != PS_OK) return rc;
+            const int g = grid(N, m->ctx->sms);
+            if (dim == 3)
+                k_pj_rhs<3><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, nullptr, P->dir, h_out, rhok_out,
+                                             wu, we, pn, dt, P->c);
+            else
+                k_pj_rhs<2><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, nullptr, P->dir, h_out, rhok_out,
+                                             wu, we, pn, dt, P->c);
+            rc = cuda_rc(cudaGetLastError());
+            if (rc != PS_OK) return rc;
+        }
+        converged = !(tol > 0.0);
+        for (int j = 0;; ++j) {
+            {
+                std::lock_guard<std::mutex> lk(m->ctx->mu);
+                ProjData *P = static_cast<ProjData *>(m->proj);
+                rc = cuda_rc(cudaMemsetAsync(P->flag, 0, sizeof(int), s));
+                if (rc != PS_OK) return rc;
+                k_nt_linearise<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->dir, pn, dp, P->mi, P->si, P->c, a, b,
+                                                                    P->au, P->r, P->flag);
+                int h = 0;
+                rc = cuda_rc(cudaMemcpyAsync(&h, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+                if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+                if (rc != PS_OK) return rc;
+                if (h) {
+                    ps_set_last_error("general-EOS projection: a Jacobian entry Q'_i is not positive and finite");
+                    return PS_EINVAL;
+                }
+                rc = alpha_update_device(m, P->au, s);
+                if (rc != PS_OK) return rc;
+                m->coeff_ok = true;
+                m->alpha_set = true;
+                m->alpha_newton = true;
+            }
+            if (check) {
+                double res = 0.0;
+                rc = newton_residual(m, dp, s, &res);
+                if (rc != PS_OK) return rc;
+                if (res_host) res_host[k * stride + j] = res;
+                if (tol > 0.0 && res <= tol) {
+                    converged = true;
+                    break;
+                }
+            }
+            if (j == o->max_newton) break;
+            ps_solve_info inf;
+            rc = ps_pressure_solve(m, static_cast<ProjData *>(m->proj)->r, dp, &o->solve, &inf, stream);
+            add_solve(acc, inf);
+            if (rc != PS_OK) break;
+        }
+        if (rc != PS_OK) break;
+        {
+            std::lock_guard<std::mutex> lk(m->ctx->mu);
+            ProjData *P = static_cast<ProjData *>(m->proj);
+            const int g = grid(E, m->ctx->sms);
+            if (dim == 3)
+                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
+            else
+                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
+            k_pj_add<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, pn, dp, p_out);
+            rc = cuda_rc(cudaGetLastError());
+            if (rc != PS_OK) return rc;
+        }
+    }
+    if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+    acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = acc;
+    if (rc == PS_OK && !converged) return PS_ENOTCONV;
     return rc;
 }

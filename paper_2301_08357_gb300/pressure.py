@@ -26,6 +26,7 @@ PS_F32, PS_F64 = 1, 2
 PS_MODE_FP64, PS_MODE_MIXED = 0, 1
 PS_PRECOND_NONE, PS_PRECOND_JACOBI = 0, 1
 PS_ENGINE_AUTO, PS_ENGINE_GRAPH, PS_ENGINE_PERSISTENT, PS_ENGINE_FUSED = 0, 1, 2, 3
+PS_MASS_CONSISTENT, PS_MASS_LUMPED = 0, 1
 SOFT = {PS_OK, PS_PENDING, PS_ENOTCONV, PS_EBREAKDOWN}
 
 
@@ -93,6 +94,12 @@ class ps_server_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class ps_eos_opts(C.Structure):
+    _fields_ = [("eos_a", C.c_double), ("eos_b", C.c_double), ("dt", C.c_double), ("n_picard", C.c_int32),
+                ("max_newton", C.c_int32), ("newton_tol", C.c_double), ("reserved", C.c_double * 4),
+                ("solve", ps_solve_opts)]
+
+
 _vp, _i64, _i32, _dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
 
 # name -> (restype, argtypes); mirrors include/pressure.h plus the debug hooks.
@@ -117,6 +124,10 @@ SIGNATURES = {
     "ps_projection_opts_default": (None, [C.POINTER(ps_projection_opts)]),
     "ps_projection_step": (C.c_int, [_vp, C.POINTER(ps_projection_opts), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp, C.POINTER(ps_solve_info), _vp]),
+    "ps_mesh_set_mass": (C.c_int, [_vp, C.c_int]),
+    "ps_eos_opts_default": (None, [C.POINTER(ps_eos_opts)]),
+    "ps_projection_step_eos": (C.c_int, [_vp, C.POINTER(ps_eos_opts), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         _vp, _vp, _vp, C.POINTER(ps_solve_info), _vp]),
     "ps_solve_opts_default": (None, [C.POINTER(ps_solve_opts)]),
     "ps_batch_solve": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                                  C.POINTER(ps_solve_opts), C.POINTER(ps_solve_info), _vp]),
@@ -297,6 +308,37 @@ def ps_projection_step(mesh, rho, wu, we, pn, dp, p_out, wu_out, h_out, rhok_out
     st = _lib.ps_projection_step(mesh, C.byref(o), _dev(rho), _dev(wu), _dev(we), _dev(pn), _dev(dp), _dev(p_out),
                                  _dev(wu_out), _dev(h_out), _dev(rhok_out), C.byref(info), _stream(stream))
     return _check(st, "ps_projection_step"), info
+
+
+def ps_mesh_set_mass(mesh, mass):
+    """PS_MASS_CONSISTENT or PS_MASS_LUMPED (vertex-quadrature mass)."""
+    return _check(_lib.ps_mesh_set_mass(mesh, int(mass)), "ps_mesh_set_mass")
+
+
+def ps_eos_opts_default():
+    o = ps_eos_opts()
+    _lib.ps_eos_opts_default(C.byref(o))
+    return o
+
+
+def ps_projection_step_eos(mesh, rho, wu, we, pn, dp, p_out, wu_out, h_out, rhok_out, eos_a=2.5, eos_b=0.0,
+                           dt=None, n_picard=2, max_newton=8, newton_tol=1e-8, solve_opts=None, stream=None):
+    """Projection stage with rho e = eos_a P + eos_b P^2 / rho, lumped mass and
+    Newton's method per Picard iteration.  Returns (status, info, res) with
+    res[k, j] = ||F|| / ||c|| at Newton check j of Picard iteration k (-1:
+    no check)."""
+    o = ps_eos_opts_default()
+    o.eos_a, o.eos_b = float(eos_a), float(eos_b)
+    o.dt = float(dt) if dt is not None else 0.0
+    o.n_picard, o.max_newton, o.newton_tol = int(n_picard), int(max_newton), float(newton_tol)
+    if solve_opts is not None:
+        o.solve = solve_opts
+    res = np.full((max(int(n_picard), 1), max(int(max_newton), 0) + 1), -1.0)
+    info = ps_solve_info()
+    st = _lib.ps_projection_step_eos(mesh, C.byref(o), _dev(rho), _dev(wu), _dev(we), _dev(pn), _dev(dp),
+                                     _dev(p_out), _dev(wu_out), _dev(h_out), _dev(rhok_out),
+                                     res.ctypes.data_as(_vp), C.byref(info), _stream(stream))
+    return _check(st, "ps_projection_step_eos"), info, res
 
 
 def ps_batch_solve(meshes, b_devs, x_devs, opts=None, stream=None):
