@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "fused"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "projection", "periodic"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "projection", "periodic", "eos"],
                     help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
                          "c4 = 256-mesh batch; c5 = served Poisson stream")
     ap.add_argument("--meshes", type=int, default=256, help="c4: meshes in the batch")
@@ -655,11 +655,14 @@ def run_served(args):
     P.ps_ctx_destroy(ctx)
 
 
-def run_projection(args):
+def run_projection(args, eos=False):
     """One time step's projection stage (ps_projection_step) on the 3D Kuhn cube
     n^3 with seeded flow fields: first guesses, 2 Picard iterations of [operator
     update, right-hand side, mixed-precision solve to 1e-10, post-projection].
-    Every step starts from dP = 0 (the same work each step)."""
+    Every step starts from dP = 0 (the same work each step).
+    eos: the general-EOS step instead (ps_projection_step_eos, rho e =
+    2.5 P + 0.5 P^2 / rho, lumped mass, Newton to ||F|| <= 1e-8 ||c|| with
+    mixed-precision solves to 1e-10 inside each Picard iteration)."""
     import contextlib
     import torch
     from __graft_entry__ import build
@@ -668,11 +671,14 @@ def run_projection(args):
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
     n_pic = 2
-    case = S.make_projection_case(3, args.n)
+    case = S.make_eos_case(3, args.n) if eos else S.make_projection_case(3, args.n)
     e = case.extra
     ctx = P.ps_ctx_create(0)
     m = P.ps_mesh_upload(ctx, 3, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk)
     P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+    if eos:
+        P.ps_mesh_set_mass(m, P.PS_MASS_LUMPED)
+    n_checks = [0]
     stream = torch.cuda.current_stream()
     N, E = case.n_nodes, case.n_elems
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
@@ -685,6 +691,12 @@ def run_projection(args):
 
     def step():
         dp.zero_()
+        if eos:
+            st, info, res = P.ps_projection_step_eos(m, *ins, dp, *outs, eos_a=e["eos_a"], eos_b=e["eos_b"],
+                                                     dt=e["dt"], n_picard=n_pic, max_newton=8, newton_tol=1e-8,
+                                                     solve_opts=opts, stream=stream)
+            n_checks[0] = int((res >= 0).sum())
+            return st, info
         return P.ps_projection_step(m, *ins, dp, *outs, gamma=e["gamma"], dt=e["dt"], n_picard=n_pic,
                                     solve_opts=opts, stream=stream)
 
@@ -706,8 +718,14 @@ def run_projection(args):
             raise RuntimeError("projection step failed: %s" % P.ps_status_str(st))
         times.append(e0.elapsed_time(e1))
         iters += info.iters_inner + info.iters_outer
-        # solve launches + per Picard iteration: check, beta, diagonal (2), right-hand side, post (2); + first guess
-        launches += info.kernel_launches + 6 * n_pic + 1
+        if eos:
+            # solve launches + first guess, weights + per Picard iteration: check, beta, right-hand side,
+            # post (2) + per Newton check: linearise, alpha, diagonal (2), FP64 apply (4), norms
+            launches += info.kernel_launches + 2 + 5 * n_pic + 9 * n_checks[0]
+        else:
+            # solve launches + per Picard iteration: check, beta, diagonal (2), right-hand side, post (2);
+            # + first guess
+            launches += info.kernel_launches + 6 * n_pic + 1
     clk = clocks.stop() if not args.no_clocks else None
     tot = float(np.sum(times))
     # end to end: host inputs copied in, outputs copied back, inside the timed region
@@ -727,10 +745,25 @@ def run_projection(args):
         torch.cuda.synchronize()
         e2e.append(1e3 * (time.perf_counter() - t0))
     stats = P.ps_mesh_get_stats(m)
-    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream,
-                           "projection_3d_kuhn_%d" % args.n)
+    wname = ("eos_3d_kuhn_%d" if eos else "projection_3d_kuhn_%d") % args.n
+    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream, wname)
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and eos:
+        from oracle import lumped as LO
+        import oracle
+        n_s = min(args.n, 24)
+        cs = S.make_eos_case(3, n_s)
+        es = cs.extra
+        t0 = time.perf_counter()
+        LO.projection_step_eos(3, cs.coords, cs.conn, cs.dirichlet, es["rho"], es["wu"], es["we"], es["pn"],
+                               es["eos_a"], es["eos_b"], es["dt"], n_pic, 8, tol=1e-8)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": 1.0 / t_cpu, "unit": "steps/s (%d^3 sample)" % n_s, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": "one general-EOS projection step on the %d^3 Kuhn cube (%d free nodes; 2 Picard "
+                         "iterations, Newton with SciPy direct sparse solves), %.2f s; not in DOF-it/s: the "
+                         "oracle solves directly" % (n_s, cs.n_free, t_cpu)}
+    elif not args.no_cpu_baseline:
         from oracle import projection as PJ
         t0 = time.perf_counter()
         ref = PJ.projection_step(3, case.coords, case.conn, case.dirichlet, case.alpha, e["rho"], e["wu"], e["we"],
@@ -747,9 +780,11 @@ def run_projection(args):
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
            "data": "synthetic",
-           "config": {"workload": "projection_3d_kuhn_%d^3_picard%d" % (args.n, n_pic), "n_free": case.n_free,
+           "config": {"workload": "%s^3_picard%d" % (wname, n_pic), "n_free": case.n_free,
                       "n_elems": E, "iters_per_step": iters // max(args.steps, 1), "dt": e["dt"],
-                      "gamma": e["gamma"], "l2": "flushed between steps (256 MB write)"},
+                      "l2": "flushed between steps (256 MB write)",
+                      **({"eos": "rho e = %g P + %g P^2/rho" % (e["eos_a"], e["eos_b"]), "mass": "lumped",
+                          "newton_checks_per_step": n_checks[0]} if eos else {"gamma": e["gamma"]})},
            "steps_per_s": 1e3 * args.steps / tot, "p50_ms": _pctl(times, 50), "p99_ms": _pctl(times, 99),
            "roofline": roof, "cpu_baseline": cpu,
            "e2e": {"value": case.n_free * iters / (np.sum(e2e) / 1e3), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
@@ -772,6 +807,8 @@ def main():
         run_served(args)
     elif args.workload == "projection":
         run_projection(args)
+    elif args.workload == "eos":
+        run_projection(args, eos=True)
     else:
         run_ours(args)
 

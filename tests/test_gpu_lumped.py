@@ -151,7 +151,7 @@ def _dev(torch, a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
-def _eos_gpu(P, torch, m, case, n_picard, max_newton, tol, dp0=None, **solve_kw):
+def _eos_gpu(P, torch, m, case, n_picard, max_newton, ntol, dp0=None, **solve_kw):
     e = case.extra
     N, E, d = case.n_nodes, case.n_elems, case.dim
     dp = _dev(torch, np.zeros(N) if dp0 is None else dp0)
@@ -162,7 +162,7 @@ def _eos_gpu(P, torch, m, case, n_picard, max_newton, tol, dp0=None, **solve_kw)
     st, info, res = P.ps_projection_step_eos(m, _dev(torch, e["rho"]), _dev(torch, e["wu"]), _dev(torch, e["we"]),
                                              _dev(torch, e["pn"]), dp, *outs, eos_a=e["eos_a"], eos_b=e["eos_b"],
                                              dt=e["dt"], n_picard=n_picard, max_newton=max_newton,
-                                             newton_tol=tol, solve_opts=P.make_opts(**solve_kw))
+                                             newton_tol=ntol, solve_opts=P.make_opts(**solve_kw))
     p, wu, H, rhok = (o.cpu().numpy() for o in outs)
     return st, info, res, dp.cpu().numpy(), p, wu.reshape(E, d), H, rhok
 
