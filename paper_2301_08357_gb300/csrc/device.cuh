@@ -471,4 +471,157 @@ __device__ __forceinline__ void patch_eval(const N4 *__restrict__ s_node, const 
     }
 }
 
+// FP64 evaluation of one star patch from geometry computed once per mesh on
+// the host (mesh upload): for every element slot the symmetric stiffness
+// weights G_ab = c_a.c_b / (d! |det|) of its vertex pairs (K^e_ab = beta G_ab)
+// and |det|.  The element arithmetic per tet drops to differences, products
+// and sums (no cross products, no division), which is what matters on a GPU
+// whose FP64 rate is a small fraction of its FP32 rate.  The result equals
+// patch_eval<D, double, ...> up to rounding.
+// Slot layout, 3D (8 doubles): G_AB, G_A0, G_A1, G_B0, G_B1, G_01, |det|, 0
+// with A, B the patch's edge and 0, 1 ring nodes j, j+1; 2D (4 doubles):
+// G_A0, G_A1, G_01, |det|.  Rows of G sum to zero (sum_a c_a = 0), so
+// (K^e v)_a = beta sum_b G_ab (v_b - v_a) and G_aa = -sum_{b != a} G_ab.
+template <int D, bool DIAG, bool LUMP>
+__device__ __forceinline__ void patch_eval_geo(const NodeD *__restrict__ s_node, const double *__restrict__ s_val,
+                                               const uint16_t *__restrict__ rec, const double (&bd)[kPatchMax],
+                                               const double *__restrict__ geo, double *__restrict__ out) {
+    const ushort4 q0 = reinterpret_cast<const ushort4 *>(rec)[0];
+    const ushort4 q1 = reinterpret_cast<const ushort4 *>(rec)[1];
+    const ushort4 q2 = reinterpret_cast<const ushort4 *>(rec)[2];
+    const int pm = q0.x;
+    const int ring[7] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
+    const int ia = q0.y;
+    const double aa = fabs(s_node[ia].w);
+    const double va = DIAG ? 0.0 : s_val[ia];
+    double acc_a = 0.0, acc_b = 0.0, acc_c = 0.0;
+    if (D == 3) {
+        const int ib = q0.z;
+        const double ab = fabs(s_node[ib].w);
+        const double vb = DIAG ? 0.0 : s_val[ib];
+        double a2 = fabs(s_node[ring[0]].w);
+        double v0 = DIAG ? 0.0 : s_val[ring[0]];
+        const double2 *g2 = reinterpret_cast<const double2 *>(geo);
+#pragma unroll
+        for (int j = 0; j < kPatchMax; ++j) {
+            if (j >= pm) break;
+            const double2 g0 = __ldg(g2 + 4 * j), g1 = __ldg(g2 + 4 * j + 1), gg = __ldg(g2 + 4 * j + 2),
+                          g3 = __ldg(g2 + 4 * j + 3);
+            const double gAB = g0.x, gA0 = g0.y, gA1 = g1.x, gB0 = g1.y, gB1 = gg.x, g01 = gg.y, ad = g3.x;
+            const int r1 = ring[j + 1];
+            const double a3 = fabs(s_node[r1].w);
+            const double v1 = DIAG ? 0.0 : s_val[r1];
+            const double b = bd[j];
+            double o0, o1, o2, o3;
+            if (DIAG) {
+                const double kA = -(gAB + gA0 + gA1), kB = -(gAB + gB0 + gB1), k0 = -(gA0 + gB0 + g01),
+                             k1 = -(gA1 + gB1 + g01);
+                if (LUMP) {
+                    const double cl = ad * (1.0 / 24.0);
+                    o0 = cl * aa + b * kA;
+                    o1 = cl * ab + b * kB;
+                    o2 = cl * a2 + b * k0;
+                    o3 = cl * a3 + b * k1;
+                } else {
+                    const double cm = ad * (1.0 / 720.0);
+                    const double S = (aa + ab) + (a2 + a3);
+                    o0 = cm * (2.0 * S + 4.0 * aa) + b * kA;
+                    o1 = cm * (2.0 * S + 4.0 * ab) + b * kB;
+                    o2 = cm * (2.0 * S + 4.0 * a2) + b * k0;
+                    o3 = cm * (2.0 * S + 4.0 * a3) + b * k1;
+                }
+            } else {
+                const double wAB = gAB * (vb - va), wA0 = gA0 * (v0 - va), wA1 = gA1 * (v1 - va);
+                const double wB0 = gB0 * (v0 - vb), wB1 = gB1 * (v1 - vb), w01 = g01 * (v1 - v0);
+                const double kA = b * ((wAB + wA0) + wA1);
+                const double kB = b * ((wB0 + wB1) - wAB);
+                const double k0 = b * (w01 - (wA0 + wB0));
+                const double k1 = -b * ((wA1 + wB1) + w01);
+                if (LUMP) {
+                    const double cl = ad * (1.0 / 24.0);
+                    o0 = cl * aa * va + kA;
+                    o1 = cl * ab * vb + kB;
+                    o2 = cl * a2 * v0 + k0;
+                    o3 = cl * a3 * v1 + k1;
+                } else {
+                    const double cm = ad * (1.0 / 720.0);
+                    const double S = (aa + ab) + (a2 + a3);
+                    const double X = (va + vb) + (v0 + v1);
+                    const double Q = (aa * va + ab * vb) + (a2 * v0 + a3 * v1);
+                    const double base = S * X + Q;
+                    o0 = cm * (base + S * va + aa * (X + 2.0 * va)) + kA;
+                    o1 = cm * (base + S * vb + ab * (X + 2.0 * vb)) + kB;
+                    o2 = cm * (base + S * v0 + a2 * (X + 2.0 * v0)) + k0;
+                    o3 = cm * (base + S * v1 + a3 * (X + 2.0 * v1)) + k1;
+                }
+            }
+            acc_a += o0;
+            acc_b += o1;
+            out[2 + j] = acc_c + o2;
+            acc_c = o3;
+            a2 = a3;
+            v0 = v1;
+        }
+        out[2 + pm] = acc_c;
+        out[0] = acc_a;
+        out[1] = acc_b;
+    } else {
+        double a1 = fabs(s_node[ring[0]].w);
+        double v0 = DIAG ? 0.0 : s_val[ring[0]];
+        const double2 *g2 = reinterpret_cast<const double2 *>(geo);
+#pragma unroll
+        for (int j = 0; j < kPatchMax; ++j) {
+            if (j >= pm) break;
+            const double2 g0 = __ldg(g2 + 2 * j), g1 = __ldg(g2 + 2 * j + 1);
+            const double gA0 = g0.x, gA1 = g0.y, g01 = g1.x, ad = g1.y;
+            const int r1 = ring[j + 1];
+            const double a2 = fabs(s_node[r1].w);
+            const double v1 = DIAG ? 0.0 : s_val[r1];
+            const double b = bd[j];
+            double o0, o1, o2;
+            if (DIAG) {
+                const double kA = -(gA0 + gA1), k0 = -(gA0 + g01), k1 = -(gA1 + g01);
+                if (LUMP) {
+                    const double cl = ad * (1.0 / 6.0);
+                    o0 = cl * aa + b * kA;
+                    o1 = cl * a1 + b * k0;
+                    o2 = cl * a2 + b * k1;
+                } else {
+                    const double cm = ad * (1.0 / 120.0);
+                    const double S = aa + a1 + a2;
+                    o0 = cm * (2.0 * S + 4.0 * aa) + b * kA;
+                    o1 = cm * (2.0 * S + 4.0 * a1) + b * k0;
+                    o2 = cm * (2.0 * S + 4.0 * a2) + b * k1;
+                }
+            } else {
+                const double wA0 = gA0 * (v0 - va), wA1 = gA1 * (v1 - va), w01 = g01 * (v1 - v0);
+                const double kA = b * (wA0 + wA1);
+                const double k0 = b * (w01 - wA0);
+                const double k1 = -b * (wA1 + w01);
+                if (LUMP) {
+                    const double cl = ad * (1.0 / 6.0);
+                    o0 = cl * aa * va + kA;
+                    o1 = cl * a1 * v0 + k0;
+                    o2 = cl * a2 * v1 + k1;
+                } else {
+                    const double cm = ad * (1.0 / 120.0);
+                    const double S = aa + a1 + a2;
+                    const double X = va + v0 + v1, Q = aa * va + a1 * v0 + a2 * v1;
+                    const double base = S * X + Q;
+                    o0 = cm * (base + S * va + aa * (X + 2.0 * va)) + kA;
+                    o1 = cm * (base + S * v0 + a1 * (X + 2.0 * v0)) + k0;
+                    o2 = cm * (base + S * v1 + a2 * (X + 2.0 * v1)) + k1;
+                }
+            }
+            acc_a += o0;
+            out[2 + j] = acc_c + o1;
+            acc_c = o2;
+            a1 = a2;
+            v0 = v1;
+        }
+        out[2 + pm] = acc_c;
+        out[0] = acc_a;
+    }
+}
+
 }  // namespace ps

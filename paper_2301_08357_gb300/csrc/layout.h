@@ -22,6 +22,10 @@ namespace ps {
 constexpr int kPatchMax = 6;     // elements per patch (star) at most
 constexpr int kPatchIds = 12;    // u16 per patch record: m, a, b, ring[0..m], padding
 constexpr int kPatchSlots = 9;   // contribution slots per patch: a, b, ring[0..6]
+// FP64 element geometry per patch slot: 3D G_AB, G_A0, G_A1, G_B0, G_B1, G_01, |det|, pad;
+// 2D G_A0, G_A1, G_01, |det| (G_ab = c_a.c_b / (d! |det|), c_a the cofactor vectors)
+template <int D>
+constexpr int kGeoWords = D == 3 ? 8 : 4;
 constexpr int kPatchPad = 4;     // patch segments padded to 4 patches (96 B)
 constexpr int kIncPad = 8;       // incidence segments padded to 8 u16
 constexpr int kIncpPad = 8;      // incidence-pointer segments padded to 8 u16

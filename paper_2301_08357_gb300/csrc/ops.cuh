@@ -38,6 +38,7 @@ struct MeshDev {
     const NodeD *node64;
     const float *bdt2_32;
     const double *bdt2_64;
+    const double *geo64;     // [patch_total * kPatchMax * kGeoWords<dim>] FP64 element geometry
     const float *dinv32;
     const double *dinv64;
     const uint8_t *dirichlet;
@@ -159,7 +160,26 @@ __device__ __forceinline__ void patches_eval(const MeshDev &m, const ChunkDesc &
     using N4 = typename NodeOf<T>::type;
     const T *gbdt2 = (sizeof(T) == 4) ? reinterpret_cast<const T *>(m.bdt2_32) : reinterpret_cast<const T *>(m.bdt2_64);
     const T *g_bdt2 = gbdt2 + (size_t)cd.patch_off * kPatchMax;
-    if (m.lumped) {
+    if constexpr (sizeof(T) == 8) {
+        // FP64: element geometry precomputed per slot (patch_eval_geo)
+        constexpr int GW = kGeoWords<D>;
+        const double *g_geo = m.geo64 + (size_t)cd.patch_off * kPatchMax * GW;
+        if (m.lumped) {
+            for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
+                double bd[kPatchMax];
+                load_bd(g_bdt2 + q * kPatchMax, bd);
+                patch_eval_geo<D, DIAG, true>(S.node, S.val, S.pids + q * kPatchIds, bd, g_geo + q * kPatchMax * GW,
+                                              S.contrib + q * kPatchSlots);
+            }
+        } else {
+            for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
+                double bd[kPatchMax];
+                load_bd(g_bdt2 + q * kPatchMax, bd);
+                patch_eval_geo<D, DIAG, false>(S.node, S.val, S.pids + q * kPatchIds, bd, g_geo + q * kPatchMax * GW,
+                                               S.contrib + q * kPatchSlots);
+            }
+        }
+    } else if (m.lumped) {
         for (int q = threadIdx.x; q < cd.n_patch; q += blockDim.x) {
             T bd[kPatchMax];
             load_bd(g_bdt2 + q * kPatchMax, bd);

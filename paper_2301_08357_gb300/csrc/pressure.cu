@@ -71,6 +71,54 @@ void dfree_all(ps_ctx *ctx, std::vector<DevAlloc> &owner) {
 
 static uint32_t align128(uint64_t v) { return (uint32_t)((v + 127) / 128 * 128); }
 
+// Geometry of element j of a star patch (vertices A, B, ring j, ring j+1 in
+// 3D; A, ring j, ring j+1 in 2D; chunk-relative coordinates rel): the
+// cofactor vectors c_a (grad lambda_a = c_a / det) and the slot words of
+// patch_eval_geo.
+static void element_geometry(int dim, const double *rel, const uint16_t *rec, int j, double *out) {
+    auto P = [&](int l) { return rel + (size_t)l * dim; };
+    if (dim == 3) {
+        const double *A = P(rec[1]), *B = P(rec[2]), *R0 = P(rec[3 + j]), *R1 = P(rec[4 + j]);
+        double e1[3], d0[3], d1[3], c[4][3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = B[k] - A[k];
+            d0[k] = R0[k] - A[k];
+            d1[k] = R1[k] - A[k];
+        }
+        auto cross = [](const double *u, const double *v, double *w) {
+            w[0] = u[1] * v[2] - u[2] * v[1];
+            w[1] = u[2] * v[0] - u[0] * v[2];
+            w[2] = u[0] * v[1] - u[1] * v[0];
+        };
+        cross(d0, d1, c[1]);   // B
+        cross(d1, e1, c[2]);   // ring j
+        cross(e1, d0, c[3]);   // ring j + 1
+        for (int k = 0; k < 3; ++k) c[0][k] = -(c[1][k] + c[2][k] + c[3][k]);
+        const double ad = std::fabs(e1[0] * c[1][0] + e1[1] * c[1][1] + e1[2] * c[1][2]);
+        const double inv = 1.0 / (6.0 * ad);
+        auto G = [&](int a, int b) { return (c[a][0] * c[b][0] + c[a][1] * c[b][1] + c[a][2] * c[b][2]) * inv; };
+        out[0] = G(0, 1);
+        out[1] = G(0, 2);
+        out[2] = G(0, 3);
+        out[3] = G(1, 2);
+        out[4] = G(1, 3);
+        out[5] = G(2, 3);
+        out[6] = ad;
+        out[7] = 0.0;
+    } else {
+        const double *A = P(rec[1]), *R0 = P(rec[3 + j]), *R1 = P(rec[4 + j]);
+        const double d0[2] = {R0[0] - A[0], R0[1] - A[1]}, d1[2] = {R1[0] - A[0], R1[1] - A[1]};
+        const double c[3][2] = {{-(d1[1] - d0[1]), -(-d1[0] + d0[0])}, {d1[1], -d1[0]}, {-d0[1], d0[0]}};
+        const double ad = std::fabs(d0[0] * d1[1] - d0[1] * d1[0]);
+        const double inv = 1.0 / (2.0 * ad);
+        auto G = [&](int a, int b) { return (c[a][0] * c[b][0] + c[a][1] * c[b][1]) * inv; };
+        out[0] = G(0, 1);
+        out[1] = G(0, 2);
+        out[2] = G(1, 2);
+        out[3] = ad;
+    }
+}
+
 SmemLayout make_layout(int esz, int nsz, int max_loc, int max_patch, int max_inc, int max_sh) {
     SmemLayout L;
     const uint64_t ppad = (uint64_t)round_up(max_patch, kPatchPad);
@@ -342,6 +390,25 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         RC(upload(c, m, &pd, nd.data(), nd.size() * sizeof(NodeD)));
         d.node32 = pf;
         d.node64 = pd;
+    }
+    // FP64 element geometry per patch slot (patch_eval_geo): stiffness weights
+    // G_ab = c_a.c_b / (d! |det|) and |det|, from the chunk-relative FP64
+    // coordinates the device would otherwise recompute them from
+    {
+        const int gw = pm.dim == 3 ? kGeoWords<3> : kGeoWords<2>;
+        std::vector<double> geo((size_t)pm.patch_total * kPatchMax * gw, 0.0);
+        for (int ch = 0; ch < pm.n_chunks; ++ch) {
+            const ChunkDesc &cd = pm.chunks[ch];
+            const double *rel = &pm.loc_rel[(size_t)cd.node_off * pm.dim];
+            for (int q = 0; q < cd.n_patch; ++q) {
+                const uint16_t *rec = &pm.pids[(size_t)(cd.patch_off + q) * kPatchIds];
+                double *gs = &geo[(size_t)(cd.patch_off + q) * kPatchMax * gw];
+                for (int j = 0; j < rec[0]; ++j) element_geometry(pm.dim, rel, rec, j, gs + (size_t)j * gw);
+            }
+        }
+        double *gp;
+        RC(upload(c, m, &gp, geo.data(), geo.size() * 8));
+        d.geo64 = gp;
     }
     float *f;
     double *g;
