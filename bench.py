@@ -212,10 +212,31 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def kernel_roofline(P, m, stats, mode, fused, stream, workload):
+# FP64 peak of the part: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_flops(stats, lumped, cg):
+    """Algorithmic FP64 flops of one FP64 operator pass with the precomputed
+    element geometry (an FMA counts 2): per element the stiffness differences
+    (3D 24, 2D 13) and the mass term (consistent 3D 47 / 2D 35, lumped 4(d+1)+1),
+    3 accumulations; per node the incidence sums E(d+1)/N plus 3 (residual and
+    its dot) or 4 (CG direction and p.Ap)."""
+    E, N, d = stats.n_elems, stats.n_nodes, stats.dim
+    k = 24 if d == 3 else 13
+    mass = (2 * (d + 1) + 1) if lumped else (47 if d == 3 else 35)
+    per_elem = k + mass + (d if d == 3 else 2)
+    per_node = E * (d + 1) / N + (4 if cg else 3)
+    return per_elem * E + per_node * N
+
+
+def kernel_roofline(P, m, stats, mode, fused, stream, workload, lumped=False):
     """Roofline entry of the solve's dominant kernel: algorithmic bytes per
     launch over its CUDA-event time (ps_profile_kernel, back-to-back launches
-    on `stream`), against the measured HBM copy bandwidth."""
+    on `stream`), against the measured HBM copy bandwidth.  The FP64 passes
+    are bound by the FP64 pipe instead: FP64 mode reports its operator kernel
+    as "alu" (algorithmic FP64 flops against FP64_PEAK_TFLOPS, HBM fraction
+    beside it), and every line carries the FP64 residual pass the same way."""
     if fused:
         which, kname = P.PS_KERNEL_CG1_F32, "k_cg1_chunks<%d>" % stats.dim
     elif mode == P.PS_MODE_MIXED:
@@ -240,10 +261,26 @@ def kernel_roofline(P, m, stats, mode, fused, stream, workload):
     alg_bytes = elem_b * E + node_b * N
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    res_ms = kern_other["resid_f64"]
+    res_flops = fp64_flops(stats, lumped, cg=False)
+    res_bytes = (4 * (d + 1) + 8) * E + (8 * (d + 1) + 3 * 8) * N
+    fp64_resid = {"kernel": "k_chunks<%d,double,kResid>" % d, "bound": "alu", "unit": "TFLOP/s",
+                  "achieved": res_flops / (res_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                  "frac": res_flops / (res_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                  "hbm_frac": res_bytes / (res_ms / 1e3) / 1e9 / peak, "flops_per_launch": res_flops,
+                  "kernel_ms": res_ms}
+    if mode == P.PS_MODE_FP64:
+        flops = fp64_flops(stats, lumped, cg=True)
+        tf = flops / (kern_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((kname, workload)), "kernel": kname,
+                "kernel_ms": kern_ms, "flops_per_launch": flops, "hbm_frac": achieved / peak,
+                "alg_bytes_per_launch": alg_bytes, "peak_kind": "nominal FP64 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "other_kernels_ms": kern_other, "fp64_resid": fp64_resid, "chunks": stats.n_chunks}
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": TRAFFIC.get((kname, workload)), "kernel": kname,
             "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
-            "other_kernels_ms": kern_other, "chunks": stats.n_chunks,
+            "other_kernels_ms": kern_other, "fp64_resid": fp64_resid, "chunks": stats.n_chunks,
             "shared_node_frac": stats.n_shared / stats.n_nodes,
             "note": "working set ~%.0f MB/launch: %s" % (
                 alg_bytes / 1e6, "L2-resident between iterations" if alg_bytes < 100e6 else "exceeds L2 (129 MB)")}
@@ -746,7 +783,7 @@ def run_projection(args, eos=False):
         e2e.append(1e3 * (time.perf_counter() - t0))
     stats = P.ps_mesh_get_stats(m)
     wname = ("eos_3d_kuhn_%d" if eos else "projection_3d_kuhn_%d") % args.n
-    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream, wname)
+    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream, wname, lumped=eos)
     cpu = None
     if not args.no_cpu_baseline and eos:
         from oracle import lumped as LO

@@ -76,3 +76,18 @@ def test_clock_parser():
     assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
     assert c["reasons"] == ["sw_power_cap"] and c["samples"] == 3
     assert bench.parse_clocks([]) is None
+
+
+def test_fp64_flop_model():
+    """The FP64 roofline's peak and per-pass flop count (C2: 1,572,864 tets,
+    274,625 nodes; 74 flops per consistent tet, 36 per lumped tet)."""
+    class St:
+        n_elems, n_nodes, dim = 1572864, 274625, 3
+    assert abs(bench.FP64_PEAK_TFLOPS - 152 * 4 * 2.07e-3) < 1e-12
+    inc = St.n_elems * 4 / St.n_nodes
+    assert bench.fp64_flops(St, False, False) == pytest.approx(74 * St.n_elems + (inc + 3) * St.n_nodes)
+    assert bench.fp64_flops(St, True, True) == pytest.approx(36 * St.n_elems + (inc + 4) * St.n_nodes)
+
+    class St2:
+        n_elems, n_nodes, dim = 8192, 4225, 2
+    assert bench.fp64_flops(St2, False, False) == pytest.approx(50 * 8192 + (8192 * 3 / 4225 + 3) * 4225)
