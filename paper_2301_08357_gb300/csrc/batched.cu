@@ -159,9 +159,7 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
                 chunk_cg1f<2>(s_md, cg1_pass(s_v, par), s_v.dinv, tk.y, ab.x, ab.y, S, phase, acc, failed);
             if (failed) return;
             double out[3];
-            out[0] = block_sum(acc[0], S.red);
-            out[1] = block_sum(acc[1], S.red);
-            out[2] = block_sum(acc[2], S.red);
+            block_sum_n<3>(acc, S.red, out);
             if (threadIdx.x == 0) {
                 M.v.dots[3 * tk.y] = df_pack(out[0]);
                 M.v.dots[3 * tk.y + 1] = df_pack(out[1]);

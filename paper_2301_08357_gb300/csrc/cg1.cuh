@@ -212,9 +212,8 @@ __device__ __forceinline__ void cg1_reduce(const float2 *dots, int n_chunks, dou
         ad.merge(d2.x, d2.y);
         ar.merge(r2.x, r2.y);
     }
-    out[0] = block_sum(ag, red);
-    out[1] = block_sum(ad, red);
-    out[2] = block_sum(ar, red);
+    const DotF v[3] = {ag, ad, ar};
+    block_sum_n<3>(v, red, out);
 }
 
 // Graph engine: one block per chunk; the last block advances the scalars.
@@ -243,9 +242,7 @@ __global__ void __launch_bounds__(256) k_cg1_chunks(MeshDev m, CG1Vec V, CgState
     chunk_cg1f<D>(m, cg1_pass(V, s_par), V.dinv, blockIdx.x, s_ab[0], s_ab[1], S, phase, acc, failed);
     if (failed) return;
     double out[3];
-    out[0] = block_sum(acc[0], S.red);
-    out[1] = block_sum(acc[1], S.red);
-    out[2] = block_sum(acc[2], S.red);
+    block_sum_n<3>(acc, S.red, out);
     if (threadIdx.x == 0) {
         V.dots[3 * blockIdx.x] = df_pack(out[0]);
         V.dots[3 * blockIdx.x + 1] = df_pack(out[1]);

@@ -48,6 +48,26 @@ __device__ __forceinline__ double part_sum(const double *a, int n, double *red) 
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(a + i);
     return block_sum(s, red);
 }
+__device__ __forceinline__ void block_sum2(const DotD &a, const DotD &b, double *red, double &ra, double &rb) {
+    ra = block_sum(a, red);
+    rb = block_sum(b, red);
+}
+__device__ __forceinline__ void part_sum2(const double *a, const double *b, int n, double *red, double &ra,
+                                          double &rb) {
+    ra = part_sum(a, n, red);
+    rb = part_sum(b, n, red);
+}
+// Two fixed-order partial sums with one set of barriers (FP32 iteration).
+__device__ __forceinline__ void part_sum2(const float2 *a, const float2 *b, int n, double *red, double &ra,
+                                          double &rb) {
+    DotF acc_a, acc_b;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 va = __ldcg(a + i), vb = __ldcg(b + i);
+        acc_a.merge(va.x, va.y);
+        acc_b.merge(vb.x, vb.y);
+    }
+    block_sum2(acc_a, acc_b, red, ra, rb);
+}
 
 template <typename T>
 struct Cg2Args {
@@ -379,8 +399,8 @@ __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
         }
     }
     for (int64_t i = 4 * n4 + tid; i < m.n_nodes; i += nthr) one(i);
-    const double vrz = block_sum(arz, red);
-    const double vrr = block_sum(arr, red);
+    double vrz, vrr;
+    block_sum2(arz, arr, red, vrz, vrr);
     if (threadIdx.x == 0) {
         part_pack(vrz, a.z2[blockIdx.x]);
         part_pack(vrr, a.z2[a.g3 + blockIdx.x]);
@@ -389,8 +409,8 @@ __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     }
     __syncthreads();
     if (!s_last) return;
-    const double rz = part_sum(a.z2, gridDim.x, red);
-    const double rr = part_sum(a.z2 + a.g3, gridDim.x, red);
+    double rz, rr;
+    part_sum2(a.z2, a.z2 + a.g3, gridDim.x, red, rz, rr);
     if (threadIdx.x == 0) {
         CgState *st = a.st;
         st->cnt_b = 0;
@@ -433,8 +453,8 @@ __global__ void __launch_bounds__(256) k_cg2_start(MeshDev m, Cg2Args<T> a, cons
         arz.add_prod(ri, a.dinv[i] * ri);
         arr.add_prod(ri, ri);
     }
-    const double vrz = block_sum(arz, red);
-    const double vrr = block_sum(arr, red);
+    double vrz, vrr;
+    block_sum2(arz, arr, red, vrz, vrr);
     if (threadIdx.x == 0) {
         part_pack(vrz, a.z2[blockIdx.x]);
         part_pack(vrr, a.z2[a.g3 + blockIdx.x]);
@@ -443,8 +463,8 @@ __global__ void __launch_bounds__(256) k_cg2_start(MeshDev m, Cg2Args<T> a, cons
     }
     __syncthreads();
     if (!s_last) return;
-    const double rz0 = part_sum(a.z2, gridDim.x, red);
-    const double rr0 = part_sum(a.z2 + a.g3, gridDim.x, red);
+    double rz0, rr0;
+    part_sum2(a.z2, a.z2 + a.g3, gridDim.x, red, rz0, rr0);
     if (threadIdx.x == 0) {
         CgState *st = a.st;
         st->cnt_a = 0;

@@ -187,6 +187,54 @@ __device__ __forceinline__ double block_sum(const DotF &a, double *red) {
 }
 __device__ __forceinline__ double block_sum(const DotD &a, double *red) { return block_sum(a.v, red); }
 
+// N block sums (N <= 3) with one set of barriers; each result is bitwise the
+// one block_sum gives (same per-warp values, same fixed-order sums).  Blocks
+// of at most 256 threads; `red` holds >= 34 doubles.
+__device__ __forceinline__ float2 warp_dotf(const DotF &a) {
+    float hi = a.hi, lo = a.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        DotF t;
+        t.hi = hi;
+        t.lo = lo;
+        t.merge(h2, l2);
+        hi = t.hi;
+        lo = t.lo;
+    }
+    return make_float2(hi, lo);
+}
+template <int N>
+__device__ __forceinline__ void block_sum_n(const DotF *a, double *red, double *out) {
+    float2 w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = warp_dotf(a[k]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[8 * k + wid] = (double)w[k].x + (double)w[k].y;
+    }
+    __syncthreads();
+    if (lane == 0 && wid < N) {
+        double t = 0.0;
+        for (int v = 0; v < nw; ++v) t += red[8 * wid + v];
+        red[24 + wid] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = red[24 + k];
+    __syncthreads();
+}
+__device__ __forceinline__ void block_sum2(const DotF &a, const DotF &b, double *red, double &ra, double &rb) {
+    const DotF v[2] = {a, b};
+    double o[2];
+    block_sum_n<2>(v, red, o);
+    ra = o[0];
+    rb = o[1];
+}
+
 // ---------------------------------------------------------------- P1 element kernels
 // Notation: vertices p0..pd with coordinates (x,y[,z]) and nodal alpha in w;
 // nodal values v0..vd; bdt2 = beta_e * dt^2.  Jacobian columns e_k = p_k - p0,
