@@ -325,13 +325,58 @@ __global__ void __launch_bounds__(256) k_cg2_chunks_pipe(MeshDev m, Cg2Args<floa
     }
 }
 
-// K2: fixed grid over the padded node range [0, n_pad).
+// K2: fixed grid over the padded node range [0, n_pad).  Interior nodes in
+// groups of 4 (16-byte vectors in FP32), then the rest (interior tail,
+// shared nodes) one node per thread, so the dependent partial-sum gathers of
+// shared nodes are spread over all threads.  Each thread loads its first
+// group and its first remaining node (partial sums included) before the CG
+// scalars arrive: none of those loads depends on them, so their latency
+// overlaps the scalar read.
+template <typename T>
+struct K2Node {
+    T d, r, p, q;
+    bool dir;
+};
+template <typename T>
+__device__ __forceinline__ K2Node<T> k2_load(const MeshDev &m, const Cg2Args<T> &a, int64_t i) {
+    K2Node<T> v;
+    v.d = a.dinv[i];
+    v.r = a.r[i];
+    v.p = a.p[i];
+    v.dir = false;
+    if (i < m.n_int) {
+        v.q = a.q[i];
+    } else {
+        const int64_t s = i - m.n_int;
+        T sum = T(0);
+        for (int k = m.shr_ptr[s]; k < m.shr_ptr[s + 1]; ++k) sum += a.partial[k];
+        v.q = sum;
+        v.dir = m.dirichlet[i] != 0;
+    }
+    return v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     __shared__ double red[34];
     __shared__ double s_sc[2];
     __shared__ int s_done;
     __shared__ bool s_last;
+    const int64_t n4 = m.n_int / 4;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float4 x4f, r4f, p4f, q4f, d4f;
+    const bool grp0 = sizeof(T) == 4 && tid < n4;
+    if (grp0) {
+        x4f = reinterpret_cast<const float4 *>(a.x)[tid];
+        r4f = reinterpret_cast<const float4 *>(a.r)[tid];
+        p4f = reinterpret_cast<const float4 *>(a.p)[tid];
+        q4f = reinterpret_cast<const float4 *>(a.q)[tid];
+        d4f = reinterpret_cast<const float4 *>(a.dinv)[tid];
+    }
+    const int64_t i1 = 4 * n4 + tid;
+    K2Node<T> nd1;
+    if (i1 < m.n_nodes) nd1 = k2_load(m, a, i1);
     if (threadIdx.x == 0) {
         s_done = a.st->done;
         s_sc[0] = a.st->alpha;
@@ -342,63 +387,54 @@ __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     const T alpha = (T)s_sc[0];
     const T beta = (T)s_sc[1];
     typename DotOf<T>::type arz, arr;
-    auto one = [&](int64_t i) {
-        T pi, qi;
-        const T di = a.dinv[i];
-        T ri = a.r[i];
-        if (i < m.n_int) {
-            pi = a.p[i];
-            qi = a.q[i];
-        } else {
-            const int64_t s = i - m.n_int;
-            T sum = T(0);
-            for (int k = m.shr_ptr[s]; k < m.shr_ptr[s + 1]; ++k) sum += a.partial[k];
-            pi = cg_dir(di, ri, beta, a.p[i]);
-            if (m.dirichlet[i]) {
+    auto finish = [&](int64_t i, const K2Node<T> &v) {
+        T pi = v.p, qi = v.q;
+        if (i >= m.n_int) {
+            pi = cg_dir(v.d, v.r, beta, v.p);
+            if (v.dir) {
                 pi = T(0);
-                sum = T(0);
+                qi = T(0);
             }
-            qi = sum;
             a.p[i] = pi;
             a.q[i] = qi;
         }
         a.x[i] += alpha * pi;
-        ri -= alpha * qi;
+        const T ri = v.r - alpha * qi;
         a.r[i] = ri;
-        arz.add_prod(ri, di * ri);
+        arz.add_prod(ri, v.d * ri);
         arr.add_prod(ri, ri);
     };
-    // interior nodes in groups of 4 (16-byte vectors in FP32), then the rest
-    // (interior tail, shared nodes) one node per thread, so the dependent
-    // partial-sum gathers of shared nodes are spread over all threads
-    const int64_t n4 = m.n_int / 4;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t j = tid; j < n4; j += nthr) {
-        const int64_t i0 = 4 * j;
-        if (sizeof(T) == 4) {
+    auto group = [&](int64_t j, const float4 &x4, const float4 &r4, const float4 &p4, const float4 &q4,
+                     const float4 &d4) {
+        const float al = (float)alpha;
+        float4 xo, ro;
+        xo.x = x4.x + al * p4.x; ro.x = r4.x - al * q4.x;
+        xo.y = x4.y + al * p4.y; ro.y = r4.y - al * q4.y;
+        xo.z = x4.z + al * p4.z; ro.z = r4.z - al * q4.z;
+        xo.w = x4.w + al * p4.w; ro.w = r4.w - al * q4.w;
+        reinterpret_cast<float4 *>(a.x)[j] = xo;
+        reinterpret_cast<float4 *>(a.r)[j] = ro;
+        arz.add_prod(ro.x, d4.x * ro.x); arr.add_prod(ro.x, ro.x);
+        arz.add_prod(ro.y, d4.y * ro.y); arr.add_prod(ro.y, ro.y);
+        arz.add_prod(ro.z, d4.z * ro.z); arr.add_prod(ro.z, ro.z);
+        arz.add_prod(ro.w, d4.w * ro.w); arr.add_prod(ro.w, ro.w);
+    };
+    if (sizeof(T) == 4) {
+        if (grp0) group(tid, x4f, r4f, p4f, q4f, d4f);
+        for (int64_t j = tid + nthr; j < n4; j += nthr) {
             const float4 x4 = reinterpret_cast<const float4 *>(a.x)[j];
             const float4 r4 = reinterpret_cast<const float4 *>(a.r)[j];
             const float4 p4 = reinterpret_cast<const float4 *>(a.p)[j];
             const float4 q4 = reinterpret_cast<const float4 *>(a.q)[j];
             const float4 d4 = reinterpret_cast<const float4 *>(a.dinv)[j];
-            const float al = (float)alpha;
-            float4 xo, ro;
-            xo.x = x4.x + al * p4.x; ro.x = r4.x - al * q4.x;
-            xo.y = x4.y + al * p4.y; ro.y = r4.y - al * q4.y;
-            xo.z = x4.z + al * p4.z; ro.z = r4.z - al * q4.z;
-            xo.w = x4.w + al * p4.w; ro.w = r4.w - al * q4.w;
-            reinterpret_cast<float4 *>(a.x)[j] = xo;
-            reinterpret_cast<float4 *>(a.r)[j] = ro;
-            arz.add_prod(ro.x, d4.x * ro.x); arr.add_prod(ro.x, ro.x);
-            arz.add_prod(ro.y, d4.y * ro.y); arr.add_prod(ro.y, ro.y);
-            arz.add_prod(ro.z, d4.z * ro.z); arr.add_prod(ro.z, ro.z);
-            arz.add_prod(ro.w, d4.w * ro.w); arr.add_prod(ro.w, ro.w);
-        } else {
-            for (int t = 0; t < 4; ++t) one(i0 + t);
+            group(j, x4, r4, p4, q4, d4);
         }
+    } else {
+        for (int64_t j = tid; j < n4; j += nthr)
+            for (int t = 0; t < 4; ++t) finish(4 * j + t, k2_load(m, a, 4 * j + t));
     }
-    for (int64_t i = 4 * n4 + tid; i < m.n_nodes; i += nthr) one(i);
+    if (i1 < m.n_nodes) finish(i1, nd1);
+    for (int64_t i = i1 + nthr; i < m.n_nodes; i += nthr) finish(i, k2_load(m, a, i));
     double vrz, vrr;
     block_sum2(arz, arr, red, vrz, vrr);
     if (threadIdx.x == 0) {
