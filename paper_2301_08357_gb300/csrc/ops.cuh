@@ -287,12 +287,17 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
         return Acc();
     }
 
-    // ---- gather the input vector (masked on Dirichlet nodes)
+    // ---- gather the input vector (masked on Dirichlet nodes).  Apply and
+    // residual skip the element phase of a chunk whose input is zero on all
+    // its nodes (a zero first guess, a zero correction): every contribution
+    // is then exactly 0.
+    bool nonzero = false;
     if (MODE != kDiag) {
         auto finish = [&](int l, T v) {
             if (is_dirichlet(S.node[l].w)) v = T(0);
             if (MODE == kCG && l < n_int) a.p[cd.int_begin + l] = v;
             S.val[l] = v;
+            nonzero |= v != T(0);
         };
         auto fetch = [&](int l) -> T {
             const int g = l < n_int ? cd.int_begin + l : S.shid[l - n_int];
@@ -304,15 +309,16 @@ __device__ typename DotOf<T>::type process_chunk(const MeshDev &m, const VecArgs
             if (l < n_loc) finish(l, l < n_int ? vin[k] : fetch(l));
         }
         for (int l = threadIdx.x + 4 * blockDim.x; l < n_loc; l += blockDim.x) finish(l, fetch(l));
-        __syncthreads();
     }
+    const bool work = (MODE == kApply || MODE == kResid) ? __syncthreads_or(nonzero) != 0 : true;
+    if (MODE != kDiag && !(MODE == kApply || MODE == kResid)) __syncthreads();
 
-    patches_eval<D, T, MODE == kDiag>(m, cd, S);
+    if (work) patches_eval<D, T, MODE == kDiag>(m, cd, S);
 
     // ---- per-node sums in incidence order
     Acc dot;
     for (int l = threadIdx.x; l < n_loc; l += blockDim.x) {
-        T s = node_sum(S, l);
+        T s = work ? node_sum(S, l) : T(0);
         const bool dir = is_dirichlet(S.node[l].w);
         if (dir) s = T(0);
         if (l < n_int) {
