@@ -92,6 +92,34 @@ def test_apply_matches_oracle(P, torch_mod, ctx, name, make, chunk, prec):
         P.ps_mesh_free(m)
 
 
+@pytest.mark.parametrize("prec", [2, 1], ids=["f64", "f32"])
+def test_apply_sparse_and_zero_inputs(P, torch_mod, ctx, prec):
+    """Chunks whose input is zero skip their element phase: an input that is
+    nonzero on a few nodes only (most chunks zero, a few partly) still matches
+    the oracle on every row, and a zero input gives exactly zero."""
+    case = S.make_c2(12)
+    m = upload(P, ctx, case, 96)
+    try:
+        A = oracle.PressureMatrix.from_case(case)
+        rng = np.random.default_rng(21)
+        x = np.zeros(case.n_nodes)
+        idx = rng.choice(case.n_nodes, size=7, replace=False)
+        x[idx] = rng.standard_normal(7)
+        if prec == 1:
+            x = x.astype(np.float32).astype(np.float64)
+        y = _gpu_apply(P, torch_mod, m, x, prec)
+        yo = A.apply(x)
+        sc = row_scale_fast(A, x)
+        free = ~case.dirichlet.astype(bool)
+        touched = free & (sc > 0)
+        assert np.max(np.abs(y - yo)[touched] / sc[touched]) <= TOL[prec]
+        assert np.all(y[free & (sc == 0)] == 0.0)
+        z = _gpu_apply(P, torch_mod, m, np.zeros(case.n_nodes), prec)
+        assert np.all(z == 0.0)
+    finally:
+        P.ps_mesh_free(m)
+
+
 def test_apply_full_size_c2(P, torch_mod, ctx):
     """64^3 Kuhn cube (1,572,864 tets), both precisions, every row."""
     case = S.make_c2()
