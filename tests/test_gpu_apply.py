@@ -100,7 +100,6 @@ def test_apply_sparse_and_zero_inputs(P, torch_mod, ctx, prec):
     case = S.make_c2(12)
     m = upload(P, ctx, case, 96)
     try:
-        A = oracle.PressureMatrix.from_case(case)
         rng = np.random.default_rng(21)
         x = np.zeros(case.n_nodes)
         idx = rng.choice(case.n_nodes, size=7, replace=False)
@@ -108,12 +107,18 @@ def test_apply_sparse_and_zero_inputs(P, torch_mod, ctx, prec):
         if prec == 1:
             x = x.astype(np.float32).astype(np.float64)
         y = _gpu_apply(P, torch_mod, m, x, prec)
-        yo = A.apply(x)
-        sc = row_scale_fast(A, x)
-        free = ~case.dirichlet.astype(bool)
-        touched = free & (sc > 0)
-        assert np.max(np.abs(y - yo)[touched] / sc[touched]) <= TOL[prec]
-        assert np.all(y[free & (sc == 0)] == 0.0)
+        # rows of the nodes that share an element with a nonzero input; their
+        # scale is element-level (sum over elements of |A^e_ij x_j|): assembled
+        # off-diagonal entries can cancel between the elements around an edge
+        near = np.zeros(case.n_nodes, bool)
+        hit = np.isin(case.conn, idx).any(axis=1)
+        near[case.conn[hit].ravel()] = True
+        nodes = np.where(near)[0]
+        yo, sc = sampled_rows(case, x, nodes)
+        live = sc > 0
+        assert np.max(np.abs(y[nodes] - yo)[live] / sc[live]) <= TOL[prec]
+        assert np.all(y[nodes][~live] == 0.0)
+        assert np.all(y[~near] == 0.0)
         z = _gpu_apply(P, torch_mod, m, np.zeros(case.n_nodes), prec)
         assert np.all(z == 0.0)
     finally:
