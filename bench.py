@@ -191,6 +191,25 @@ def cpu_baseline(case, seconds, steps=None):
             "solves": done, "seconds": t_used, "times": times}
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def run_reference(args):
     ws, rank, local = dist_setup()
     if rank != 0:
@@ -393,6 +412,16 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(case, args.cpu_seconds)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # the same oracle on one core (one solve), and the host's CPU model
+        import oracle
+        n_all = oracle.num_threads()
+        oracle.set_threads(1)
+        try:
+            c1 = cpu_baseline(case, 0.0, steps=1)
+        finally:
+            oracle.set_threads(n_all)
+        cpu["single_core"] = {"value": c1["value"], "unit": UNIT, "cores": 1, "sample": c1["sample"]}
+        cpu["cpu_model"] = cpu_model()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
