@@ -305,7 +305,10 @@ void ps_solve_opts_default(ps_solve_opts *opts);
  * info: the last solve's record, with iters_inner / iters_outer / seconds
  * summed over the Picard iterations (may be NULL).  Errors: PS_EINVAL (bad
  * argument, or an enthalpy that is not positive and finite), PS_ESTATE
- * (coefficients not set), and the statuses of ps_pressure_solve.  Device
+ * (coefficients not set), and the statuses of ps_pressure_solve (a solve
+ * that does not return PS_OK ends the step at once: dp_dev holds its last
+ * iterate, h_dev and rhok_dev the guesses that solve used, p_dev and wun_dev
+ * the previous Picard iteration's values, unset if it was the first).  Device
  * data for the element passes (coordinates, connectivity, node-to-element
  * lists) is allocated on the first call and counted in the context budget. */
 typedef struct {
@@ -349,7 +352,11 @@ int ps_projection_step(ps_mesh *mesh, const ps_projection_opts *opts, const doub
  *   new ps_coeff_set).  Errors: PS_EINVAL (bad argument, periodic mesh, an
  *   enthalpy or Jacobian entry Q'_i that is not positive and finite),
  *   PS_ESTATE (consistent mass), PS_ENOTCONV (newton_tol > 0 not reached in
- *   the last Picard iteration; outputs written), solve statuses. */
+ *   the last Picard iteration; outputs written), and the statuses of
+ *   ps_pressure_solve: a linear solve that does not return PS_OK ends the
+ *   step at once (dp_dev holds its last iterate, h_dev and rhok_dev the
+ *   guesses of that Picard iteration, p_dev and wun_dev the previous one's,
+ *   unset if it was the first). */
 typedef struct {
     double eos_a;            /* > 0                                               */
     double eos_b;            /* >= 0                                              */
