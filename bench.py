@@ -794,6 +794,15 @@ def run_projection(args, eos=False):
             launches += info.kernel_launches + 6 * n_pic + 1
     clk = clocks.stop() if not args.no_clocks else None
     tot = float(np.sum(times))
+    wname = ("eos_3d_kuhn_%d" if eos else "projection_3d_kuhn_%d") % args.n
+    if args.launch_list:
+        # warm-up and timed steps only (identical work), for a launch-list capture
+        print(json.dumps({"metric": METRIC, "value": case.n_free * iters / (tot / 1e3), "unit": UNIT,
+                          "ms_per_step": tot / args.steps, "config": {"workload": wname},
+                          "gpu_launches": launches, "launch_list_run": True}))
+        P.ps_mesh_free(m)
+        P.ps_ctx_destroy(ctx)
+        return
     # end to end: host inputs copied in, outputs copied back, inside the timed region
     h_in = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
             for a in (e["rho"], e["wu"], e["we"], e["pn"])]
@@ -811,7 +820,6 @@ def run_projection(args, eos=False):
         torch.cuda.synchronize()
         e2e.append(1e3 * (time.perf_counter() - t0))
     stats = P.ps_mesh_get_stats(m)
-    wname = ("eos_3d_kuhn_%d" if eos else "projection_3d_kuhn_%d") % args.n
     roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, case.n_nodes <= 200000, stream, wname, lumped=eos)
     cpu = None
     if not args.no_cpu_baseline and eos:
