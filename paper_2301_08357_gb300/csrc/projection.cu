@@ -35,6 +35,7 @@ struct ProjData {
     double *alpha = nullptr;      // [n_nodes]
     uint8_t *dir = nullptr;       // [n_nodes] Dirichlet flags
     double *b = nullptr;          // [n_nodes] right-hand side
+    double *loc = nullptr;        // [n_elems * (dim + 1)] per-element contributions before the gather
     int *flag = nullptr;          // enthalpy check
     int64_t alpha_version = -1;
     // general-EOS Newton iteration (allocated on its first call)
@@ -113,26 +114,63 @@ __global__ void __launch_bounds__(kT) k_pj_check(int64_t n, const double *__rest
         if (!(v[i] > 0.0) || !isfinite(v[i])) atomicOr(flag, 1);
 }
 
-// Right-hand side of the weak problem at node i, gathered over its elements
-// in ascending order:
+// Right-hand side of the weak problem, in two passes.  Element pass (one
+// thread per element, the element's geometry computed once): the
+// contribution to each local vertex k,
 //   (W~_E - rho K)_e |T| / (d+1)                       source term
 // + dt H_e |T| W~~_u,e . grad lambda_k                 divergence term
 // - (M^e_alpha P^n)_k = cm (S X + Q + S P_k + alpha_k (X + 2 P_k))
-// with k the local index of i in e, S = sum alpha, X = sum P, Q = sum alpha P
-// over the element's vertices and cm = |T| d! / (d+3)!.  alpha == nullptr
-// drops the mass term (the general-EOS residual carries it itself).
+// with S = sum alpha, X = sum P, Q = sum alpha P over the element's vertices
+// and cm = |T| d! / (d+3)!; alpha == nullptr drops the mass term (the
+// general-EOS residual carries it itself).  Node pass (k_pj_gather): b_i is
+// the sum of its vertices' contributions in ascending element order over a
+// node-to-element list (deterministic, no atomics), 0 on Dirichlet nodes.
 template <int D>
-__global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *__restrict__ n2e_ptr,
-                                               const int32_t *__restrict__ n2e, const int32_t *__restrict__ conn,
-                                               const double *__restrict__ x, const double *__restrict__ alpha,
-                                               const uint8_t *__restrict__ dir, const double *__restrict__ H,
-                                               const double *__restrict__ rhok, const double *__restrict__ wu,
-                                               const double *__restrict__ we, const double *__restrict__ p,
-                                               double dt, double *__restrict__ b) {
+__global__ void __launch_bounds__(kT) k_pj_elem_rhs(int64_t n_el, const int32_t *__restrict__ conn,
+                                                    const double *__restrict__ x, const double *__restrict__ alpha,
+                                                    const double *__restrict__ H, const double *__restrict__ rhok,
+                                                    const double *__restrict__ wu, const double *__restrict__ we,
+                                                    const double *__restrict__ p, double dt, double *__restrict__ loc) {
     constexpr double fact = D == 3 ? 6.0 : 2.0;           // d!
     constexpr double cmden = D == 3 ? 720.0 : 120.0;      // cm = |T| d! / (d+3)! = |det| / (d+3)!
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+        double v[D + 1][D], c[D + 1][D];
+        double al[D + 1], pv[D + 1];
+        for (int q = 0; q <= D; ++q) {
+            const int64_t g = conn[e * (D + 1) + q];
+            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
+            al[q] = alpha ? alpha[g] : 0.0;
+            pv[q] = alpha ? p[g] : 0.0;
+        }
+        const double det = cofactors<D>(v, c);
+        const double adet = fabs(det);
+        const double sgn = det > 0.0 ? 1.0 : -1.0;
+        const double vol = adet / fact;
+        double S = 0.0, X = 0.0, Q = 0.0;
+        for (int q = 0; q <= D; ++q) {
+            S += al[q];
+            X += pv[q];
+            Q += al[q] * pv[q];
+        }
+        const double cm = adet / cmden;
+        const double src = (we[e] - rhok[e]) * vol / (D + 1);
+        for (int k = 0; k <= D; ++k) {
+            double cw = 0.0;
+            for (int a = 0; a < D; ++a) cw += c[k][a] * wu[e * D + a];
+            const double mass = alpha ? cm * (S * X + Q + S * pv[k] + al[k] * (X + 2.0 * pv[k])) : 0.0;
+            loc[e * (D + 1) + k] = src + dt * H[e] * sgn * cw / fact - mass;
+        }
+    }
+}
+
+// b_i = sum over the node's (element, vertex) incidences, ascending element
+// order, of loc[e (d+1) + k]; 0 on Dirichlet nodes (dir may be nullptr: no
+// masking).  Also the lumped weights: loc = w_e per element (nv = 1).
+__global__ void __launch_bounds__(kT) k_pj_gather(int64_t n_nodes, const int64_t *__restrict__ n2e_ptr,
+                                                  const int32_t *__restrict__ n2e, const uint8_t *__restrict__ dir,
+                                                  const double *__restrict__ loc, int nv, double *__restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
-        if (dir[i]) {
+        if (dir && dir[i]) {
             b[i] = 0.0;
             continue;
         }
@@ -140,30 +178,7 @@ __global__ void __launch_bounds__(kT) k_pj_rhs(int64_t n_nodes, const int64_t *_
         for (int64_t t = n2e_ptr[i]; t < n2e_ptr[i + 1]; ++t) {
             const int code = n2e[t];
             const int64_t e = code >> 2;
-            const int k = code & 3;
-            double v[D + 1][D], c[D + 1][D];
-            double al[D + 1], pv[D + 1];
-            for (int q = 0; q <= D; ++q) {
-                const int64_t g = conn[e * (D + 1) + q];
-                for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
-                al[q] = alpha ? alpha[g] : 0.0;
-                pv[q] = alpha ? p[g] : 0.0;
-            }
-            const double det = cofactors<D>(v, c);
-            const double adet = fabs(det);
-            const double sgn = det > 0.0 ? 1.0 : -1.0;
-            const double vol = adet / fact;
-            double cw = 0.0;
-            for (int a = 0; a < D; ++a) cw += c[k][a] * wu[e * D + a];
-            double S = 0.0, X = 0.0, Q = 0.0;
-            for (int q = 0; q <= D; ++q) {
-                S += al[q];
-                X += pv[q];
-                Q += al[q] * pv[q];
-            }
-            const double cm = adet / cmden;
-            const double mass = alpha ? cm * (S * X + Q + S * pv[k] + al[k] * (X + 2.0 * pv[k])) : 0.0;
-            acc += (we[e] - rhok[e]) * vol / (D + 1) + dt * H[e] * sgn * cw / fact - mass;
+            acc += nv == 1 ? loc[e] : loc[e * nv + (code & 3)];
         }
         b[i] = acc;
     }
@@ -187,12 +202,12 @@ __global__ void __launch_bounds__(kT) k_pj_post(int64_t n_el, const int32_t *__r
             d[q] = dp[g];
             pb += pn[g] + dp[g];
         }
-        const double det = cofactors<D>(v, c);
+        const double dtdet = dt / cofactors<D>(v, c);
         double u2 = 0.0;
         for (int a = 0; a < D; ++a) {
             double gr = 0.0;
             for (int q = 0; q <= D; ++q) gr += c[q][a] * d[q];
-            const double u = wu_tt[e * D + a] - dt * (gr / det);
+            const double u = wu_tt[e * D + a] - dtdet * gr;
             wu_new[e * D + a] = u;
             u2 += u * u;
         }
@@ -207,30 +222,24 @@ __global__ void __launch_bounds__(kT) k_pj_add(int64_t n, const double *__restri
         y[i] = a[i] + b[i];
 }
 
-// Lumped nodal weights of the general-EOS mass sum, gathered per node over
-// its elements in ascending order: m_i = sum_e w_ei, s_i = sum_e w_ei / rho_e,
-// w_ei = |T_e| / (d+1) (vertex quadrature).
+// Lumped weights of the general-EOS mass sum, per element: w_e = |T_e|/(d+1)
+// into w[e] and w_e / rho_e into wr[e]; k_pj_gather then forms
+// m_i = sum_e w_e and s_i = sum_e w_e / rho_e over each node's elements in
+// ascending order (vertex quadrature).
 template <int D>
-__global__ void __launch_bounds__(kT) k_nt_weights(int64_t n_nodes, const int64_t *__restrict__ n2e_ptr,
-                                                   const int32_t *__restrict__ n2e, const int32_t *__restrict__ conn,
-                                                   const double *__restrict__ x, const double *__restrict__ rho,
-                                                   double *__restrict__ mi, double *__restrict__ si) {
+__global__ void __launch_bounds__(kT) k_nt_elem_weights(int64_t n_el, const int32_t *__restrict__ conn,
+                                                        const double *__restrict__ x, const double *__restrict__ rho,
+                                                        double *__restrict__ w, double *__restrict__ wr) {
     constexpr double fact = D == 3 ? 6.0 : 2.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
-        double m = 0.0, sr = 0.0;
-        for (int64_t t = n2e_ptr[i]; t < n2e_ptr[i + 1]; ++t) {
-            const int64_t e = n2e[t] >> 2;
-            double v[D + 1][D], c[D + 1][D];
-            for (int q = 0; q <= D; ++q) {
-                const int64_t g = conn[e * (D + 1) + q];
-                for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
-            }
-            const double w = fabs(cofactors<D>(v, c)) / fact / (D + 1);
-            m += w;
-            sr += w / rho[e];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+        double v[D + 1][D], c[D + 1][D];
+        for (int q = 0; q <= D; ++q) {
+            const int64_t g = conn[e * (D + 1) + q];
+            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
         }
-        mi[i] = m;
-        si[i] = sr;
+        const double we = fabs(cofactors<D>(v, c)) / fact / (D + 1);
+        w[e] = we;
+        wr[e] = we / rho[e];
     }
 }
 
@@ -314,6 +323,7 @@ int ensure_proj(ps_mesh *m) {
         if (rc == PS_OK) rc = A(&p, (size_t)N * 8), P->alpha = (double *)p;
         if (rc == PS_OK) rc = A(&p, (size_t)N), P->dir = (uint8_t *)p;
         if (rc == PS_OK) rc = A(&p, (size_t)N * 8), P->b = (double *)p;
+        if (rc == PS_OK) rc = A(&p, (size_t)E * nv * 8), P->loc = (double *)p;
         if (rc == PS_OK) rc = A(&p, 256), P->flag = (int *)p;
         if (rc != PS_OK) {
             dfree_all(c, P->allocs);
@@ -476,13 +486,12 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
             rc = check_positive(m, h_out, s);
             if (rc == PS_OK) rc = beta_update_device(m, h_out, dt * dt, s);
             if (rc != PS_OK) return rc;
-            const int g = grid(N, m->ctx->sms);
+            const int ge = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_rhs<3><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, P->alpha, P->dir, h_out, rhok_out,
-                                             wu, we, pn, dt, P->b);
+                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
             else
-                k_pj_rhs<2><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, P->alpha, P->dir, h_out, rhok_out,
-                                             wu, we, pn, dt, P->b);
+                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
+            k_pj_gather<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->dir, P->loc, dim + 1, P->b);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
         }
@@ -605,13 +614,17 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
         if (rc != PS_OK) return rc;
         ProjData *P = static_cast<ProjData *>(m->proj);
         const int ge = grid(E, m->ctx->sms), gn = grid(N, m->ctx->sms);
+        // the per-element weights use the two halves of the contribution buffer
+        double *w = P->loc, *wr = P->loc + E;
         if (dim == 3) {
             k_pj_first<3><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
-            k_nt_weights<3><<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, rho, P->mi, P->si);
+            k_nt_elem_weights<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, rho, w, wr);
         } else {
             k_pj_first<2><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
-            k_nt_weights<2><<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, rho, P->mi, P->si);
+            k_nt_elem_weights<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, rho, w, wr);
         }
+        k_pj_gather<<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, nullptr, w, 1, P->mi);
+        k_pj_gather<<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, nullptr, wr, 1, P->si);
         rc = cuda_rc(cudaGetLastError());
         if (rc != PS_OK) return rc;
     }
@@ -623,13 +636,12 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
             rc = check_positive(m, h_out, s);
             if (rc == PS_OK) rc = beta_update_device(m, h_out, dt * dt, s, false);
             if (rc != PS_OK) return rc;
-            const int g = grid(N, m->ctx->sms);
+            const int ge = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_rhs<3><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, nullptr, P->dir, h_out, rhok_out,
-                                             wu, we, pn, dt, P->c);
+                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
             else
-                k_pj_rhs<2><<<g, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->conn, P->x, nullptr, P->dir, h_out, rhok_out,
-                                             wu, we, pn, dt, P->c);
+                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
+            k_pj_gather<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->dir, P->loc, dim + 1, P->c);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
         }
