@@ -36,6 +36,7 @@ struct ProjData {
     uint8_t *dir = nullptr;       // [n_nodes] Dirichlet flags
     double *b = nullptr;          // [n_nodes] right-hand side
     double *loc = nullptr;        // [n_elems * (dim + 1)] per-element contributions before the gather
+    double *geo = nullptr;        // [n_elems * (1 + (dim + 1) dim)] |T| and grad lambda_k per element
     int *flag = nullptr;          // enthalpy check
     int64_t alpha_version = -1;
     // general-EOS Newton iteration (allocated on its first call)
@@ -114,9 +115,31 @@ __global__ void __launch_bounds__(kT) k_pj_check(int64_t n, const double *__rest
         if (!(v[i] > 0.0) || !isfinite(v[i])) atomicOr(flag, 1);
 }
 
+// Element geometry, once per mesh (FP64): geo[e G] = |T_e|, then
+// grad lambda_k = c_k / det for k = 0..d (G = 1 + (d+1) d).  The element
+// passes below read it instead of recomputing cofactors from coordinates:
+// FP64 arithmetic is scarce on this part.
+template <int D>
+__global__ void __launch_bounds__(kT) k_pj_geometry(int64_t n_el, const int32_t *__restrict__ conn,
+                                                    const double *__restrict__ x, double *__restrict__ geo) {
+    constexpr int G = 1 + (D + 1) * D;
+    constexpr double fact = D == 3 ? 6.0 : 2.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+        double v[D + 1][D], c[D + 1][D];
+        for (int q = 0; q <= D; ++q) {
+            const int64_t g = conn[e * (D + 1) + q];
+            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
+        }
+        const double det = cofactors<D>(v, c);
+        const double inv = 1.0 / det;
+        geo[e * G] = fabs(det) / fact;
+        for (int k = 0; k <= D; ++k)
+            for (int a = 0; a < D; ++a) geo[e * G + 1 + k * D + a] = c[k][a] * inv;
+    }
+}
+
 // Right-hand side of the weak problem, in two passes.  Element pass (one
-// thread per element, the element's geometry computed once): the
-// contribution to each local vertex k,
+// thread per element): the contribution to each local vertex k,
 //   (W~_E - rho K)_e |T| / (d+1)                       source term
 // + dt H_e |T| W~~_u,e . grad lambda_k                 divergence term
 // - (M^e_alpha P^n)_k = cm (S X + Q + S P_k + alpha_k (X + 2 P_k))
@@ -127,38 +150,36 @@ __global__ void __launch_bounds__(kT) k_pj_check(int64_t n, const double *__rest
 // node-to-element list (deterministic, no atomics), 0 on Dirichlet nodes.
 template <int D>
 __global__ void __launch_bounds__(kT) k_pj_elem_rhs(int64_t n_el, const int32_t *__restrict__ conn,
-                                                    const double *__restrict__ x, const double *__restrict__ alpha,
+                                                    const double *__restrict__ geo, const double *__restrict__ alpha,
                                                     const double *__restrict__ H, const double *__restrict__ rhok,
                                                     const double *__restrict__ wu, const double *__restrict__ we,
                                                     const double *__restrict__ p, double dt, double *__restrict__ loc) {
-    constexpr double fact = D == 3 ? 6.0 : 2.0;           // d!
-    constexpr double cmden = D == 3 ? 720.0 : 120.0;      // cm = |T| d! / (d+3)! = |det| / (d+3)!
+    constexpr int G = 1 + (D + 1) * D;
+    constexpr double cmf = D == 3 ? 1.0 / 120.0 : 1.0 / 60.0;   // d! / (d+3)!
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
-        double v[D + 1][D], c[D + 1][D];
-        double al[D + 1], pv[D + 1];
+        const double *ge = geo + e * G;
+        const double vol = ge[0];
+        double al[D + 1], pv[D + 1], u[D];
         for (int q = 0; q <= D; ++q) {
             const int64_t g = conn[e * (D + 1) + q];
-            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
             al[q] = alpha ? alpha[g] : 0.0;
             pv[q] = alpha ? p[g] : 0.0;
         }
-        const double det = cofactors<D>(v, c);
-        const double adet = fabs(det);
-        const double sgn = det > 0.0 ? 1.0 : -1.0;
-        const double vol = adet / fact;
+        for (int a = 0; a < D; ++a) u[a] = wu[e * D + a];
         double S = 0.0, X = 0.0, Q = 0.0;
         for (int q = 0; q <= D; ++q) {
             S += al[q];
             X += pv[q];
             Q += al[q] * pv[q];
         }
-        const double cm = adet / cmden;
+        const double cm = vol * cmf;
         const double src = (we[e] - rhok[e]) * vol / (D + 1);
+        const double dhv = dt * H[e] * vol;
         for (int k = 0; k <= D; ++k) {
-            double cw = 0.0;
-            for (int a = 0; a < D; ++a) cw += c[k][a] * wu[e * D + a];
+            double gw = 0.0;
+            for (int a = 0; a < D; ++a) gw += ge[1 + k * D + a] * u[a];
             const double mass = alpha ? cm * (S * X + Q + S * pv[k] + al[k] * (X + 2.0 * pv[k])) : 0.0;
-            loc[e * (D + 1) + k] = src + dt * H[e] * sgn * cw / fact - mass;
+            loc[e * (D + 1) + k] = src + dhv * gw - mass;
         }
     }
 }
@@ -188,26 +209,26 @@ __global__ void __launch_bounds__(kT) k_pj_gather(int64_t n_nodes, const int64_t
 // H), H from it (enthalpy above), rho K = |W_u|^2 / (2 rho).
 template <int D>
 __global__ void __launch_bounds__(kT) k_pj_post(int64_t n_el, const int32_t *__restrict__ conn,
-                                                const double *__restrict__ x, const double *__restrict__ pn,
+                                                const double *__restrict__ geo, const double *__restrict__ pn,
                                                 const double *__restrict__ dp, const double *__restrict__ wu_tt,
                                                 const double *__restrict__ rho, double h1, double hb, double dt,
                                                 double *__restrict__ wu_new, double *__restrict__ H,
                                                 double *__restrict__ rhok) {
+    constexpr int G = 1 + (D + 1) * D;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
-        double v[D + 1][D], c[D + 1][D], d[D + 1];
+        const double *ge = geo + e * G;
+        double d[D + 1];
         double pb = 0.0;
         for (int q = 0; q <= D; ++q) {
             const int64_t g = conn[e * (D + 1) + q];
-            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
             d[q] = dp[g];
             pb += pn[g] + dp[g];
         }
-        const double dtdet = dt / cofactors<D>(v, c);
         double u2 = 0.0;
         for (int a = 0; a < D; ++a) {
             double gr = 0.0;
-            for (int q = 0; q <= D; ++q) gr += c[q][a] * d[q];
-            const double u = wu_tt[e * D + a] - dtdet * gr;
+            for (int q = 0; q <= D; ++q) gr += ge[1 + q * D + a] * d[q];
+            const double u = wu_tt[e * D + a] - dt * gr;
             wu_new[e * D + a] = u;
             u2 += u * u;
         }
@@ -227,17 +248,12 @@ __global__ void __launch_bounds__(kT) k_pj_add(int64_t n, const double *__restri
 // m_i = sum_e w_e and s_i = sum_e w_e / rho_e over each node's elements in
 // ascending order (vertex quadrature).
 template <int D>
-__global__ void __launch_bounds__(kT) k_nt_elem_weights(int64_t n_el, const int32_t *__restrict__ conn,
-                                                        const double *__restrict__ x, const double *__restrict__ rho,
-                                                        double *__restrict__ w, double *__restrict__ wr) {
-    constexpr double fact = D == 3 ? 6.0 : 2.0;
+__global__ void __launch_bounds__(kT) k_nt_elem_weights(int64_t n_el, const double *__restrict__ geo,
+                                                        const double *__restrict__ rho, double *__restrict__ w,
+                                                        double *__restrict__ wr) {
+    constexpr int G = 1 + (D + 1) * D;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
-        double v[D + 1][D], c[D + 1][D];
-        for (int q = 0; q <= D; ++q) {
-            const int64_t g = conn[e * (D + 1) + q];
-            for (int a = 0; a < D; ++a) v[q][a] = x[g * D + a];
-        }
-        const double we = fabs(cofactors<D>(v, c)) / fact / (D + 1);
+        const double we = geo[e * G] / (D + 1);
         w[e] = we;
         wr[e] = we / rho[e];
     }
@@ -324,6 +340,7 @@ int ensure_proj(ps_mesh *m) {
         if (rc == PS_OK) rc = A(&p, (size_t)N), P->dir = (uint8_t *)p;
         if (rc == PS_OK) rc = A(&p, (size_t)N * 8), P->b = (double *)p;
         if (rc == PS_OK) rc = A(&p, (size_t)E * nv * 8), P->loc = (double *)p;
+        if (rc == PS_OK) rc = A(&p, (size_t)E * (1 + nv * dim) * 8), P->geo = (double *)p;
         if (rc == PS_OK) rc = A(&p, 256), P->flag = (int *)p;
         if (rc != PS_OK) {
             dfree_all(c, P->allocs);
@@ -366,6 +383,16 @@ int ensure_proj(ps_mesh *m) {
         if (er == cudaSuccess) er = cudaMemcpy(P->n2e_ptr, ptr.data(), ptr.size() * 8, cudaMemcpyHostToDevice);
         if (er == cudaSuccess) er = cudaMemcpy(P->n2e, n2e.data(), n2e.size() * 4, cudaMemcpyHostToDevice);
         if (er == cudaSuccess) er = cudaMemcpy(P->dir, dir.data(), dir.size(), cudaMemcpyHostToDevice);
+        if (er != cudaSuccess) {
+            dfree_all(c, P->allocs);
+            delete P;
+            return cuda_rc(er);
+        }
+        // element geometry once per mesh: |T| and the barycentric gradients
+        if (dim == 3) k_pj_geometry<3><<<grid(E, m->ctx->sms), kT>>>(E, P->conn, P->x, P->geo);
+        else k_pj_geometry<2><<<grid(E, m->ctx->sms), kT>>>(E, P->conn, P->x, P->geo);
+        er = cudaGetLastError();
+        if (er == cudaSuccess) er = cudaDeviceSynchronize();
         if (er != cudaSuccess) {
             dfree_all(c, P->allocs);
             delete P;
@@ -488,9 +515,9 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
             if (rc != PS_OK) return rc;
             const int ge = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
+                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->geo, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
             else
-                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
+                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->geo, P->alpha, h_out, rhok_out, wu, we, pn, dt, P->loc);
             k_pj_gather<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->dir, P->loc, dim + 1, P->b);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
@@ -509,9 +536,9 @@ extern "C" int ps_projection_step(ps_mesh *m, const ps_projection_opts *o, const
             ProjData *P = static_cast<ProjData *>(m->proj);
             const int g = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
+                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->geo, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
             else
-                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
+                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->geo, pn, dp, wu, rho, g1, 0.0, dt, wu_out, h_out, rhok_out);
             k_pj_add<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, pn, dp, p_out);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
@@ -618,10 +645,10 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
         double *w = P->loc, *wr = P->loc + E;
         if (dim == 3) {
             k_pj_first<3><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
-            k_nt_elem_weights<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, rho, w, wr);
+            k_nt_elem_weights<3><<<ge, kT, 0, s>>>(E, P->geo, rho, w, wr);
         } else {
             k_pj_first<2><<<ge, kT, 0, s>>>(E, P->conn, pn, rho, wu, h1, hb, h_out, rhok_out);
-            k_nt_elem_weights<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, rho, w, wr);
+            k_nt_elem_weights<2><<<ge, kT, 0, s>>>(E, P->geo, rho, w, wr);
         }
         k_pj_gather<<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, nullptr, w, 1, P->mi);
         k_pj_gather<<<gn, kT, 0, s>>>(N, P->n2e_ptr, P->n2e, nullptr, wr, 1, P->si);
@@ -638,9 +665,9 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
             if (rc != PS_OK) return rc;
             const int ge = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->x, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
+                k_pj_elem_rhs<3><<<ge, kT, 0, s>>>(E, P->conn, P->geo, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
             else
-                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->x, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
+                k_pj_elem_rhs<2><<<ge, kT, 0, s>>>(E, P->conn, P->geo, nullptr, h_out, rhok_out, wu, we, pn, dt, P->loc);
             k_pj_gather<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->n2e_ptr, P->n2e, P->dir, P->loc, dim + 1, P->c);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
@@ -690,9 +717,9 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
             ProjData *P = static_cast<ProjData *>(m->proj);
             const int g = grid(E, m->ctx->sms);
             if (dim == 3)
-                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
+                k_pj_post<3><<<g, kT, 0, s>>>(E, P->conn, P->geo, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
             else
-                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->x, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
+                k_pj_post<2><<<g, kT, 0, s>>>(E, P->conn, P->geo, pn, dp, wu, rho, h1, hb, dt, wu_out, h_out, rhok_out);
             k_pj_add<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, pn, dp, p_out);
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
