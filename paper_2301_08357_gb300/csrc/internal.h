@@ -48,6 +48,7 @@ struct Workspace {
     bool ones_ready = false;
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphRec> graphs;
+    int64_t last_iters[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // iterations of the last CG run per graph kind
 };
 
 int dalloc(ps_ctx *ctx, void **p, size_t bytes, std::vector<DevAlloc> &owner);

@@ -901,14 +901,23 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, bool fused, cudaStrea
             if (w.h_st->done) return PS_OK;
         }
     }
-    GraphRec *g = nullptr;
-    for (auto &r : w.graphs)
-        if (r.kind == kind && r.iters == gi) g = &r;
-    if (!g) {
+    // Graph lengths follow the iteration count of this kind's previous run on
+    // the mesh (successive CG runs of one mesh need similar counts): the
+    // first launches cover that count in graphs of at most gi iterations,
+    // rounded up to 4; past it, graphs of 4, 8, 16, ... iterations.  A
+    // converged state makes the remaining iterations of a graph return at
+    // once, so this only trims those idle launches.  Lengths are multiples
+    // of 4 up to gi: a handful of captured graphs per kind.
+    auto graph_of = [&](int len, GraphRec **out) -> int {
+        for (auto &r : w.graphs)
+            if (r.kind == kind && r.iters == len) {
+                *out = &r;
+                return PS_OK;
+            }
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
         const int64_t saved_launches = m->launches;
-        int rc = enqueue_cg_iters<T>(m, gi, fused, w.cap_stream);
+        int rc = enqueue_cg_iters<T>(m, len, fused, w.cap_stream);
         m->launches = saved_launches;
         cudaError_t e2 = cudaMemcpyAsync(w.h_st, w.st, sizeof(CgState), cudaMemcpyDeviceToHost, w.cap_stream);
         cudaError_t e = cudaStreamEndCapture(w.cap_stream, &graph);
@@ -919,14 +928,30 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, bool fused, cudaStrea
         e = cudaGraphInstantiate(&ex, graph, 0);
         cudaGraphDestroy(graph);
         CK(e);
-        w.graphs.push_back(GraphRec{kind, gi, ex});
-        g = &w.graphs.back();
-    }
+        w.graphs.push_back(GraphRec{kind, len, ex});
+        *out = &w.graphs.back();
+        return PS_OK;
+    };
+    const int64_t hint = w.last_iters[kind];
+    int64_t ran = 0;
+    int extra = 0;
     for (;;) {
+        int len = gi;
+        if (hint > 0) {
+            const int64_t rem = hint - ran;
+            len = rem > 0 ? (int)std::min<int64_t>(gi, (rem + 3) / 4 * 4) : std::min(gi, 4 << std::min(extra++, 8));
+            len = std::max(1, std::min(len, gi));
+        }
+        GraphRec *g = nullptr;
+        RC(graph_of(len, &g));
         CK(cudaGraphLaunch(g->exec, s));
-        m->launches += per_iter * (int64_t)gi;
+        m->launches += per_iter * (int64_t)len;
         CK(cudaStreamSynchronize(s));
-        if (w.h_st->done) return PS_OK;
+        ran += len;
+        if (w.h_st->done) {
+            w.last_iters[kind] = w.h_st->iters;
+            return PS_OK;
+        }
     }
 }
 
