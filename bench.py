@@ -785,9 +785,10 @@ def run_projection(args, eos=False):
         times.append(e0.elapsed_time(e1))
         iters += info.iters_inner + info.iters_outer
         if eos:
-            # solve launches + first guess, weights (3) + per Picard iteration: check, beta, right-hand
-            # side (2), post (2) + per Newton check: linearise, alpha, diagonal (2), FP64 apply (4), norms
-            launches += info.kernel_launches + 4 + 6 * n_pic + 9 * n_checks[0]
+            # solve launches + first guess, weights (3), final alpha + diagonal (3) + per Picard
+            # iteration: check, beta, right-hand side (2), post (2), diagonal (2) + per Newton check:
+            # linearise, alpha, FP64 apply (4), norms
+            launches += info.kernel_launches + 7 + 8 * n_pic + 7 * n_checks[0]
         else:
             # solve launches + per Picard iteration: check, beta, diagonal (2), right-hand side (2),
             # post (2); + first guess

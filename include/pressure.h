@@ -340,7 +340,8 @@ int ps_projection_step(ps_mesh *mesh, const ps_projection_opts *opts, const doub
  * Newton from the current dP: J = diag(Q'_i) + dt^2 K_H, Q'_i the derivative
  * of the mass sum, set as the mesh's alpha_i = Q'_i / m_i (lumped operator),
  * then J dP_new = J dP - F(dP) solved by ps_pressure_solve (opts->solve,
- * warm start dP).  The step stops when ||F||_2 <= newton_tol ||c||_2 over
+ * warm start dP; its Jacobi preconditioner is the diagonal of the Picard
+ * iteration's first Jacobian).  The step stops when ||F||_2 <= newton_tol ||c||_2 over
  * the free nodes (checked before each solve and after the last) or after
  * max_newton solves.  Then the post-projection of ps_projection_step with
  * the EOS enthalpy.

@@ -61,7 +61,7 @@ template <typename T, int MODE>
 int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 
 int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s, bool diag = true);
-int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s);
+int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s, bool diag = true);
 
 // projection.cu
 void projection_release(ps_mesh *m);

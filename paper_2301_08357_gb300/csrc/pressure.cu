@@ -712,10 +712,10 @@ int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStrea
 }
 
 // Nodal alpha (caller's numbering, device; each unknown takes its master
-// vertex's value) into both node records, then the Jacobi diagonal; on
+// vertex's value) into both node records, then (diag) the Jacobi diagonal; on
 // stream s without allocating or synchronising.  The caller holds the
 // context mutex.
-int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s) {
+int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s, bool diag) {
     RC(ensure_workspace(m));
     const PrepMesh &p = m->prep;
     MeshDev &d = m->dev;
@@ -723,7 +723,7 @@ int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s) {
         p.loc_total, m->d_loc_node, m->d_old_of_new, alpha_dev, d.dirichlet, const_cast<NodeF *>(d.node32),
         const_cast<NodeD *>(d.node64));
     CK(cudaGetLastError());
-    return diag_update_device(m, s);
+    return diag ? diag_update_device(m, s) : PS_OK;
 }
 
 int ensure_workspace(ps_mesh *m) {

@@ -689,7 +689,10 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
                     ps_set_last_error("general-EOS projection: a Jacobian entry Q'_i is not positive and finite");
                     return PS_EINVAL;
                 }
-                rc = alpha_update_device(m, P->au, s);
+                // the Jacobi preconditioner of this Picard iteration's Newton
+                // solves is the diagonal of its first Jacobian (beta is fixed
+                // within the iteration; alpha moves little between steps)
+                rc = alpha_update_device(m, P->au, s, j == 0);
                 if (rc != PS_OK) return rc;
                 m->coeff_ok = true;
                 m->alpha_set = true;
@@ -724,6 +727,11 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
             rc = cuda_rc(cudaGetLastError());
             if (rc != PS_OK) return rc;
         }
+    }
+    if (rc == PS_OK) {
+        // leave the mesh's Jacobi diagonal consistent with its final alpha
+        std::lock_guard<std::mutex> lk(m->ctx->mu);
+        rc = alpha_update_device(m, static_cast<ProjData *>(m->proj)->au, s, true);
     }
     if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
     acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
