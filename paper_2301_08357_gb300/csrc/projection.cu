@@ -274,12 +274,15 @@ __global__ void __launch_bounds__(kT) k_nt_linearise(int64_t n, const uint8_t *_
         const double m = mi[i], sw = si[i];
         const double q = P * (a * m + b * sw * P);
         const double qp = a * m + 2.0 * b * sw * P;
-        alpha[i] = m > 0.0 ? qp / m : a;
+        const bool ok = qp > 0.0 && isfinite(qp);
+        // a rejected entry still leaves a positive alpha in the node records
+        // (their sign bit marks Dirichlet nodes); the call then fails
+        alpha[i] = (m > 0.0 && ok) ? qp / m : a;
         if (dir[i]) {
             r[i] = 0.0;
             continue;
         }
-        if (!(qp > 0.0) || !isfinite(qp)) atomicOr(flag, 1);
+        if (!ok) atomicOr(flag, 1);
         r[i] = c[i] - q + qp * dp[i];
     }
 }
@@ -576,7 +579,9 @@ void add_solve(ps_solve_info &acc, const ps_solve_info &inf) {
 
 // ||F(dP)|| / ||c|| over the free nodes, F = J dP - r with J the lumped
 // operator now on the mesh (FP64 apply); deterministic (fixed-order sums).
-int newton_residual(ps_mesh *m, const double *dp, cudaStream_t s, double *res) {
+// Also returns the linearisation's rejection flag (one synchronisation for
+// both).
+int newton_residual(ps_mesh *m, const double *dp, cudaStream_t s, double *res, int *flag) {
     ProjData *P = static_cast<ProjData *>(m->proj);
     int rc = ps_pressure_apply(m, dp, P->y, PS_F64, s);
     if (rc != PS_OK) return rc;
@@ -587,6 +592,7 @@ int newton_residual(ps_mesh *m, const double *dp, cudaStream_t s, double *res) {
         rc = cuda_rc(cudaGetLastError());
         if (rc == PS_OK)
             rc = cuda_rc(cudaMemcpyAsync(red.data(), P->red, red.size() * 8, cudaMemcpyDeviceToHost, s));
+        if (rc == PS_OK) rc = cuda_rc(cudaMemcpyAsync(flag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
         if (rc != PS_OK) return rc;
     }
@@ -681,14 +687,6 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
                 if (rc != PS_OK) return rc;
                 k_nt_linearise<<<grid(N, m->ctx->sms), kT, 0, s>>>(N, P->dir, pn, dp, P->mi, P->si, P->c, a, b,
                                                                     P->au, P->r, P->flag);
-                int h = 0;
-                rc = cuda_rc(cudaMemcpyAsync(&h, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-                if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
-                if (rc != PS_OK) return rc;
-                if (h) {
-                    ps_set_last_error("general-EOS projection: a Jacobian entry Q'_i is not positive and finite");
-                    return PS_EINVAL;
-                }
                 // the Jacobi preconditioner of this Picard iteration's Newton
                 // solves is the diagonal of its first Jacobian (beta is fixed
                 // within the iteration; alpha moves little between steps)
@@ -698,10 +696,22 @@ extern "C" int ps_projection_step_eos(ps_mesh *m, const ps_eos_opts *o, const do
                 m->alpha_set = true;
                 m->alpha_newton = true;
             }
+            int bad = 0;
+            double res = 0.0;
             if (check) {
-                double res = 0.0;
-                rc = newton_residual(m, dp, s, &res);
-                if (rc != PS_OK) return rc;
+                rc = newton_residual(m, dp, s, &res, &bad);
+            } else {
+                std::lock_guard<std::mutex> lk(m->ctx->mu);
+                rc = cuda_rc(cudaMemcpyAsync(&bad, static_cast<ProjData *>(m->proj)->flag, sizeof(int),
+                                             cudaMemcpyDeviceToHost, s));
+                if (rc == PS_OK) rc = cuda_rc(cudaStreamSynchronize(s));
+            }
+            if (rc != PS_OK) return rc;
+            if (bad) {
+                ps_set_last_error("general-EOS projection: a Jacobian entry Q'_i is not positive and finite");
+                return PS_EINVAL;
+            }
+            if (check) {
                 if (res_host) res_host[k * stride + j] = res;
                 if (tol > 0.0 && res <= tol) {
                     converged = true;
