@@ -248,106 +248,14 @@ __device__ __forceinline__ void block_sum2(const DotF &a, const DotF &b, double 
 //               cm = |T| d! / (d+3)!  (= |det|/720 in 3D, |det|/120 in 2D),
 //   from int lambda^a = d! |T| prod(a_i!) / (d + sum a_i)!.
 
-template <typename T, typename N4>
-__device__ __forceinline__ void elem_apply_3d(const N4 &p0, const N4 &p1, const N4 &p2, const N4 &p3, T v0,
-                                              T v1, T v2, T v3, T bdt2, T &o0, T &o1, T &o2, T &o3) {
-    const T e1x = p1.x - p0.x, e1y = p1.y - p0.y, e1z = p1.z - p0.z;
-    const T e2x = p2.x - p0.x, e2y = p2.y - p0.y, e2z = p2.z - p0.z;
-    const T e3x = p3.x - p0.x, e3y = p3.y - p0.y, e3z = p3.z - p0.z;
-    const T c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
-    const T c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
-    const T c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
-    const T ad = fabs(e1x * c1x + e1y * c1y + e1z * c1z);
-    const T d1 = v1 - v0, d2 = v2 - v0, d3 = v3 - v0;
-    const T gx = d1 * c1x + d2 * c2x + d3 * c3x;
-    const T gy = d1 * c1y + d2 * c2y + d3 * c3y;
-    const T gz = d1 * c1z + d2 * c2z + d3 * c3z;
-    const T kc = bdt2 / (T(6) * ad);
-    const T k1 = kc * (c1x * gx + c1y * gy + c1z * gz);
-    const T k2 = kc * (c2x * gx + c2y * gy + c2z * gz);
-    const T k3 = kc * (c3x * gx + c3y * gy + c3z * gz);
-    const T k0 = -(k1 + k2 + k3);
-    const T a0 = fabs(p0.w), a1 = fabs(p1.w), a2 = fabs(p2.w), a3 = fabs(p3.w);
-    const T S = (a0 + a1) + (a2 + a3);
-    const T X = (v0 + v1) + (v2 + v3);
-    const T Q = (a0 * v0 + a1 * v1) + (a2 * v2 + a3 * v3);
-    const T cm = ad * T(1.0 / 720.0);
-    const T base = S * X + Q;
-    o0 = cm * (base + S * v0 + a0 * (X + T(2) * v0)) + k0;
-    o1 = cm * (base + S * v1 + a1 * (X + T(2) * v1)) + k1;
-    o2 = cm * (base + S * v2 + a2 * (X + T(2) * v2)) + k2;
-    o3 = cm * (base + S * v3 + a3 * (X + T(2) * v3)) + k3;
-}
-
-template <typename T, typename N4>
-__device__ __forceinline__ void elem_apply_2d(const N4 &p0, const N4 &p1, const N4 &p2, T v0, T v1, T v2,
-                                              T bdt2, T &o0, T &o1, T &o2) {
-    const T e1x = p1.x - p0.x, e1y = p1.y - p0.y;
-    const T e2x = p2.x - p0.x, e2y = p2.y - p0.y;
-    const T c1x = e2y, c1y = -e2x, c2x = -e1y, c2y = e1x;
-    const T ad = fabs(e1x * e2y - e1y * e2x);
-    const T d1 = v1 - v0, d2 = v2 - v0;
-    const T gx = d1 * c1x + d2 * c2x, gy = d1 * c1y + d2 * c2y;
-    const T kc = bdt2 / (T(2) * ad);
-    const T k1 = kc * (c1x * gx + c1y * gy);
-    const T k2 = kc * (c2x * gx + c2y * gy);
-    const T k0 = -(k1 + k2);
-    const T a0 = fabs(p0.w), a1 = fabs(p1.w), a2 = fabs(p2.w);
-    const T S = a0 + a1 + a2, X = v0 + v1 + v2, Q = a0 * v0 + a1 * v1 + a2 * v2;
-    const T cm = ad * T(1.0 / 120.0);
-    const T base = S * X + Q;
-    o0 = cm * (base + S * v0 + a0 * (X + T(2) * v0)) + k0;
-    o1 = cm * (base + S * v1 + a1 * (X + T(2) * v1)) + k1;
-    o2 = cm * (base + S * v2 + a2 * (X + T(2) * v2)) + k2;
-}
-
-// Diagonal entries of the element matrix: cm (2 S + 4 alpha_i) + bdt2 |c_i|^2 / (d! |det|).
-template <typename T, typename N4>
-__device__ __forceinline__ void elem_diag_3d(const N4 &p0, const N4 &p1, const N4 &p2, const N4 &p3, T bdt2,
-                                             T &o0, T &o1, T &o2, T &o3) {
-    const T e1x = p1.x - p0.x, e1y = p1.y - p0.y, e1z = p1.z - p0.z;
-    const T e2x = p2.x - p0.x, e2y = p2.y - p0.y, e2z = p2.z - p0.z;
-    const T e3x = p3.x - p0.x, e3y = p3.y - p0.y, e3z = p3.z - p0.z;
-    const T c1x = e2y * e3z - e2z * e3y, c1y = e2z * e3x - e2x * e3z, c1z = e2x * e3y - e2y * e3x;
-    const T c2x = e3y * e1z - e3z * e1y, c2y = e3z * e1x - e3x * e1z, c2z = e3x * e1y - e3y * e1x;
-    const T c3x = e1y * e2z - e1z * e2y, c3y = e1z * e2x - e1x * e2z, c3z = e1x * e2y - e1y * e2x;
-    const T c0x = -(c1x + c2x + c3x), c0y = -(c1y + c2y + c3y), c0z = -(c1z + c2z + c3z);
-    const T ad = fabs(e1x * c1x + e1y * c1y + e1z * c1z);
-    const T kc = bdt2 / (T(6) * ad);
-    const T a0 = fabs(p0.w), a1 = fabs(p1.w), a2 = fabs(p2.w), a3 = fabs(p3.w);
-    const T S = (a0 + a1) + (a2 + a3);
-    const T cm = ad * T(1.0 / 720.0);
-    o0 = cm * (T(2) * S + T(4) * a0) + kc * (c0x * c0x + c0y * c0y + c0z * c0z);
-    o1 = cm * (T(2) * S + T(4) * a1) + kc * (c1x * c1x + c1y * c1y + c1z * c1z);
-    o2 = cm * (T(2) * S + T(4) * a2) + kc * (c2x * c2x + c2y * c2y + c2z * c2z);
-    o3 = cm * (T(2) * S + T(4) * a3) + kc * (c3x * c3x + c3y * c3y + c3z * c3z);
-}
-
-template <typename T, typename N4>
-__device__ __forceinline__ void elem_diag_2d(const N4 &p0, const N4 &p1, const N4 &p2, T bdt2, T &o0, T &o1,
-                                             T &o2) {
-    const T e1x = p1.x - p0.x, e1y = p1.y - p0.y;
-    const T e2x = p2.x - p0.x, e2y = p2.y - p0.y;
-    const T c1x = e2y, c1y = -e2x, c2x = -e1y, c2y = e1x;
-    const T c0x = -(c1x + c2x), c0y = -(c1y + c2y);
-    const T ad = fabs(e1x * e2y - e1y * e2x);
-    const T kc = bdt2 / (T(2) * ad);
-    const T a0 = fabs(p0.w), a1 = fabs(p1.w), a2 = fabs(p2.w);
-    const T S = a0 + a1 + a2;
-    const T cm = ad * T(1.0 / 120.0);
-    o0 = cm * (T(2) * S + T(4) * a0) + kc * (c0x * c0x + c0y * c0y);
-    o1 = cm * (T(2) * S + T(4) * a1) + kc * (c1x * c1x + c1y * c1y);
-    o2 = cm * (T(2) * S + T(4) * a2) + kc * (c2x * c2x + c2y * c2y);
-}
-
-// ---------------------------------------------------------------- star patches
 // One thread evaluates a whole patch (layout.h): element j is (a, b, r_j,
 // r_{j+1}) in 3D and (a, r_j, r_{j+1}) in 2D.  With e1 = b - a and
 // d_j = r_j - a, the cofactor vectors of element j are
 //   c1 = d_j x d_{j+1},  c2 = -(e1 x d_{j+1}),  c3 = e1 x d_j   (3D)
 //   c1 = perp(d_{j+1}),  c2 = -perp(d_j), perp(v) = (v.y, -v.x)  (2D)
 // so e1 x d_j and the node data of r_j carry over from element j-1 to j.
-// The per-element arithmetic is the one of elem_apply_3d / elem_diag_3d.
+// Per element: the stiffness and mass formulas above; the diagonal (DIAG)
+// takes v = e_i: kc |c_i|^2 and cm (2 S + 4 alpha_i).
 // out[slot]: 0 -> a, 1 -> b, 2 + j -> r_j (j = 0..m); other slots untouched.
 __device__ __forceinline__ float fdiv_fast(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_fast(double a, double b) { return a / b; }

@@ -444,70 +444,6 @@ __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_f
     }
 }
 
-// Kernel 3: x += alpha p; r -= alpha q; z = D^-1 r; rz = r.z; rr = r.r; the
-// last block decides convergence and forms beta.  Vectors are padded to a
-// multiple of 4 entries with zeros.
-template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(int64_t n_pad, T *__restrict__ x, T *__restrict__ r,
-                                                   const T *__restrict__ p, const T *__restrict__ q,
-                                                   const T *__restrict__ dinv, CgState *st, double *dotbuf,
-                                                   int *host_done) {
-    __shared__ double s_red[34];
-    __shared__ bool s_last;
-    if (threadIdx.x == 0) {
-        s_red[0] = st->alpha;
-        s_red[1] = (double)st->done;
-    }
-    __syncthreads();
-    if (s_red[1] != 0.0) return;
-    const T al = (T)s_red[0];
-    typename DotOf<T>::type arz, arr;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
-        const T xi = x[i] + al * p[i];
-        const T ri = r[i] - al * q[i];
-        x[i] = xi;
-        r[i] = ri;
-        const T zi = dinv[i] * ri;
-        arz.add_prod(ri, zi);
-        arr.add_prod(ri, ri);
-    }
-    const double rz = block_sum(arz, s_red);
-    const double rr = block_sum(arr, s_red);
-    if (threadIdx.x == 0) {
-        dotbuf[blockIdx.x] = rz;
-        dotbuf[gridDim.x + blockIdx.x] = rr;
-        const unsigned int t = atomic_add_acq_rel(&st->cnt_b, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    const double rz_new = block_sum_array(dotbuf, gridDim.x, s_red);
-    const double rr_new = block_sum_array(dotbuf + gridDim.x, gridDim.x, s_red);
-    if (threadIdx.x == 0) {
-        st->cnt_b = 0;
-        st->iters += 1;
-        st->rr = rr_new;
-        int done = 0;
-        if (!isfinite(rz_new) || !isfinite(rr_new)) {
-            st->status = kCgBreakdown;
-            done = 1;
-        } else if (rr_new <= st->stop_rr) {
-            st->status = kCgConverged;
-            done = 1;
-        } else if (st->iters >= st->max_iters) {
-            st->status = kCgMaxIter;
-            done = 1;
-        } else {
-            st->beta = rz_new / st->rz;
-            st->rz = rz_new;
-        }
-        if (done) {
-            st->done = 1;
-            if (host_done) *(volatile int *)host_done = 1;
-        }
-    }
-}
-
 // Start of an inner FP32 solve of A d = r64 * scale (mixed mode), or of an
 // FP64 PCG run from a residual already in r (mode FP64: rsrc == nullptr).
 // Sets d = 0, p = 0, rz = r.D^-1 r, rr0 = r.r, stop_rr = tol2 * (rr0 or bb).
