@@ -97,7 +97,9 @@ typedef struct {
     int64_t max_iters;       /* cap on total CG iterations (0 = 100000)            */
     int32_t mode;            /* PS_MODE_FP64 or PS_MODE_MIXED                       */
     int32_t precond;         /* PS_PRECOND_JACOBI (default) or PS_PRECOND_NONE     */
-    double inner_tol;        /* mixed: inner FP32 relative reduction (0 = 1e-4)    */
+    double inner_tol;        /* mixed: inner FP32 relative reduction (0 = 1e-4);   */
+                             /* an outer step that needs less to reach tol asks    */
+                             /* for 10x what it needs instead (at most 0.5)        */
     int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
     int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
                              /* negative = launch kernels directly, no graph)      */

@@ -256,7 +256,11 @@ __global__ void __launch_bounds__(256) k_b_resid2(const BMesh *meshes, const int
             st->scale = 1.0 / sqrt(rr);
             CgState &in = st->in;
             in.rz = in.pq = in.alpha = in.beta = in.rr = in.rr0 = in.stop_rr = 0.0;
-            in.tol2 = st->inner_tol2;
+            // the inner reduction of the single-solve engines (inner_reduction)
+            const double itol = sqrt(st->inner_tol2);
+            const double need = 0.1 * sqrt(st->tol2) * sqrt(bb) / sqrt(rr);
+            const double it_k = need > itol ? fmin(need, 0.5) : itol;
+            in.tol2 = it_k * it_k;
             in.iters = 0;
             in.max_iters = st->max_iters - st->iters_total;
             in.done = 0;

@@ -62,6 +62,7 @@ int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 
 int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s, bool diag = true);
 int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s, bool diag = true);
+double inner_reduction(double itol, double tol, double bb, double rr);
 
 // projection.cu
 void projection_release(ps_mesh *m);

@@ -992,6 +992,20 @@ static int check_dev_err(ps_ctx *c) {
 
 static constexpr int64_t kFusedMaxNodes = 200000;
 
+}  // namespace ps
+
+// Relative reduction asked of an inner FP32 solve of the mixed solver: the
+// configured one, or, when the outer residual is already close to the
+// target, only what is still needed times 0.1 (at most 0.5).  ||r||^2 = rr,
+// ||b||^2 = bb.
+double ps::inner_reduction(double itol, double tol, double bb, double rr) {
+    if (!(rr > 0.0)) return itol;
+    const double need = 0.1 * tol * std::sqrt(bb > 0.0 ? bb : 1.0) / std::sqrt(rr);
+    return need > itol ? std::min(need, 0.5) : itol;
+}
+
+namespace ps {
+
 int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cudaStream_t s) {
     Workspace &w = m->ws;
     const int64_t np = m->dev.n_pad;
@@ -1077,14 +1091,17 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
             if (rr <= stop_abs2) { status = PS_OK; break; }
             if (used >= max_it || outer > max_outer) { status = PS_ENOTCONV; break; }
             const double scale = 1.0 / std::sqrt(rr);
+            // inner reduction: itol, or only what the outer tolerance still
+            // needs (with a factor 10 of margin) when that is less
+            const double it_k = inner_reduction(itol, tol, bb, rr);
             if (fused) {
                 const CG1Vec v = cg1_vec(m);
-                k_cg1_init_state<<<1, 32, 0, s>>>(w.st, itol * itol, max_it - used);
+                k_cg1_init_state<<<1, 32, 0, s>>>(w.st, it_k * it_k, max_it - used);
                 k_cg1_start<<<g3, kBlock, 0, s>>>(np, m->prep.sh_total, v, w.r64, scale);
                 m->launches += 2;
             } else {
                 Cg2Args<float> a = cg2_args<float>(m);
-                k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, itol * itol, 1,
+                k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, it_k * it_k, 1,
                                                              max_it - used);
                 m->launches += 1;
             }
