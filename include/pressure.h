@@ -183,7 +183,10 @@ int64_t ps_ctx_bytes_in_use(const ps_ctx *ctx);
  *   opts        preprocessing options or NULL
  * Host work: element partition into chunks along a Morton curve, node
  * renumbering (chunk-interior nodes contiguous per chunk, nodes shared between
- * chunks after them), per-chunk local connectivity and incidence lists.
+ * chunks after them), per-chunk local connectivity and incidence lists, and
+ * the FP64 stiffness weights of every element for the FP64 passes (about
+ * 75 B per tetrahedron, 40 B per triangle of device memory, padding
+ * included; ps_mesh_stats.device_bytes gives the total).
  * Errors: PS_EINVAL for dim not 2/3, n_elems < 1, a vertex id out of range, a
  * non-finite coordinate or an element of zero volume; PS_ENOMEM. */
 int ps_mesh_upload(ps_ctx *ctx, int dim, int64_t n_nodes, const double *coords,
