@@ -311,3 +311,43 @@ def test_eos_step_rejects_periodic_meshes(env):
         assert ei.value.status == P.PS_EINVAL
     finally:
         P.ps_mesh_free(m)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (3, 6)])
+def test_lumped_apply_on_periodic_mesh(env, dim, n):
+    """Lumped mass on a mesh with merged periodic vertices: the merged operator
+    P^T (diag(alpha m) + dt^2 K) P of the unmerged mesh (every vertex its own
+    weight m_v, alpha from the master), built here from the oracle's pieces."""
+    import scipy.sparse as sp
+    from oracle.periodic import PeriodicMatrix
+    P, torch, ctx = env
+    case = S.make_periodic_case(dim, n)
+    master = case.extra["master"]
+    N = case.n_nodes
+    Pm = PeriodicMatrix(dim, case.coords, case.conn, case.dirichlet, master, case.alpha, case.beta, case.dt2)
+    K = oracle.PressureMatrix(dim, case.coords, case.conn, np.zeros(N, np.uint8), case.alpha, case.beta, 1.0,
+                              part=2)
+    assert np.array_equal(K.node_of_free, np.arange(N))
+    mv = L.lumped_weights(dim, case.coords, case.conn)
+    A_full = sp.diags(np.asarray(case.alpha)[master] * mv) + case.dt2 * K.scipy()
+    Ad = (Pm.P.T @ A_full @ Pm.P).tocsr()[Pm.free][:, Pm.free]
+    m = P.ps_mesh_upload(ctx, dim, case.coords, case.conn, case.dirichlet, periodic=master)
+    try:
+        P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+        P.ps_mesh_set_mass(m, P.PS_MASS_LUMPED)
+        x = np.random.default_rng(8).standard_normal(N)
+        for prec, tol in ((2, 1e-12), (1, 2e-5)):
+            dt = torch.float64 if prec == 2 else torch.float32
+            xd = torch.as_tensor(x, dtype=dt, device="cuda")
+            yd = torch.full_like(xd, float("nan"))
+            P.ps_pressure_apply(m, xd, yd, prec)
+            y = yd.cpu().double().numpy()
+            xu = xd.cpu().double().numpy()
+            xf = Pm.to_dofs(xu)[Pm.free]
+            ref = Pm.to_user(Ad @ xf)
+            scale = Pm.to_user(abs(Ad) @ np.abs(xf))
+            free = scale > 0
+            assert np.max(np.abs(y - ref)[free] / scale[free]) <= tol, prec
+            assert np.array_equal(y, y[master])
+    finally:
+        P.ps_mesh_free(m)
