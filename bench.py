@@ -622,9 +622,10 @@ def run_served(args):
         meshes.append(m)
     nodes_total = sum(c.n_nodes for c in cases)
 
-    def one_run(rate):
-        """rate None = closed loop (each case submits its next step when the last completes)."""
-        srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32)
+    def one_run(rate, budget=0):
+        """rate None = closed loop (each case submits its next step when the last completes);
+        budget: the server's HBM cap on in-flight solver workspaces (0 = the context's)."""
+        srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32, hbm_budget_bytes=budget)
         ids = [P.ps_server_add_case(srv, m) for m in meshes]
         state = [(c.beta.copy(), c.b.copy()) for c in cases]
         lat, qwait, done_iters = [], [], 0
@@ -705,6 +706,11 @@ def run_served(args):
     runs = [sat]
     for f in [float(v) for v in args.rates.split(",") if v]:
         runs.append(dict(one_run(f * sat["solves_per_s"]), rate_x_sat=f))
+    # closed loop under an HBM budget that admits about a quarter of the cases'
+    # workspaces at once (never less than the largest): admission queues requests
+    ws_bytes = [P.ps_mesh_get_stats(m).solve_bytes for m in meshes]
+    budget = int(max(max(ws_bytes), sum(ws_bytes) // 4))
+    runs.append(dict(one_run(None, budget), hbm_budget_bytes=budget, workspace_bytes_total=int(sum(ws_bytes))))
     singles = [single_run(P.PS_MODE_FP64), single_run(P.PS_MODE_MIXED)]
     out = {"metric": METRIC, "value": sat["dof_iters_per_s"], "unit": UNIT, "n_gpus": 1,
            "steps": args.case_steps, "warmup": 0, "ms_per_step": 1e3 / sat["solves_per_s"],
