@@ -101,7 +101,9 @@ typedef struct {
                              /* an outer step that needs less to reach tol asks    */
                              /* for 10x what it needs instead (at most 0.5)        */
     int32_t max_outer;       /* mixed: cap on defect-correction steps (0 = 40)     */
-    int32_t graph_iters;     /* iterations per captured CUDA graph launch (0 = 32; */
+    int32_t graph_iters;     /* most iterations per captured CUDA graph launch     */
+                             /* (0 = 32; shorter batches follow the previous run's */
+                             /* iteration count;                                   */
                              /* negative = launch kernels directly, no graph)      */
     int32_t engine;          /* single solves, captured in CUDA graphs:             */
                              /* PS_ENGINE_GRAPH: two kernels per CG iteration;      */

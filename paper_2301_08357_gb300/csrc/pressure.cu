@@ -884,8 +884,9 @@ static int enqueue_cg_iters(ps_mesh *m, int iters, bool fused, cudaStream_t s) {
     return PS_OK;
 }
 
-// Run CG iterations until the device state says done: graph batches of
-// `gi` iterations followed by a copy of the state to pinned host memory.
+// Run CG iterations until the device state says done: graph batches of at
+// most `gi` iterations (lengths below), each followed by a copy of the state
+// to pinned host memory; gi <= 0 launches kernels directly.
 template <typename T>
 static int run_cg_until_done(ps_mesh *m, int gi, bool jac, bool fused, cudaStream_t s) {
     Workspace &w = m->ws;
