@@ -40,6 +40,17 @@ def test_header_declarations_are_exported(P):
         assert n in P.SIGNATURES, n
 
 
+def test_binding_constants_match_the_header(P):
+    """Every PS_* constant the header defines has the same value in the
+    binding (the binding restates them; a drift would pass wrong flags)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = dict(re.findall(r"#define\s+(PS_[A-Z0-9_]+)\s+(-?\d+)", src))
+    assert len(defs) >= 25
+    for name, value in defs.items():
+        assert hasattr(P, name), name
+        assert getattr(P, name) == int(value), (name, getattr(P, name), value)
+
+
 def test_version_and_status_strings(P):
     assert "sm_103a" in P.ps_version()
     assert P.ps_status_str(P.PS_OK) == "ok"
