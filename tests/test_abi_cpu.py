@@ -2,6 +2,7 @@
 include/pressure.h declares, and its host preprocessing (chunking, renumbering,
 incidence lists) satisfies the invariants the kernels rely on.  No device
 call is made here."""
+import ctypes as C
 import os
 import re
 import subprocess
@@ -49,6 +50,29 @@ def test_binding_constants_match_the_header(P):
     for name, value in defs.items():
         assert hasattr(P, name), name
         assert getattr(P, name) == int(value), (name, getattr(P, name), value)
+
+
+def test_struct_layouts_match_the_header(P, tmp_path):
+    """Size and field offsets of every struct the binding mirrors equal those a
+    C compiler gives the header's declarations (gcc, this host's ABI)."""
+    structs = [P.ps_mesh_opts, P.ps_solve_opts, P.ps_projection_opts, P.ps_solve_info, P.ps_mesh_stats,
+               P.ps_server_opts, P.ps_server_stats, P.ps_eos_opts]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pressure.h"', 'int main(void) {']
+    expect = []
+    for st in structs:
+        name = st.__name__
+        lines.append('  printf("%%s %%zu\\n", "%s", sizeof(%s));' % (name, name))
+        expect.append("%s %d" % (name, C.sizeof(st)))
+        for field, _ in st._fields_:
+            lines.append('  printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));' % (name, field, name, field))
+            expect.append("%s.%s %d" % (name, field, getattr(st, field).offset))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = subprocess.check_output([str(exe)]).decode().split("\n")
+    assert [g for g in got if g] == expect
 
 
 def test_version_and_status_strings(P):
