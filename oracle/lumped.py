@@ -32,8 +32,10 @@ steps.  Enthalpy per element H_e = (rho e(Pbar_e, rho_e) + Pbar_e) / rho_e.
 
 Parity status: pinned by ``tests/test_oracle_lumped.py`` (row sums of the C
 oracle's consistent mass for constant alpha, closed-form int phi_i on regular
-meshes, b = 0 reducing to one linear solve, a manufactured root recovered,
-quadratic convergence, the enthalpy and first guesses of the ideal gas).
+meshes, a hand-derived two-triangle operator in ``tests/golden/``, O(h^2)
+convergence of a manufactured solution, b = 0 reducing to one linear solve, a
+manufactured root recovered, quadratic convergence, the enthalpy of the ideal
+gas).
 """
 from __future__ import annotations
 

@@ -11,7 +11,9 @@ what the mathematics fixes, independently of the oracle's own formulas:
 * with b = 0 (ideal gas) one Newton step is the linear lumped solve and the
   next check sees F = 0;
 * Newton recovers a manufactured root, and its residuals fall quadratically;
-* the EOS enthalpy reduces to gamma/(gamma-1) Pbar/rho for b = 0.
+* the EOS enthalpy reduces to gamma/(gamma-1) Pbar/rho for b = 0;
+* the operator on two right triangles equals the hand-derived rows of
+  tests/golden/lumped_two_triangles.txt.
 """
 import math
 
@@ -185,3 +187,16 @@ def test_eos_projection_step_b0_is_the_lumped_picard_loop():
     assert out["steps"] == [1, 1]
     assert np.linalg.norm(out["dp"] - dp) <= 1e-11 * np.linalg.norm(dp)
     assert np.allclose(out["H"], H, rtol=1e-12)
+
+
+def test_lumped_operator_on_two_triangles_golden():
+    """The lumped operator on the unit square cut into two right triangles
+    against the hand-derived rows of tests/golden/lumped_two_triangles.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "lumped_two_triangles.txt")
+    rows = [list(map(float, ln.split()[1:])) for ln in open(path) if ln.startswith("row")]
+    want = np.array(rows)
+    coords, conn = S.square_mesh(1)
+    assert np.array_equal(conn, [[0, 1, 3], [0, 3, 2]])
+    A = L.LumpedMatrix(2, coords, conn, np.zeros(4, np.uint8), np.array([1.0, 2.0, 3.0, 4.0]), np.ones(2), 0.5)
+    assert np.allclose(A.A.toarray(), want, rtol=0, atol=1e-15)
