@@ -15,7 +15,7 @@ Lumped operator: A_L = diag(alpha_i m_i) + dt^2 K_beta on the free nodes,
 m_i = int phi_i = sum over the elements e around i of w_e, w_e = |T_e|/(d+1)
 (the alpha-weighted mass integral by vertex quadrature on every element).
 
-General EOS (reading, see the design notes): rho e(P, rho) = a P + b P^2/rho,
+General EOS (a reading: the paper names none): rho e(P, rho) = a P + b P^2/rho,
 the caloric equation of a thermally perfect gas with c_v linear in the
 temperature; b = 0 is the ideal gas with a = 1/(gamma-1).  Per Picard
 iteration (H and rho K frozen) the unknown is dP on the free nodes and

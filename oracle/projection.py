@@ -14,7 +14,7 @@ Section 3.3 produces: density rho, intermediate momentum W~~_u, intermediate
 total energy W~_E) and per node (pressure P^n, mass coefficient alpha, the
 paper's 1/(gamma - 1)); element order and node numbering are the caller's.
 
-Readings (also listed in the design notes): the boundary term
+Readings of the paper taken here: the boundary term
 -dt int_Gamma H W_u^{n+1}.eta z of the weak problem vanishes (closed walls,
 W_u.eta = 0 on the Neumann boundary; on Dirichlet faces z = 0); element
 values of the enthalpy use the vertex mean of the nodal pressure,
