@@ -24,7 +24,9 @@ H^{n+1,1} from P^n and (rho K)^{n+1,1} = |W~~_u|^2 / (2 rho).
 Parity status: pinned by ``tests/test_oracle_projection.py`` (partition of
 unity, closed-form nodal integrals on regular meshes, the discrete divergence
 theorem for P0 projections of linear fields, exact gradients of linear
-fields, a single Picard iteration against a direct solve).
+fields, a single Picard iteration against a direct solve, and the element
+values of the kinetic energy density and the enthalpy against hand-derived
+values in ``tests/golden/projection_element_values.txt``).
 """
 from __future__ import annotations
 

@@ -142,3 +142,29 @@ def test_one_picard_iteration_is_a_direct_solve():
                               gamma, dt, n_picard=2)
     assert np.allclose(out2["solves"][1]["H"], out["H"], rtol=1e-12)
     assert not np.allclose(out2["dp"], out["dp"], rtol=1e-6)
+
+
+def test_element_values_golden():
+    """Kinetic energy density and enthalpy of single elements against values
+    derived by hand (tests/golden/projection_element_values.txt): a dropped
+    1/2, a sum instead of a mean, or gamma/(gamma-1) inverted fails them."""
+    from conftest import golden
+    from oracle import lumped as LO
+    seen = set()
+    for row in golden("projection_element_values.txt"):
+        kind, vals = row[0], [float(v) for v in row[1:]]
+        expected = vals[-1]
+        if kind == "kinetic":
+            dim, rho, wu = int(vals[0]), vals[1], np.array(vals[2:-1])
+            assert wu.size == dim
+            got = PJ.kinetic(wu.reshape(1, dim), np.array([rho]), dim)[0]
+        elif kind == "enthalpy":
+            gamma, rho, p = vals[0], vals[1], np.array(vals[2:-1])
+            got = PJ.enthalpy(np.arange(p.size).reshape(1, -1), p, np.array([rho]), gamma)[0]
+        else:
+            assert kind == "enthalpy_eos"
+            a, b, rho, p = vals[0], vals[1], vals[2], np.array(vals[3:-1])
+            got = LO.enthalpy(np.arange(p.size).reshape(1, -1), p, np.array([rho]), a, b)[0]
+        assert abs(got - expected) <= 1e-14 * abs(expected), (row, got)
+        seen.add(kind)
+    assert seen == {"kinetic", "enthalpy", "enthalpy_eos"}
