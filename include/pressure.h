@@ -469,6 +469,21 @@ int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_e
                      const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
                      const ps_mesh_opts *opts, ps_mesh_stats *stats);
 
+/* ---- Jacobi preconditioner of a mesh (diagnostics) ----------------------
+ * Copy the inverse diagonal D^-1 that the Jacobi preconditioner applies, with
+ * D_ii = sum over the elements e around node i of (M^e_ii + dt2 K^e_ii) (the
+ * diagonal of the weak problem's matrix, Section 3.4; the mass term in the
+ * mesh's current form), to host memory in the caller's numbering.
+ *   precision  PS_F64: dinv_host is [n_nodes] double (the FP64 passes' copy);
+ *              PS_F32: [n_nodes] float (the FP32 inner iterations' copy, the
+ *              FP64 value rounded to nearest)
+ *   stream     the diagonal is read after the work queued on this stream
+ *              (coefficient updates of a projection step are stream-ordered)
+ * Dirichlet nodes hold 0 (the preconditioned residual is zero there); merged
+ * periodic vertices hold their unknown's value.  Synchronises the stream.
+ * Errors: PS_EINVAL, PS_ESTATE (coefficients not set), PS_ECUDA. */
+int ps_mesh_get_jacobi(const ps_mesh *mesh, int precision, void *dinv_host, void *stream);
+
 /* ---- kernel timing (diagnostics for roofline reports) -------------------
  * Launch one internal kernel of the solver `reps` times back to back on
  * `stream` between two CUDA events recorded on that stream, and report the

@@ -1228,6 +1228,21 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
 }
 
 // ---------------------------------------------------------------- debug hooks (host only)
+extern "C" int ps_mesh_get_jacobi(const ps_mesh *m, int precision, void *dinv_host, void *stream) {
+    if (!m || !dinv_host || (precision != PS_F32 && precision != PS_F64)) return PS_EINVAL;
+    if (!m->coeff_ok) return PS_ESTATE;
+    CK(cudaSetDevice(m->ctx->device));
+    CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    const PrepMesh &p = m->prep;
+    const size_t esz = precision == PS_F64 ? 8 : 4;
+    std::vector<unsigned char> d(p.n_dofs * esz);
+    const void *src = precision == PS_F64 ? (const void *)m->dev.dinv64 : (const void *)m->dev.dinv32;
+    CK(cudaMemcpy(d.data(), src, d.size(), cudaMemcpyDeviceToHost));
+    unsigned char *out = static_cast<unsigned char *>(dinv_host);
+    for (int64_t j = 0; j < p.n_nodes; ++j) std::memcpy(out + j * esz, d.data() + (size_t)p.new_of_old[j] * esz, esz);
+    return PS_OK;
+}
+
 extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,
                                 const int32_t *conn, const uint8_t *dirichlet, const int32_t *periodic,
                                 const ps_mesh_opts *opts, ps_mesh_stats *stats) {

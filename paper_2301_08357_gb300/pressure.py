@@ -140,6 +140,7 @@ SIGNATURES = {
     "ps_server_release": (C.c_int, [_vp, _i64]),
     "ps_server_get_stats": (C.c_int, [_vp, C.POINTER(ps_server_stats)]),
     "ps_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double)]),
+    "ps_mesh_get_jacobi": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "ps_debug_prepare": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, _vp, C.POINTER(ps_mesh_opts),
                                    C.POINTER(ps_mesh_stats)]),
 }
@@ -425,6 +426,16 @@ def ps_profile_kernel(mesh, which, reps=20, stream=None):
     ms = C.c_double()
     _check(_lib.ps_profile_kernel(mesh, int(which), int(reps), _stream(stream), C.byref(ms)), "ps_profile_kernel")
     return float(ms.value)
+
+
+def ps_mesh_get_jacobi(mesh, precision=PS_F64, stream=None):
+    """The Jacobi preconditioner's inverse diagonal, caller numbering (host
+    NumPy array, float64 or float32)."""
+    n = ps_mesh_get_stats(mesh).n_nodes
+    out = np.empty(n, dtype=np.float64 if precision == PS_F64 else np.float32)
+    _check(_lib.ps_mesh_get_jacobi(mesh, int(precision), out.ctypes.data_as(C.c_void_p), _stream(stream)),
+           "ps_mesh_get_jacobi")
+    return out
 
 
 def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, periodic=None):
