@@ -82,12 +82,17 @@ struct PatchRec {
 };
 
 // Group the elements of one chunk into star patches.  lc: [n][4] local vertex
-// ids.  Pivots are edges (3D) or vertices (2D); pivots are taken greedily by
-// the number of still unassigned elements around them (more first, ties by
-// pivot key), and the unassigned elements around a pivot are linked into
-// chains through their shared ring vertices, at most kPatchMax per chain.
-// Whatever is left becomes patches of one element.
-void build_patches(int dim, int n, const std::vector<std::array<int, 4>> &lc, std::vector<PatchRec> &out) {
+// ids; lx: [local node][dim] coordinates (3D only, may be null).  Pivots are
+// edges (3D) or vertices (2D); pivots are taken greedily by the number of
+// still unassigned elements around them (more first; among equal counts the
+// longer edge first, then by pivot key), and the unassigned elements around a
+// pivot are linked into chains through their shared ring vertices, at most
+// kPatchMax per chain.  Whatever is left becomes patches of one element.
+// Longer edges first: on Kuhn-type meshes the six tetrahedra of a cube cell
+// share its main diagonal, the longest edge of the cell, so every cell
+// becomes one closed star of six.
+void build_patches(int dim, int n, const std::vector<std::array<int, 4>> &lc, std::vector<PatchRec> &out,
+                   const double *lx) {
     const int nv = dim + 1;
     out.clear();
     std::vector<char> used(n, 0);
@@ -113,10 +118,29 @@ void build_patches(int dim, int n, const std::vector<std::array<int, 4>> &lc, st
     const size_t ng = gstart.size() - 1;
     int maxc = 0;
     for (size_t g = 0; g < ng; ++g) maxc = std::max(maxc, (int)(gstart[g + 1] - gstart[g]));
+    // visiting order of the pivots: longer edges first (3D with coordinates),
+    // ties by pivot key
+    std::vector<size_t> gorder(ng);
+    for (size_t g = 0; g < ng; ++g) gorder[g] = g;
+    if (dim == 3 && lx) {
+        std::vector<double> len2(ng);
+        for (size_t g = 0; g < ng; ++g) {
+            const uint64_t key = inc[gstart[g]].first;
+            const int u = (int)(key >> 20), v = (int)(key & 0xfffff);
+            double s2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double d = lx[(size_t)u * 3 + k] - lx[(size_t)v * 3 + k];
+                s2 += d * d;
+            }
+            len2[g] = s2;
+        }
+        std::stable_sort(gorder.begin(), gorder.end(), [&](size_t x, size_t y) { return len2[x] > len2[y]; });
+    }
     std::vector<int> cand;
     std::vector<std::array<int, 2>> rp;   // ring pair of each candidate
     for (int c = maxc; c >= 2; --c) {
-        for (size_t g = 0; g < ng; ++g) {
+        for (size_t gi = 0; gi < ng; ++gi) {
+            const size_t g = gorder[gi];
             cand.clear();
             for (size_t k = gstart[g]; k < gstart[g + 1]; ++k)
                 if (!used[inc[k].second]) cand.push_back(inc[k].second);
@@ -439,6 +463,7 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
     std::vector<int32_t> shr_cnt(m.n_shared + 1, 0);
     std::vector<std::array<int, 4>> lc;
     std::vector<PatchRec> patches;
+    std::vector<double> lxyz;                        // the chunk's local node coordinates (3D)
     for (int c = 0; c < nc; ++c) {
         ChunkDesc &cd = m.chunks[c];
         const int n_el = (int)(chunk_begin[c + 1] - chunk_begin[c]);
@@ -478,7 +503,14 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
             int32_t src = order[chunk_begin[c] + e];
             for (int a = 0; a < nv; ++a) lc[e][a] = loc_of_vtx[conn[(int64_t)src * nv + a]];
         }
-        build_patches(dim, n_el, lc, patches);
+        if (dim == 3) {
+            lxyz.resize((size_t)cd.n_loc * 3);
+            for (int32_t l = 0; l < cd.n_loc; ++l) {
+                const int32_t vtx = l < cd.n_int ? m.old_of_new[cd.int_begin + l] : shl[l - cd.n_int];
+                for (int k = 0; k < 3; ++k) lxyz[(size_t)l * 3 + k] = coords[(int64_t)vtx * 3 + k];
+            }
+        }
+        build_patches(dim, n_el, lc, patches, dim == 3 ? lxyz.data() : nullptr);
         balance_patches(patches);
         const int np = (int)patches.size();
         if (np > kMaxChunkPatches) return "internal: too many patches in a chunk";
