@@ -2,20 +2,30 @@
 """Benchmark of the pressure solve: DOF-iterations/s of matrix-free (P)CG on the
 P1 pressure system A = M_alpha + dt^2 K_beta (Section 3.4), one GB300.
 
-Default workload: the 3D 64^3 Kuhn-cube system (1,572,864 tetrahedra,
-274,625 nodes, 270,400 free), alpha from 8 seeded Fourier modes, beta
-lognormal(0, 0.5), dt^2 = 1e-2, Dirichlet x = 0, b ~ N(0,1), x0 = 0.  One step
-= one solve to a true FP64 relative residual of 1e-10 through the C ABI
-(FP32 Jacobi-PCG inside FP64 defect correction by default; --mode fp64 for the
-plain FP64 PCG).  value = free nodes x (inner + outer iterations) / device
-time, inputs resident in HBM, L2 flushed (256 MB write) between steps.
+Default (no flags): the headline line on the stiff 3D case -- the unit cube
+160^3 cut into 24,576,000 Kuhn tetrahedra (4,173,281 nodes), alpha from 8
+seeded Fourier modes x 1e-4, beta lognormal(0, 1) with a 100x spherical
+inclusion, dt^2 = 1e-2, Dirichlet x = 0, b = A x* formed by the FP64 oracle's
+assembled matrix, warm start x0 = x*(1 + 0.01 xi).  One step = one solve to a
+true FP64 relative residual of 1e-10 through the C ABI (FP32 Jacobi-PCG inside
+FP64 defect correction).  value = free nodes x (inner + outer iterations) /
+device time, inputs resident in HBM (0.64 GB per operator pass, five times
+the L2) and a 256 MB write between steps.  The same line carries the error
+against the oracle's solution, the time at the tightened tolerance that
+meets the 1e-9 error gate, the roofline of the dominant kernels, the oracle
+timed on the host cores, an end-to-end figure with host buffers, and three
+sub-objects: "batched" (256 meshes in one batched solve), "served" (a
+continuous-batching stream of 64 cases x 20 time steps with per-size-bucket
+latency, against the same requests solved one at a time in plain FP64) and
+"c2" (the 64^3 single solve).
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own
 replica of the workload (independent systems, no collective on the data
 path: weak scaling); value is the sum over ranks / the max time over ranks.
 
 --impl reference times the FP64 CPU oracle (CSR assembly excluded, textbook
-Jacobi-PCG with OpenMP sparse products) on the same system, same metric.
+Jacobi-PCG with OpenMP sparse products) on the same system, same metric:
+each step a bounded sample of Jacobi-PCG iterations.
 """
 from __future__ import annotations
 
@@ -36,18 +46,12 @@ if ROOT not in sys.path:
 METRIC = "pressure CG DOF-iters/s + HBM GB/s; solves/s, p50/p99 ms at 1e-10 rel residual"
 UNIT = "DOF-iter/s"
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the current kernel source (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by (kernel, workload).  An entry is
-# removed whenever the kernel changes; missing means not captured (null).
-TRAFFIC = {
-    # C2 capture (cold cache: ncu flushes the caches before it)
-    ("k_cg2_chunks<3,float>", "c2_3d_kuhn_64^3_tets1572864_nodes274625"): 37314560,
-    # C3 capture
-    ("k_cg2_chunks<3,float>", "c3_3d_160"): 561702912,
-    # 32^3 capture of the fused pass (cold cache)
-    ("k_cg1_chunks<3>", "c2_3d_kuhn_32^3_tets196608_nodes35937"): 5914624,
-}
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel source as it
+# stands, keyed by (kernel, workload), with the capture it came from.  An
+# entry is removed whenever the kernel changes; missing means not captured
+# (the line then reports null).
+TRAFFIC = {}
 
 
 def parse():
@@ -57,7 +61,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--n", type=int, default=64, help="cells per side of the Kuhn cube")
+    ap.add_argument("--n", type=int, default=0, help="cells per side of the Kuhn cube (0 = 160 for c3, 64 else)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -68,9 +72,14 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "fused"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "projection", "periodic", "eos"],
-                    help="c2 (default) = the timed 64^3 single solve; c1/c3 single solves; "
-                         "c4 = 256-mesh batch; c5 = served Poisson stream")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "c1", "c2", "c3", "c4", "c5", "projection", "periodic", "eos"],
+                    help="headline (default) = the c3 line with batched, served and c2 sub-objects; "
+                         "c1/c2/c3 single solves alone; c4 = 256-mesh batch; c5 = served stream with a "
+                         "Poisson rate sweep")
+    ap.add_argument("--no-sub", action="store_true", help="headline: the c3 line without sub-objects")
+    ap.add_argument("--tight-tol", type=float, default=1e-13,
+                    help="c3: tolerance of the solves that meet the 1e-9 error gate")
     ap.add_argument("--meshes", type=int, default=256, help="c4: meshes in the batch")
     ap.add_argument("--cases", type=int, default=64, help="c5: simulated cases")
     ap.add_argument("--case-steps", type=int, default=20, help="c5: time steps per case")
@@ -210,23 +219,66 @@ def cpu_model():
     return "unknown"
 
 
+C3_ITERS_PER_CALL = 25   # oracle Jacobi-PCG iterations per timed call (CPU samples)
+
+
+def c3_name(case):
+    return "c3_3d_kuhn_%d^3_stiff_warm_tets%d_nodes%d" % (case.n, case.n_elems, case.n_nodes)
+
+
+def headline_config(case, ws=1):
+    """The workload of the headline line, shared by both arms (same keys and values)."""
+    return {"workload": c3_name(case), "n_free": int(case.n_free), "n_elems": int(case.n_elems),
+            "mode": "mixed (FP32 Jacobi-PCG inside FP64 defect correction)", "precond": "jacobi", "tol": 1e-10,
+            "b": "A x* formed by the FP64 oracle's assembled matrix", "x0": "x* (1 + 0.01 xi)",
+            "l2": "inputs larger than L2 (0.64 GB per operator pass) and a 256 MB write between steps",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
+def oracle_pcg_sample(A, b, x0, seconds=0.0, calls=None):
+    """The oracle's Jacobi-PCG on a bounded sample of the workload: calls of
+    C3_ITERS_PER_CALL iterations from x0 (each starting from the true
+    residual), repeated until `seconds` have passed (or `calls` times)."""
+    import oracle
+    iters, t_used, n, times = 0, 0.0, 0, []
+    while (calls is None and (n == 0 or t_used < seconds)) or (calls is not None and n < calls):
+        t0 = time.perf_counter()
+        _, _, it, _ = A.cg(b, x0_full=x0, precond=1, tol=1e-30, max_it=C3_ITERS_PER_CALL, max_restarts=0)
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        t_used += dt
+        iters += it
+        n += 1
+    return {"value": A.n_free * iters / t_used, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d call(s) of %d Jacobi-PCG iterations of the oracle on the full system from x0 "
+                      "(CSR assembly excluded), %.1f s" % (n, C3_ITERS_PER_CALL, t_used),
+            "iters": iters, "seconds": t_used, "times": times}
+
+
 def run_reference(args):
+    """The oracle on the headline workload, timed on the host cores: every
+    step is one bounded sample (C3_ITERS_PER_CALL Jacobi-PCG iterations on
+    the full system from x0).  Rank 0 only under torchrun."""
     ws, rank, local = dist_setup()
     if rank != 0:
         return
+    import oracle
     from paper_2301_08357_gb300 import synthetic as S
-    case = S.make_c2(args.n)
-    for _ in range(max(args.warmup, 0) and 1):
-        cpu_baseline(case, 0.0, steps=1)
-    cb = cpu_baseline(case, 0.0, steps=max(args.steps, 1))
-    ms = 1e3 * cb["seconds"] / cb["solves"]
+    case = S.make_c3(args.n or 160)
+    t0 = time.perf_counter()
+    A = oracle.PressureMatrix.from_case(case)
+    t_asm = time.perf_counter() - t0
+    b = A.apply(case.extra["xstar"])
+    if max(args.warmup, 0):
+        oracle_pcg_sample(A, b, case.x0, calls=1)
+    cb = oracle_pcg_sample(A, b, case.x0, calls=max(args.steps, 1))
+    ms = 1e3 * cb["seconds"] / max(args.steps, 1)
     out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args.n), "n_free": case.n_free, "solver": "oracle Jacobi-PCG",
-                      "l2": "n/a (CPU)"},
+           "config": headline_config(case),
            "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                            "sample": cb["sample"]},
+                            "sample": cb["sample"] + "; each step is one call", "assembly_s": t_asm},
            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -291,13 +343,22 @@ def kernel_roofline(P, m, stats, mode, fused, stream, workload, lumped=False):
     if mode == P.PS_MODE_FP64:
         flops = fp64_flops(stats, lumped, cg=True)
         tf = flops / (kern_ms / 1e3) / 1e12
+        tr = TRAFFIC.get((kname, workload))
         return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((kname, workload)), "kernel": kname,
+                "frac": tf / FP64_PEAK_TFLOPS, "traffic": tr["bytes"] if tr else None, "kernel": kname,
                 "kernel_ms": kern_ms, "flops_per_launch": flops, "hbm_frac": achieved / peak,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": "nominal FP64 (2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
                 "other_kernels_ms": kern_other, "fp64_resid": fp64_resid, "chunks": stats.n_chunks}
+    tr = TRAFFIC.get((kname, workload))
+    upd_ms = kern_other["update_f32"]
+    upd_bytes = 28 * N   # x, r, p, q, D^-1 read and x, r written, FP32
+    update = {"kernel": "k_cg2_update<float>", "bound": "hbm", "unit": "GB/s", "kernel_ms": upd_ms,
+              "alg_bytes_per_launch": upd_bytes, "achieved": upd_bytes / (upd_ms / 1e3) / 1e9,
+              "peak": peak, "frac": upd_bytes / (upd_ms / 1e3) / 1e9 / peak}
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get((kname, workload)), "kernel": kname,
+            "traffic": tr["bytes"] if tr else None,
+            "traffic_source": tr["source"] if tr else "not captured for the kernel as it stands",
+            "kernel": kname, "update": update,
             "kernel_ms": kern_ms, "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
             "other_kernels_ms": kern_other, "fp64_resid": fp64_resid, "chunks": stats.n_chunks,
             "shared_node_frac": stats.n_shared / stats.n_nodes,
@@ -324,6 +385,7 @@ def run_ours(args):
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
 
+    args.n = args.n or 64
     case = S.make_c2(args.n)
     ctx = P.ps_ctx_create(local)
     m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
@@ -461,7 +523,8 @@ def run_single(args, which):
         build()
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
-    case = S.make_c1() if which == "c1" else (S.make_c3() if which == "c3" else S.make_periodic_case(3, args.n))
+    case = S.make_c1() if which == "c1" else (S.make_c3(args.n or 160) if which == "c3"
+                                              else S.make_periodic_case(3, args.n or 64))
     mode = P.PS_MODE_FP64 if (which == "c1" or args.mode == "fp64") else P.PS_MODE_MIXED
     ctx = P.ps_ctx_create(0)
     m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
@@ -539,16 +602,10 @@ def batch_chunk(args, autotune, P, ctx, cases):
     return res["chunk_elems"], {"sample_meshes": len(sample), "table": res["table"]}
 
 
-def run_batch(args):
-    """c4: 256 independent meshes (half 2D, half 3D, 2k-200k nodes) in one batched solve."""
-    import contextlib
-    import torch
-    from __graft_entry__ import build
-    with contextlib.redirect_stdout(sys.stderr):
-        build()
-    from paper_2301_08357_gb300 import pressure as P
-    from paper_2301_08357_gb300 import synthetic as S
-    from paper_2301_08357_gb300 import autotune
+def bench_batch(args, P, S, autotune, torch):
+    """c4: 256 independent meshes (half 2D triangle squares, half 3D Kuhn cubes,
+    2k-200k nodes) in one batched solve per step.  Returns the measurement as
+    a dict (solves/s, batch-time percentiles over the steps, accuracy, clocks)."""
     ctx = P.ps_ctx_create(0)
     meshes, bs, xs, n_free = [], [], [], []
     t0 = time.perf_counter()
@@ -569,7 +626,11 @@ def run_batch(args):
         for x in xs:
             x.zero_()
         P.ps_batch_solve(meshes, bs, xs, opts, stream)
-    times, dof_iters = [], 0
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    if not args.no_clocks:
+        clocks.start()
+    times, dof_iters, launches = [], 0, 0
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         for x in xs:
@@ -581,29 +642,40 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-        assert st == P.PS_OK, st
+        if st != P.PS_OK:
+            raise RuntimeError("batched solve failed: %s" % P.ps_status_str(st))
         dof_iters += sum(nf * (inf.iters_inner + inf.iters_outer) for nf, inf in zip(n_free, infos))
+        launches += max(inf.kernel_launches for inf in infos)
+    clk = clocks.stop() if not args.no_clocks else None
     tot = float(np.sum(times))
-    out = {"metric": METRIC, "value": dof_iters / (tot / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": max(args.warmup, 3), "ms_per_step": tot / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": "c4_batch_%d_meshes" % args.meshes, "n_free_total": int(sum(n_free)),
-                      "max_rel_res": max(inf.rel_res for inf in infos),
-                      "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
-                      "iters_inner_max": int(max(inf.iters_inner for inf in infos)),
-                      "chunk_elems": chunk, "chunk_tuning": tune,
-                      "setup_s": setup_s, "l2": "flushed between steps (256 MB write)"},
-           "solves_per_s": 1e3 * args.meshes * args.steps / tot}
-    print(json.dumps(out))
+    # the oracle's residual of every 32nd mesh's solution (assembled on the host)
+    check = None
+    if not args.no_cpu_baseline:
+        import oracle
+        worst = 0.0
+        for i in range(0, len(cases), 32):
+            A = oracle.PressureMatrix.from_case(cases[i])
+            worst = max(worst, A.residual(cases[i].b, xs[i].cpu().numpy()))
+        check = {"meshes": len(range(0, len(cases), 32)), "max_rel_res_oracle": worst,
+                 "note": "every 32nd mesh: the FP64 oracle's relative residual of the GPU solution"}
+    out = {"workload": "c4_batch_%d_meshes" % args.meshes, "value": dof_iters / (tot / 1e3), "unit": UNIT,
+           "steps": args.steps, "ms_per_batch": tot / args.steps, "p50_ms": _pctl(times, 50),
+           "p99_ms": _pctl(times, 99), "solves_per_s": 1e3 * args.meshes * args.steps / tot,
+           "n_free_total": int(sum(n_free)), "max_rel_res": max(inf.rel_res for inf in infos),
+           "oracle_check": check,
+           "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
+           "iters_inner_max": int(max(inf.iters_inner for inf in infos)),
+           "chunk_elems": chunk, "chunk_tuning": tune, "setup_s": setup_s, "gpu_launches": launches,
+           "l2": "flushed between steps (256 MB write)", "clocks": clk}
     for m in meshes:
         P.ps_mesh_free(m)
     P.ps_ctx_destroy(ctx)
+    return out
 
 
-def run_served(args):
-    """c5: Poisson arrivals of time-step solves from simulated cases."""
+def run_batch(args):
+    """c4 alone: one JSON line."""
     import contextlib
-    import threading
     import torch
     from __graft_entry__ import build
     with contextlib.redirect_stdout(sys.stderr):
@@ -611,6 +683,37 @@ def run_served(args):
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
     from paper_2301_08357_gb300 import autotune
+    r = bench_batch(args, P, S, autotune, torch)
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_batch"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": r["workload"], "l2": r["l2"]}, "batched": r,
+           "solves_per_s": r["solves_per_s"], "clocks": r["clocks"]}
+    print(json.dumps(out))
+
+
+SIZE_BUCKETS = ((0, 5e4, "< 50k nodes"), (5e4, 5e5, "50k-500k nodes"), (5e5, 1e12, ">= 500k nodes"))
+
+
+def _buckets(lat_s, sizes):
+    """p50/p99 latency (ms) per case-size bucket."""
+    out = []
+    lat_s, sizes = np.asarray(lat_s), np.asarray(sizes)
+    for lo, hi, name in SIZE_BUCKETS:
+        sel = (sizes >= lo) & (sizes < hi)
+        if sel.any():
+            out.append({"bucket": name, "requests": int(sel.sum()), "p50_ms": 1e3 * _pctl(lat_s[sel], 50),
+                        "p99_ms": 1e3 * _pctl(lat_s[sel], 99)})
+    return out
+
+
+def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, budget_steps=None):
+    """c5: time-step solves from simulated cases through the serving loop
+    (continuous batching), closed loop with every case in flight; optionally
+    Poisson arrivals at multiples of the closed-loop rate; the closed loop
+    under an HBM budget that admits about a quarter of the workspaces; and the
+    same requests solved one at a time (plain FP64 PCG and the mixed
+    single-solve engine).  Returns a dict."""
     ctx = P.ps_ctx_create(0)
     meshes = []
     cases = [S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
@@ -621,30 +724,51 @@ def run_served(args):
         P.ps_coeff_set(m, cs.alpha, cs.beta, cs.dt2)
         meshes.append(m)
     nodes_total = sum(c.n_nodes for c in cases)
+    sizes = [c.n_nodes for c in cases]
+    n_check = 4 if not args.no_cpu_baseline else 0
+    check_cases = sorted(range(len(cases)), key=lambda c: sizes[c])[:n_check]   # the smallest cases
 
-    def one_run(rate, budget=0):
+    def one_run(rate, budget=0, steps=None):
         """rate None = closed loop (each case submits its next step when the last completes);
         budget: the server's HBM cap on in-flight solver workspaces (0 = the context's)."""
+        steps = steps or args.case_steps
         srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32, hbm_budget_bytes=budget)
         ids = [P.ps_server_add_case(srv, m) for m in meshes]
         state = [(c.beta.copy(), c.b.copy()) for c in cases]
-        lat, qwait, done_iters = [], [], 0
+        lat, qwait, req_size, done_iters, worst = [], [], [], 0, 0.0
+        last_x = {}
         rng = np.random.default_rng(7)
+        clocks = Clocks(0)
+        if not args.no_clocks:
+            clocks.start()
         t_start = time.perf_counter()
-        order = [(k, ci) for k in range(args.case_steps) for ci in range(len(cases))]
+        order = [(k, ci) for k in range(steps) for ci in range(len(cases))]
         pending = {}
+
+        def finish(t, ci, k):
+            want_x = ci in check_cases and k + 1 == steps
+            xo = np.empty(cases[ci].n_nodes) if want_x else None
+            st, info = P.ps_solve_wait(srv, t, 600.0, x_out=xo)
+            P.ps_server_release(srv, t)
+            if st != P.PS_OK:
+                raise RuntimeError("served solve failed: %s" % P.ps_status_str(st))
+            lat.append(info.seconds)
+            qwait.append(info.queue_seconds)
+            req_size.append(sizes[ci])
+            if want_x:
+                last_x[ci] = (xo, state[ci][0].copy(), state[ci][1].copy())
+            return info
+
         if rate is None:
             for ci in range(len(cases)):
                 pending[P.ps_solve_submit(srv, ids[ci], state[ci][1])] = (ci, 0)
             while pending:
                 t = next(iter(pending))
                 ci, k = pending.pop(t)
-                st, info = P.ps_solve_wait(srv, t, 600.0)
-                P.ps_server_release(srv, t)
-                lat.append(info.seconds)
-                qwait.append(info.queue_seconds)
+                info = finish(t, ci, k)
+                worst = max(worst, info.rel_res)
                 done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
-                if k + 1 < args.case_steps:
+                if k + 1 < steps:
                     beta, b = S.served_step_drift(cases[ci], *state[ci])
                     state[ci] = (beta, b)
                     pending[P.ps_solve_submit(srv, ids[ci], b, beta)] = (ci, k + 1)
@@ -659,31 +783,44 @@ def run_served(args):
                 beta = state[ci][0] if k > 0 else None
                 pending[P.ps_solve_submit(srv, ids[ci], state[ci][1], beta)] = (ci, k)
             for t, (ci, k) in list(pending.items()):
-                st, info = P.ps_solve_wait(srv, t, 600.0)
-                P.ps_server_release(srv, t)
-                lat.append(info.seconds)
-                qwait.append(info.queue_seconds)
+                info = finish(t, ci, k)
+                worst = max(worst, info.rel_res)
                 done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
         wall = time.perf_counter() - t_start
+        clk = clocks.stop() if not args.no_clocks else None
         stats = P.ps_server_get_stats(srv).as_dict()
         P.ps_server_destroy(srv)
+        # the oracle's residual of the last step of the smallest cases, with that step's beta and b
+        ocheck = None
+        if last_x:
+            import oracle
+            ow = 0.0
+            for ci, (xo, beta, b) in last_x.items():
+                A = oracle.PressureMatrix.from_case(cases[ci], beta=beta)
+                ow = max(ow, A.residual(b, xo))
+            ocheck = {"cases": len(last_x), "max_rel_res_oracle": ow,
+                      "note": "last step of the %d smallest cases, recomputed by the FP64 oracle" % len(last_x)}
         n = len(lat)
-        return {"rate": rate, "solves": n, "wall_s": wall, "solves_per_s": n / wall,
+        return {"rate": rate, "solves": n, "steps_per_case": steps, "wall_s": wall, "solves_per_s": n / wall,
                 "dof_iters_per_s": done_iters / wall, "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99),
-                "queue_p50_ms": 1e3 * _pctl(qwait, 50), "peak_in_flight": stats["peak_in_flight"],
-                "epochs": stats["epochs"]}
+                "per_bucket": _buckets(lat, req_size), "queue_p50_ms": 1e3 * _pctl(qwait, 50),
+                "peak_in_flight": stats["peak_in_flight"], "epochs": stats["epochs"], "max_rel_res": worst,
+                "oracle_check": ocheck, "clocks": clk}
 
-    def single_run(mode):
-        """Requests of the same shape (every case, every step, its drift continuing
-        the case's seeded stream) solved one at a time through ps_pressure_solve
-        (plain FP64 PCG or the mixed single-solve engine), each case warm-starting
-        from its previous pressure; returns solves/s and latency percentiles."""
+    def single_run(mode, steps):
+        """The same kind of requests (every case, `steps` steps, its drift
+        continuing the case's seeded stream) solved one at a time through
+        ps_pressure_solve (plain FP64 PCG or the mixed single-solve engine),
+        each case warm-starting from its previous pressure."""
         opts = P.make_opts(mode=mode, tol=1e-10)
-        lat, done_iters, worst = [], 0, 0.0
+        lat, req_size, done_iters, worst = [], [], 0, 0.0
         xs = [torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda") for c in cases]
         state = [(c.beta.copy(), c.b.copy()) for c in cases]
+        clocks = Clocks(0)
+        if not args.no_clocks:
+            clocks.start()
         t_start = time.perf_counter()
-        for k in range(args.case_steps):
+        for k in range(steps):
             for ci, c in enumerate(cases):
                 if k > 0:
                     state[ci] = S.served_step_drift(c, *state[ci])
@@ -693,38 +830,289 @@ def run_served(args):
                 st, info = P.ps_pressure_solve(meshes[ci], b, xs[ci], opts)
                 torch.cuda.synchronize()
                 lat.append(time.perf_counter() - t0)
+                req_size.append(sizes[ci])
                 worst = max(worst, info.rel_res)
                 done_iters += c.n_free * (info.iters_inner + info.iters_outer)
         wall = time.perf_counter() - t_start
+        clk = clocks.stop() if not args.no_clocks else None
         for ci, c in enumerate(cases):          # restore the case coefficients
             P.ps_coeff_set_beta(meshes[ci], c.beta)
-        return {"mode": "fp64" if mode == P.PS_MODE_FP64 else "mixed", "solves": len(lat), "wall_s": wall,
-                "solves_per_s": len(lat) / wall, "dof_iters_per_s": done_iters / wall,
-                "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99), "max_rel_res": worst}
+        return {"mode": "fp64" if mode == P.PS_MODE_FP64 else "mixed", "solves": len(lat), "steps_per_case": steps,
+                "wall_s": wall, "solves_per_s": len(lat) / wall, "dof_iters_per_s": done_iters / wall,
+                "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99),
+                "per_bucket": _buckets(lat, req_size), "max_rel_res": worst, "clocks": clk}
 
     sat = one_run(None)
     runs = [sat]
-    for f in [float(v) for v in args.rates.split(",") if v]:
+    for f in (rates or []):
         runs.append(dict(one_run(f * sat["solves_per_s"]), rate_x_sat=f))
     # closed loop under an HBM budget that admits about a quarter of the cases'
     # workspaces at once (never less than the largest): admission queues requests
     ws_bytes = [P.ps_mesh_get_stats(m).solve_bytes for m in meshes]
     budget = int(max(max(ws_bytes), sum(ws_bytes) // 4))
-    runs.append(dict(one_run(None, budget), hbm_budget_bytes=budget, workspace_bytes_total=int(sum(ws_bytes))))
-    singles = [single_run(P.PS_MODE_FP64), single_run(P.PS_MODE_MIXED)]
-    out = {"metric": METRIC, "value": sat["dof_iters_per_s"], "unit": UNIT, "n_gpus": 1,
-           "steps": args.case_steps, "warmup": 0, "ms_per_step": 1e3 / sat["solves_per_s"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-           "data": "synthetic",
-           "config": {"workload": "c5_served_%d_cases_x_%d_steps" % (args.cases, args.case_steps),
-                      "nodes_total": nodes_total, "chunk_elems": chunk, "chunk_tuning": tune},
+    runs.append(dict(one_run(None, budget, steps=budget_steps), hbm_budget_bytes=budget,
+                     workspace_bytes_total=int(sum(ws_bytes))))
+    s_steps = single_steps or args.case_steps
+    singles = [single_run(P.PS_MODE_FP64, s_steps), single_run(P.PS_MODE_MIXED, s_steps)]
+    out = {"workload": "c5_served_%d_cases_x_%d_steps" % (args.cases, args.case_steps),
+           "value": sat["dof_iters_per_s"], "unit": UNIT, "nodes_total": nodes_total,
+           "case_nodes_min_max": [int(min(sizes)), int(max(sizes))],
            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+           "per_bucket": sat["per_bucket"], "max_rel_res": sat["max_rel_res"], "oracle_check": sat["oracle_check"],
            "served_vs_fp64_single_solves_per_s": sat["solves_per_s"] / singles[0]["solves_per_s"],
-           "runs": runs, "single_solves": singles}
-    print(json.dumps(out))
+           "chunk_elems": chunk, "chunk_tuning": tune, "runs": runs, "single_solves": singles,
+           "clocks": sat["clocks"]}
     for m in meshes:
         P.ps_mesh_free(m)
     P.ps_ctx_destroy(ctx)
+    return out
+
+
+def run_served(args):
+    """c5 alone (with the Poisson rate sweep): one JSON line."""
+    import contextlib
+    import torch
+    from __graft_entry__ import build
+    with contextlib.redirect_stdout(sys.stderr):
+        build()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    from paper_2301_08357_gb300 import autotune
+    rates = [float(v) for v in args.rates.split(",") if v]
+    r = bench_served(args, P, S, autotune, torch, rates=rates)
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.case_steps,
+           "warmup": 0, "ms_per_step": 1e3 / r["solves_per_s"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": {"workload": r["workload"]},
+           "served": r, "solves_per_s": r["solves_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+           "clocks": r["clocks"]}
+    print(json.dumps(out))
+
+
+def bench_c2_sub(args, P, S, torch, steps):
+    """The 64^3 single solve (mixed, x0 = 0), as a sub-object of the headline."""
+    case = S.make_c2(64)
+    ctx = P.ps_ctx_create(0)
+    m = P.ps_mesh_upload(ctx, 3, case.coords, case.conn, case.dirichlet)
+    P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+    stream = torch.cuda.current_stream()
+    opts = P.make_opts(mode=P.PS_MODE_MIXED, tol=1e-10)
+    b = torch.as_tensor(case.b, device="cuda")
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        x.zero_()
+        P.ps_pressure_solve(m, b, x, opts, stream)
+    times, iters = [], 0
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info = P.ps_pressure_solve(m, b, x, opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters += info.iters_inner + info.iters_outer
+    stats = P.ps_mesh_get_stats(m)
+    k1 = P.ps_profile_kernel(m, P.PS_KERNEL_CG1_F32 if case.n_nodes <= 200000 else P.PS_KERNEL_CG_F32, reps=50,
+                             stream=stream)
+    tot = float(np.sum(times))
+    out = {"workload": workload_name(64), "value": case.n_free * iters / (tot / 1e3), "unit": UNIT,
+           "ms_per_solve": tot / steps, "p50_ms": _pctl(times, 50), "iters_per_solve": iters // steps,
+           "rel_res": info.rel_res, "operator_pass_ms": k1, "chunks": stats.n_chunks,
+           "note": "the 64^3 system (41 MB per operator pass) is L2-resident between iterations"}
+    P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+    return out
+
+
+def run_headline(args):
+    """The default line: the stiff 160^3 solve (mixed precision, warm start,
+    b = A x* from the oracle), with the batched, served and c2 sub-objects."""
+    import contextlib
+    import torch
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+    if rank == 0 or ws == 1:
+        with contextlib.redirect_stdout(sys.stderr):   # keep stdout to the one JSON line
+            build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2301_08357_gb300 import pressure as P
+    from paper_2301_08357_gb300 import synthetic as S
+    from paper_2301_08357_gb300 import autotune
+
+    case = S.make_c3(args.n or 160)
+    ctx = P.ps_ctx_create(local)
+    m = P.ps_mesh_upload(ctx, 3, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
+                         pipeline=args.pipeline)
+    P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+    stats = P.ps_mesh_get_stats(m)
+    stream = torch.cuda.current_stream()
+    xs_h = case.extra["xstar"]
+    use_oracle = ws == 1 and not args.no_cpu_baseline
+    A, t_asm = None, None
+    if use_oracle:
+        # the oracle's b = A x* (so that x* is the solution of the oracle's system)
+        import oracle
+        t0 = time.perf_counter()
+        A = oracle.PressureMatrix.from_case(case)
+        t_asm = time.perf_counter() - t0
+        b_h = A.apply(xs_h)
+        b = torch.as_tensor(b_h, device="cuda")
+    else:
+        # replicas under torchrun: b from the library's FP64 operator on every rank
+        xs_d = torch.as_tensor(xs_h, device="cuda")
+        b = torch.empty_like(xs_d)
+        P.ps_pressure_apply(m, xs_d, b, P.PS_F64, stream)
+        torch.cuda.synchronize()
+        b_h = b.cpu().numpy()
+        del xs_d
+    engine = {"auto": P.PS_ENGINE_AUTO, "graph": P.PS_ENGINE_GRAPH, "persistent": P.PS_ENGINE_PERSISTENT,
+              "fused": P.PS_ENGINE_FUSED}[args.engine]
+    opts = P.make_opts(mode=P.PS_MODE_MIXED, tol=1e-10, engine=engine)
+    x0 = torch.as_tensor(case.x0, device="cuda")
+    x = x0.clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def solve(o):
+        x.copy_(x0)
+        st, info = P.ps_pressure_solve(m, b, x, o, stream)
+        if st != P.PS_OK:
+            raise RuntimeError("solve failed: %s" % P.ps_status_str(st))
+        return info
+
+    for _ in range(max(args.warmup, 3)):
+        solve(opts)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if not args.no_clocks:
+        clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters, launches = 0, 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)          # L2 flush between steps (not timed)
+        x.copy_(x0)
+        ev[k][0].record(stream)
+        st, info = P.ps_pressure_solve(m, b, x, opts, stream)
+        ev[k][1].record(stream)
+        if st != P.PS_OK:
+            raise RuntimeError("solve failed: %s" % P.ps_status_str(st))
+        iters += info.iters_inner + info.iters_outer
+        launches += info.kernel_launches
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if not args.no_clocks else None
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    total_ms = float(np.sum(step_ms))
+    last = info
+    x_h = x.cpu().numpy()
+    t_max, tot_dof = aggregate(total_ms, case.n_free * iters, device="cuda")
+    value = tot_dof / (t_max / 1e3)
+    nx = np.linalg.norm(xs_h)
+    accuracy = {"rel_res_gpu": last.rel_res,
+                "rel_res_oracle": A.residual(b_h, x_h) if A is not None else None,
+                "rel_err_vs_oracle": float(np.linalg.norm(x_h - xs_h) / nx) if A is not None else None,
+                "rel_err_vs_xstar": float(np.linalg.norm(x_h - xs_h) / nx),
+                "gates": "residual <= 1e-10 is the stop test; the error <= 1e-9 gate needs the tightened "
+                         "tolerance on this stiff system (error <= kappa x residual), see 'tight'"}
+    # the tolerance that meets both gates
+    tight_opts = P.make_opts(mode=P.PS_MODE_MIXED, tol=args.tight_tol, max_outer=16, engine=engine)
+    t_ms, t_it = [], 0
+    for k in range(3):
+        flush.fill_(k & 0xff)
+        x.copy_(x0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, ti = P.ps_pressure_solve(m, b, x, tight_opts, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms.append(e0.elapsed_time(e1))
+        t_it += ti.iters_inner + ti.iters_outer
+    xt = x.cpu().numpy()
+    tight = {"tol": args.tight_tol, "ms_per_solve": float(np.mean(t_ms)), "iters_per_solve": t_it // 3,
+             "status": P.ps_status_str(st), "rel_res_gpu": ti.rel_res,
+             "rel_res_oracle": A.residual(b_h, xt) if A is not None else None,
+             "rel_err_vs_oracle": float(np.linalg.norm(xt - xs_h) / nx) if A is not None else None,
+             "solves_per_s": 1e3 / float(np.mean(t_ms))}
+
+    # ---- end to end through the C ABI with host buffers (copies timed)
+    b_pin = torch.as_tensor(b_h).pin_memory()
+    x0_pin = torch.as_tensor(case.x0).pin_memory()
+    x_pin = torch.empty_like(x0_pin).pin_memory()
+    e2e_ms, e2e_it = [], 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.copy_(b_pin, non_blocking=True)
+        x.copy_(x0_pin, non_blocking=True)
+        st, ei = P.ps_pressure_solve(m, b, x, opts, stream)
+        x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e_it += ei.iters_inner + ei.iters_outer
+    e2e_val = case.n_free * e2e_it / (np.sum(e2e_ms) / 1e3)
+
+    # ---- roofline of the dominant kernels
+    roof = kernel_roofline(P, m, stats, P.PS_MODE_MIXED, False, stream, c3_name(case))
+    ipi = (last.iters_inner + last.iters_outer)
+    roof["in_solve_check"] = {
+        "solve_ms_per_iteration": total_ms / args.steps / max(ipi, 1),
+        "isolated_k1_plus_k2_ms": roof["kernel_ms"] + roof["update"]["kernel_ms"],
+        "note": "kernel_ms is the mean of back-to-back launches of the kernel alone; the solve's time per "
+                "iteration also holds the outer FP64 passes and graph launch gaps"}
+    P.ps_mesh_free(m)
+    P.ps_ctx_destroy(ctx)
+    del x, x0, b, flush
+    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and use_oracle:
+        import oracle
+        cb = oracle_pcg_sample(A, b_h, case.x0, args.cpu_seconds)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        n_all = oracle.num_threads()
+        oracle.set_threads(1)
+        try:
+            c1 = oracle_pcg_sample(A, b_h, case.x0, calls=1)
+        finally:
+            oracle.set_threads(n_all)
+        cpu["single_core"] = {"value": c1["value"], "unit": UNIT, "cores": 1, "sample": c1["sample"]}
+        cpu["cpu_model"] = cpu_model()
+        cpu["assembly_s"] = t_asm
+    del A
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": headline_config(case, ws),
+           "solves_per_s": 1e3 * args.steps / t_max * ws,
+           "p50_ms": _pctl(step_ms, 50), "p99_ms": _pctl(step_ms, 99),
+           "solve": {"iters_per_solve": ipi, "outer_per_solve": last.iters_outer, "chunks": stats.n_chunks},
+           "accuracy": accuracy, "tight": tight,
+           "roofline": roof, "cpu_baseline": cpu,
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * case.n_nodes,
+                   "d2h_bytes_per_step": 8 * case.n_nodes, "ms_per_step": float(np.mean(e2e_ms))},
+           "gpu_launches": launches, "clocks": clk}
+    if ws == 1 and not args.no_sub:
+        out["c2"] = bench_c2_sub(args, P, S, torch, args.steps)
+        out["batched"] = bench_batch(args, P, S, autotune, torch)
+        out["served"] = bench_served(args, P, S, autotune, torch)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_projection(args, eos=False):
@@ -743,6 +1131,7 @@ def run_projection(args, eos=False):
     from paper_2301_08357_gb300 import pressure as P
     from paper_2301_08357_gb300 import synthetic as S
     n_pic = 2
+    args.n = args.n or 64
     case = S.make_eos_case(3, args.n) if eos else S.make_projection_case(3, args.n)
     e = case.extra
     ctx = P.ps_ctx_create(0)
@@ -880,6 +1269,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "headline":
+        run_headline(args)
     elif args.workload in ("c1", "c3", "periodic"):
         run_single(args, args.workload)
     elif args.workload == "c4":

@@ -58,13 +58,17 @@ def test_reference_arm_rank0_prints_one_json_line(capsys, monkeypatch):
     import json
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    args = type("A", (), {"n": 6, "steps": 1, "warmup": 0, "gpus": 1})()
+    args = type("A", (), {"n": 6, "steps": 2, "warmup": 0, "gpus": 1})()
     bench.run_reference(args)
     out = capsys.readouterr().out.strip().splitlines()
     assert len(out) == 1
     d = json.loads(out[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench.UNIT
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the reference arm describes the headline workload with the main arm's config
+    from paper_2301_08357_gb300 import synthetic as S
+    assert d["config"] == bench.headline_config(S.make_c3(6))
+    assert d["config"]["workload"].startswith("c3_3d_kuhn_6^3")
 
 
 def test_clock_parser():
