@@ -88,7 +88,12 @@ typedef struct {
                              /* 1 = persistent blocks with double-buffered staging */
     int32_t update_blocks_per_sm; /* grid of the CG update kernel in blocks per SM */
                              /* (0 = auto)                                          */
-    int32_t reserved[4];
+    int32_t operator_kernel; /* FP32 CG operator kernel of 3D meshes: 0 = auto     */
+                             /* (one patch per thread), 1 = one patch per thread,  */
+                             /* 2 = paired patches (packed FP32x2 arithmetic)      */
+    int32_t operator_threads; /* threads per block of the paired-patch kernel:     */
+                             /* 0 = auto (256), 128 or 256                          */
+    int32_t reserved[2];
 } ps_mesh_opts;
 
 typedef struct {
@@ -116,7 +121,11 @@ typedef struct {
                              /* PS_ENGINE_PERSISTENT (mixed mode) runs the batched  */
                              /* persistent engine on a batch of one, which gives    */
                              /* bitwise the result the mesh gets in any batch       */
-    int32_t reserved[5];
+    int32_t grid_spin_limit; /* diagnostic: polls of the persistent kernel's grid   */
+                             /* barrier before it gives up and the call returns     */
+                             /* PS_ETIMEOUT (batched, persistent and served solves; */
+                             /* 0 = 2^26 polls, each at least 32 ns apart)          */
+    int32_t reserved[4];
 } ps_solve_opts;
 
 #define PS_ENGINE_AUTO        0
@@ -165,7 +174,10 @@ const char *ps_last_error(void);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
  * memory held by meshes, coefficients and solver workspaces of this context
- * (0 = no cap beyond the device).  *out receives the handle. */
+ * (0 = no cap beyond the device).  *out receives the handle.  The first
+ * context on a device also commits the 16 MiB scratch array of
+ * ps_pressure_apply_noalloc on it (outside every budget; held until exit):
+ * PS_ENOMEM if the device cannot provide it. */
 int ps_ctx_create(ps_ctx **out, int device, size_t hbm_budget_bytes);
 
 /* Destroy a context and every mesh still attached to it. */
@@ -262,10 +274,16 @@ int ps_pressure_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, int precisi
  * file-scope device array of 16 MiB that every GPU loading the library holds
  * until exit; meshes needing more (about 2 x n_nodes x 4 or 8 bytes plus the
  * partial sums) are rejected with PS_EINVAL and a ps_last_error message.  The
- * first call on a device looks up the array's device address (that device
- * current); make that first call before any stream capture.  Calls share the
- * array: calls whose work overlaps on the GPU race.  Calls no cudaMalloc or
- * cudaFree.  The mesh itself must have been uploaded and its coefficients set. */
+ * array's device address is looked up once per device when the first
+ * context is created on it (ps_ctx_create), which loads the module and
+ * commits the array's memory there, not inside this call; the cached address
+ * assumes the device's primary context lives until the process exits (no
+ * cudaDeviceReset in between).  The array lies outside the context's HBM
+ * budget.  Calls share the array: calls whose work overlaps on the GPU race.
+ * Calls no cudaMalloc or cudaFree.  If a bounded device wait gives up, y is
+ * undefined and the context's error flag reports PS_ETIMEOUT at its next
+ * synchronising call (a solve or coefficient update).  The mesh itself must
+ * have been uploaded and its coefficients set. */
 int ps_pressure_apply_noalloc(ps_mesh *mesh, const void *x_dev, void *y_dev, int precision, void *stream);
 
 /* ---- solve A x = b (Section 3.4: SPD system, matrix-free CG, warm start) --
@@ -483,6 +501,20 @@ int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, int64_t n_e
  * periodic vertices hold their unknown's value.  Synchronises the stream.
  * Errors: PS_EINVAL, PS_ESTATE (coefficients not set), PS_ECUDA. */
 int ps_mesh_get_jacobi(const ps_mesh *mesh, int precision, void *dinv_host, void *stream);
+
+/* ---- the FP32 CG operator kernel in isolation (diagnostics) --------------
+ * One pass of the FP32 operator kernel of the two-kernel CG iteration (the
+ * solver's dominant kernel, in the mesh's operator_kernel variant) with the
+ * direction p = x: y = A x (Section 3.4's matrix, Dirichlet rows and columns
+ * removed) and *pap = x^T A x as the kernel accumulates it (per element
+ * p_e^T A_e p_e, double-float sums).
+ *   x_dev, y_dev  device [n_nodes] float, caller numbering, must not alias
+ *   pap           host double or NULL
+ * Uses the mesh's solver workspace (its CG vectors are overwritten: run it
+ * between solves, not during one).  Synchronises the stream.  Errors:
+ * PS_EINVAL, PS_ESTATE (coefficients not set), PS_ETIMEOUT (a device wait
+ * gave up), PS_ECUDA. */
+int ps_debug_cg_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, double *pap, void *stream);
 
 /* ---- kernel timing (diagnostics for roofline reports) -------------------
  * Launch one internal kernel of the solver `reps` times back to back on

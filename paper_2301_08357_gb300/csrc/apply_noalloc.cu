@@ -12,11 +12,18 @@
 // loads the library holds until the process exits.
 //
 // The array's host-side name is only a stand-in; the device address is looked
-// up once per device with cudaGetSymbolAddress (that device current) on the
-// first call on that device.  Every call shares the array and it keeps the
-// last call's contents; nothing in it needs to start at zero because each call
-// writes every entry it later reads.  Calls whose work overlaps on the GPU
-// (different streams, or different meshes at the same time) race on it.
+// up once per device with cudaGetSymbolAddress (that device current) when a
+// context is created on it (ps_ctx_create calls noalloc_setup): the lookup
+// loads this file's module, which commits the array's device memory then and
+// not inside a later apply.  The cached address assumes the device's primary
+// context lives until the process exits (no cudaDeviceReset in between).
+// Every call shares the array and it keeps the last call's contents; nothing
+// in it needs to start at zero because a call that completes writes every
+// entry it later reads.  (If a bounded device wait gives up, the kernel
+// leaves its chunk unwritten: y is then undefined, and the context's error
+// flag reports PS_ETIMEOUT at its next synchronising call.)  Calls whose work
+// overlaps on the GPU (different streams, or different meshes at the same
+// time) race on it.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -47,8 +54,10 @@ int scratch_address(int device, void **out) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
-            ps_set_last_error(cudaGetErrorString(e));
-            return PS_ECUDA;
+            ps_set_last_error(e == cudaSuccess ? "no device address for the allocation-free scratch"
+                                               : cudaGetErrorString(e));
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? PS_ENOMEM : PS_ECUDA;
         }
         g_addr[device] = p;
     }
@@ -57,6 +66,13 @@ int scratch_address(int device, void **out) {
 }
 
 }  // namespace
+
+// Called by ps_ctx_create with `device` current: looks the scratch array up
+// (loading this module and committing its memory) once per device.
+int ps::noalloc_setup(int device) {
+    void *p = nullptr;
+    return scratch_address(device, &p);
+}
 
 extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int prec, void *stream) {
     if (!m || !x || !y || (prec != PS_F32 && prec != PS_F64) || x == y) return PS_EINVAL;
@@ -90,7 +106,7 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
     const int64_t n = m->dev.n_nodes, nu = m->prep.n_nodes;   // unknowns, caller's vertices
     const int g = grid_for(n, m->ctx->sms), gu = grid_for(nu, m->ctx->sms);
     if (prec == PS_F32) {
-        k_perm_in<float, float><<<g, 256, 0, s>>>(n, (const float *)x, (float *)xi, m->d_old_of_new, m->dev.dirichlet);
+        k_perm_in<float, float><<<g, kChunkThreads, 0, s>>>(n, (const float *)x, (float *)xi, m->d_old_of_new, m->dev.dirichlet);
         VecArgs<float> a;
         std::memset(&a, 0, sizeof(a));
         a.x = (const float *)xi;
@@ -98,9 +114,9 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
         a.partial = (float *)part;
         rc = launch_pass<float, kApply>(m, a, s);
         if (rc != PS_OK) return rc;
-        k_perm_out<float, float><<<gu, 256, 0, s>>>(nu, (const float *)yi, (float *)y, m->d_new_of_old);
+        k_perm_out<float, float><<<gu, kChunkThreads, 0, s>>>(nu, (const float *)yi, (float *)y, m->d_new_of_old);
     } else {
-        k_perm_in<double, double><<<g, 256, 0, s>>>(n, (const double *)x, (double *)xi, m->d_old_of_new,
+        k_perm_in<double, double><<<g, kChunkThreads, 0, s>>>(n, (const double *)x, (double *)xi, m->d_old_of_new,
                                                     m->dev.dirichlet);
         VecArgs<double> a;
         std::memset(&a, 0, sizeof(a));
@@ -109,7 +125,7 @@ extern "C" int ps_pressure_apply_noalloc(ps_mesh *m, const void *x, void *y, int
         a.partial = (double *)part;
         rc = launch_pass<double, kApply>(m, a, s);
         if (rc != PS_OK) return rc;
-        k_perm_out<double, double><<<gu, 256, 0, s>>>(nu, (const double *)yi, (double *)y, m->d_new_of_old);
+        k_perm_out<double, double><<<gu, kChunkThreads, 0, s>>>(nu, (const double *)yi, (double *)y, m->d_new_of_old);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -35,7 +35,8 @@ __device__ __forceinline__ int ld_acquire_i32(const int *p) {
 // takes the same decision.  The wait is bounded: on timeout the error flag is
 // set and false returned; the caller then leaves the kernel (other blocks
 // time out in turn).
-__device__ bool grid_barrier_stop(unsigned int *bar, int *err, const int *active_cnt, int *s_stop) {
+__device__ bool grid_barrier_stop(unsigned int *bar, int *err, const int *active_cnt, int *s_stop,
+                                  uint32_t spin_limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -49,7 +50,7 @@ __device__ bool grid_barrier_stop(unsigned int *bar, int *err, const int *active
             st_release_u32(gen, g + 1u);
             ok = 1;
         } else {
-            for (uint32_t i = 0; i < kGridSpinLimit; ++i) {
+            for (uint32_t i = 0; i < spin_limit; ++i) {
                 if (ld_acquire_u32(gen) != g) {
                     ok = 1;
                     break;
@@ -75,6 +76,7 @@ struct PcgArgs {
     int *active_cnt;
     int *err;
     int max_it;
+    uint32_t spin_limit;           // polls of the grid barrier before it gives up
     SmemLayout L;                  // chunk layout; the scalar cache follows at L.total
 };
 
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
             if (s_last) batch_mesh_scalars(M, S.red, A.active_cnt);
             __syncthreads();
         }
-        if (!grid_barrier_stop(A.bar, A.err, A.active_cnt, &s_stop)) return;
+        if (!grid_barrier_stop(A.bar, A.err, A.active_cnt, &s_stop, A.spin_limit)) return;
     }
 }
 
@@ -599,6 +601,7 @@ static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
     A.active_cnt = active;
     A.err = plan.ctx->d_err;
     A.max_it = plan.epoch_iters;
+    A.spin_limit = plan.spin_limit;
     A.L = plan.L32;
     void *args[] = {&A};
     cudaLaunchConfig_t cfg;
@@ -688,6 +691,7 @@ int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev
         rc = batch_upload_states(plan, s);
     }
     if (rc == PS_OK && o.graph_iters < 0) plan.graph_ok = false;
+    plan.spin_limit = o.grid_spin_limit > 0 ? (uint32_t)o.grid_spin_limit : kGridSpinLimit;
     // every epoch advances each unfinished mesh by at least one phase step;
     // bound the number of epochs by the iteration and outer-step caps
     long long max_epochs = 8;

@@ -82,6 +82,7 @@ struct BatchPlan {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = true;
+    uint32_t spin_limit = kGridSpinLimit;   // grid-barrier polls before giving up
 };
 
 // Per-mesh batch workspace beyond ps_mesh::ws (FP64 reduction partials).

@@ -356,12 +356,164 @@ __device__ __forceinline__ K2Node<T> k2_load(const MeshDev &m, const Cg2Args<T> 
     return v;
 }
 
+// FP32 path of K2: interior nodes in groups of four (16-byte vectors), two
+// groups per thread in flight; then the shared nodes (and the interior tail),
+// four per thread in flight: their partial-sum ranges are read first, then
+// the partials of all four nodes slot by slot, so the dependent loads of
+// different nodes overlap.  Each shared node sums its partials in slot order
+// (the same sums as the one-node-at-a-time form).
+template <typename Acc>
+__device__ __forceinline__ void k2_f32(const MeshDev &m, const Cg2Args<float> &a, float alpha, float beta,
+                                       int64_t tid, int64_t nthr, Acc &arz, Acc &arr) {
+    const int64_t n4 = m.n_int / 4;
+    const float4 *X4 = reinterpret_cast<const float4 *>(a.x);
+    const float4 *R4 = reinterpret_cast<const float4 *>(a.r);
+    const float4 *P4 = reinterpret_cast<const float4 *>(a.p);
+    const float4 *Q4 = reinterpret_cast<const float4 *>(a.q);
+    const float4 *D4 = reinterpret_cast<const float4 *>(a.dinv);
+    constexpr int kG = 2;
+    for (int64_t j0 = tid; j0 < n4; j0 += kG * nthr) {
+        float4 x4[kG], r4[kG], p4[kG], q4[kG], d4[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const int64_t j = j0 + k * nthr;
+            if (j < n4) {
+                x4[k] = X4[j];
+                r4[k] = R4[j];
+                p4[k] = P4[j];
+                q4[k] = Q4[j];
+                d4[k] = __ldg(D4 + j);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const int64_t j = j0 + k * nthr;
+            if (j >= n4) continue;
+            float4 xo, ro;
+            xo.x = x4[k].x + alpha * p4[k].x; ro.x = r4[k].x - alpha * q4[k].x;
+            xo.y = x4[k].y + alpha * p4[k].y; ro.y = r4[k].y - alpha * q4[k].y;
+            xo.z = x4[k].z + alpha * p4[k].z; ro.z = r4[k].z - alpha * q4[k].z;
+            xo.w = x4[k].w + alpha * p4[k].w; ro.w = r4[k].w - alpha * q4[k].w;
+            reinterpret_cast<float4 *>(a.x)[j] = xo;
+            reinterpret_cast<float4 *>(a.r)[j] = ro;
+            arz.add_prod(ro.x, d4[k].x * ro.x); arr.add_prod(ro.x, ro.x);
+            arz.add_prod(ro.y, d4[k].y * ro.y); arr.add_prod(ro.y, ro.y);
+            arz.add_prod(ro.z, d4[k].z * ro.z); arr.add_prod(ro.z, ro.z);
+            arz.add_prod(ro.w, d4[k].w * ro.w); arr.add_prod(ro.w, ro.w);
+        }
+    }
+    constexpr int kS = 4;
+    for (int64_t i0 = 4 * n4 + tid; i0 < m.n_nodes; i0 += kS * nthr) {
+        int64_t ii[kS];
+        int kb[kS], ke[kS];
+        float dv[kS], rv[kS], pv[kS], qv[kS];
+        bool dir[kS];
+        int deg = 0;
+#pragma unroll
+        for (int k = 0; k < kS; ++k) {
+            ii[k] = i0 + k * nthr;
+            kb[k] = ke[k] = 0;
+            qv[k] = 0.f;
+            dir[k] = false;
+            if (ii[k] < m.n_nodes) {
+                dv[k] = __ldg(a.dinv + ii[k]);
+                rv[k] = a.r[ii[k]];
+                pv[k] = a.p[ii[k]];
+                if (ii[k] < m.n_int) {
+                    qv[k] = a.q[ii[k]];
+                } else {
+                    const int64_t sh = ii[k] - m.n_int;
+                    kb[k] = __ldg(m.shr_ptr + sh);
+                    ke[k] = __ldg(m.shr_ptr + sh + 1);
+                    dir[k] = __ldg(m.dirichlet + ii[k]) != 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kS; ++k) deg = max(deg, ke[k] - kb[k]);
+        for (int t = 0; t < deg; ++t) {
+            float pt[kS];
+#pragma unroll
+            for (int k = 0; k < kS; ++k) pt[k] = kb[k] + t < ke[k] ? __ldcg(a.partial + kb[k] + t) : 0.f;
+#pragma unroll
+            for (int k = 0; k < kS; ++k)
+                if (kb[k] + t < ke[k]) qv[k] += pt[k];
+        }
+#pragma unroll
+        for (int k = 0; k < kS; ++k) {
+            const int64_t i = ii[k];
+            if (i >= m.n_nodes) continue;
+            float pi = pv[k], qi = qv[k];
+            if (i >= m.n_int) {
+                pi = cg_dir(dv[k], rv[k], beta, pv[k]);
+                if (dir[k]) {
+                    pi = 0.f;
+                    qi = 0.f;
+                }
+                a.p[i] = pi;
+                a.q[i] = qi;
+            }
+            a.x[i] += alpha * pi;
+            const float ri = rv[k] - alpha * qi;
+            a.r[i] = ri;
+            arz.add_prod(ri, dv[k] * ri);
+            arr.add_prod(ri, ri);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     __shared__ double red[34];
     __shared__ double s_sc[2];
     __shared__ int s_done;
     __shared__ bool s_last;
+    if constexpr (sizeof(T) == 4) {
+        if (threadIdx.x == 0) {
+            s_done = a.st->done;
+            s_sc[0] = a.st->alpha;
+            s_sc[1] = a.st->beta;
+        }
+        __syncthreads();
+        if (s_done) return;
+        DotF arz, arr;
+        k2_f32(m, a, (float)s_sc[0], (float)s_sc[1], (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (int64_t)gridDim.x * blockDim.x, arz, arr);
+        double vrz, vrr;
+        block_sum2(arz, arr, red, vrz, vrr);
+        if (threadIdx.x == 0) {
+            part_pack(vrz, a.z2[blockIdx.x]);
+            part_pack(vrr, a.z2[a.g3 + blockIdx.x]);
+            const unsigned int t = atomic_add_acq_rel(&a.st->cnt_b, 1u);
+            s_last = (t == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (!s_last) return;
+        double rz, rr;
+        part_sum2(a.z2, a.z2 + a.g3, gridDim.x, red, rz, rr);
+        if (threadIdx.x == 0) {
+            CgState *st = a.st;
+            st->cnt_b = 0;
+            st->iters += 1;
+            st->rr = rr;
+            int done = 0;
+            if (!isfinite(rz) || !isfinite(rr)) {
+                st->status = kCgBreakdown;
+                done = 1;
+            } else if (rr <= st->stop_rr) {
+                st->status = kCgConverged;
+                done = 1;
+            } else if (st->iters >= st->max_iters) {
+                st->status = kCgMaxIter;
+                done = 1;
+            } else {
+                st->beta = rz / st->rz;
+                st->rz = rz;
+            }
+            if (done) st->done = 1;
+        }
+        return;
+    }
     const int64_t n4 = m.n_int / 4;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,0 +1,364 @@
+// FP32 CG operator kernel of 3D meshes on paired patches (layout.h, "units").
+//
+// The same iteration step as k_cg2_chunks<3, float> (p = D^-1 r + beta p on
+// the chunk's nodes, q = A p, the chunk's share of p.Ap), organised for the
+// instruction budget of a pass that moves ~20 bytes per tetrahedron:
+//   * one thread evaluates one unit -- two star patches of equal size -- with
+//     packed FP32x2 arithmetic (FFMA2 / FADD2 / FMUL2: one instruction for both
+//     patches), so each element costs about half the issue slots;
+//   * unit records and beta*dt^2/6 are read straight into registers
+//     (coalesced, before the staging wait); only node records and the
+//     incidence segment are staged into shared memory by bulk copies;
+//   * contributions of a unit are stored as float2 pairs (one 8-byte store
+//     per slot), and node sums run over a degree-sorted, transposed incidence
+//     list (lanes of a warp read consecutive entries, the loop count is the
+//     group's degree: no divergence);
+//   * the p.Ap share is summed by one warp after the node phase (no block
+//     reduction tree).
+// Results are deterministic: every sum has a fixed order.  The element
+// arithmetic is that of patch_eval (device.cuh): with e1 = b - a and
+// d_j = r_j - a, element j of a patch has the cofactor vectors
+// c1 = d_j x d_{j+1}, c2 = -(e1 x d_{j+1}), c3 = e1 x d_j and c0 = -(c1+c2+c3),
+// det = e1 . c1; stiffness K v = beta dt^2 / (6 |det|) (c_i . g),
+// g = sum_k (v_k - v_a) c_k; consistent mass (M_alpha v)_i =
+// |det|/720 (S X + Q + S v_i + alpha_i (X + 2 v_i)), S = sum alpha, X = sum v,
+// Q = sum alpha v; lumped mass |det|/24 alpha_i v_i.
+#pragma once
+#include "cg2.cuh"
+
+namespace ps {
+
+// ---------------------------------------------------------------- packed FP32x2
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
+__device__ __forceinline__ float2 p_abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 p_set(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct P3 {
+    float2 x, y, z;
+};
+__device__ __forceinline__ P3 p3_sub(const P3 &a, const P3 &b) {
+    return {p_sub(a.x, b.x), p_sub(a.y, b.y), p_sub(a.z, b.z)};
+}
+// a x b
+__device__ __forceinline__ P3 p3_cross(const P3 &a, const P3 &b) {
+    return {p_fma(a.y, b.z, p_neg(p_mul(a.z, b.y))), p_fma(a.z, b.x, p_neg(p_mul(a.x, b.z))),
+            p_fma(a.x, b.y, p_neg(p_mul(a.y, b.x)))};
+}
+__device__ __forceinline__ float2 p3_dot(const P3 &a, const P3 &b) {
+    return p_fma(a.z, b.z, p_fma(a.y, b.y, p_mul(a.x, b.x)));
+}
+
+// Node of both halves: coordinates, alpha (absolute value: the sign bit marks
+// Dirichlet nodes) and the input value.
+struct PNode {
+    P3 p;
+    float2 al, v;
+};
+__device__ __forceinline__ PNode pnode(const NodeF *__restrict__ s_node, const float *__restrict__ s_val, uint32_t w) {
+    const int i0 = (int)(w & 0xffffu), i1 = (int)(w >> 16);
+    const NodeF n0 = s_node[i0], n1 = s_node[i1];
+    PNode r;
+    r.p = {make_float2(n0.x, n1.x), make_float2(n0.y, n1.y), make_float2(n0.z, n1.z)};
+    r.al = make_float2(fabsf(n0.w), fabsf(n1.w));
+    r.v = make_float2(s_val[i0], s_val[i1]);
+    return r;
+}
+
+// One unit of M tetrahedra per half: contributions into out[slot] (float2,
+// slot 0 -> a, 1 -> b, 2 + j -> r_j).  rec: the unit record; bd: beta*dt^2/6
+// of element j of each half.
+template <int M, bool LUMP>
+__device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
+                                          const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
+                                          float2 *__restrict__ out) {
+    const PNode A = pnode(s_node, s_val, rec[1]);
+    const PNode B = pnode(s_node, s_val, rec[2]);
+    const P3 e1 = p3_sub(B.p, A.p);
+    PNode R0 = pnode(s_node, s_val, rec[3]);
+    P3 d0 = p3_sub(R0.p, A.p);
+    P3 w0 = p3_cross(e1, d0);
+    const float2 t1 = p_sub(B.v, A.v);
+    float2 t2 = p_sub(R0.v, A.v);
+    const float2 sAB = p_add(A.al, B.al);
+    const float2 xAB = p_add(A.v, B.v);
+    const float2 qa = p_mul(A.al, A.v), qb = p_mul(B.al, B.v);
+    const float2 qAB = p_add(qa, qb);
+    float2 q0 = p_mul(R0.al, R0.v);
+    float2 acc_a = p_set(0.f), acc_b = p_set(0.f), acc_c = p_set(0.f);
+    const float2 two = p_set(2.f);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const PNode R1 = pnode(s_node, s_val, rec[4 + j]);
+        const P3 d1 = p3_sub(R1.p, A.p);
+        const P3 w1 = p3_cross(e1, d1);
+        const P3 c1 = p3_cross(d0, d1);
+        const float2 ad = p_abs(p3_dot(e1, c1));
+        const float2 kc = p_mul(bd[j], make_float2(rcp_approx(ad.x), rcp_approx(ad.y)));
+        const float2 t3 = p_sub(R1.v, A.v);
+        // g = t1 c1 - t2 w1 + t3 w0, scaled by kc
+        const float2 nt2 = p_neg(t2);
+        P3 g;
+        g.x = p_mul(kc, p_fma(t3, w0.x, p_fma(nt2, w1.x, p_mul(t1, c1.x))));
+        g.y = p_mul(kc, p_fma(t3, w0.y, p_fma(nt2, w1.y, p_mul(t1, c1.y))));
+        g.z = p_mul(kc, p_fma(t3, w0.z, p_fma(nt2, w1.z, p_mul(t1, c1.z))));
+        const float2 k1 = p3_dot(c1, g);
+        const float2 k2 = p_neg(p3_dot(w1, g));
+        const float2 k3 = p3_dot(w0, g);
+        const float2 k0 = p_neg(p_add(p_add(k1, k2), k3));
+        const float2 q1 = p_mul(R1.al, R1.v);
+        float2 o0, o1, o2, o3;
+        if constexpr (LUMP) {
+            const float2 cl = p_mul(ad, p_set(1.0f / 24.0f));
+            o0 = p_fma(cl, qa, k0);
+            o1 = p_fma(cl, qb, k1);
+            o2 = p_fma(cl, q0, k2);
+            o3 = p_fma(cl, q1, k3);
+        } else {
+            const float2 S = p_add(sAB, p_add(R0.al, R1.al));
+            const float2 X = p_add(xAB, p_add(R0.v, R1.v));
+            const float2 Q = p_add(qAB, p_add(q0, q1));
+            const float2 base = p_fma(S, X, Q);
+            const float2 cm = p_mul(ad, p_set(1.0f / 720.0f));
+            // o_i = cm (base + S v_i + alpha_i (X + 2 v_i)) + k_i
+            o0 = p_fma(cm, p_fma(A.al, p_fma(two, A.v, X), p_fma(S, A.v, base)), k0);
+            o1 = p_fma(cm, p_fma(B.al, p_fma(two, B.v, X), p_fma(S, B.v, base)), k1);
+            o2 = p_fma(cm, p_fma(R0.al, p_fma(two, R0.v, X), p_fma(S, R0.v, base)), k2);
+            o3 = p_fma(cm, p_fma(R1.al, p_fma(two, R1.v, X), p_fma(S, R1.v, base)), k3);
+        }
+        acc_a = p_add(acc_a, o0);
+        acc_b = p_add(acc_b, o1);
+        out[2 + j] = p_add(acc_c, o2);
+        acc_c = o3;
+        d0 = d1;
+        w0 = w1;
+        R0 = R1;
+        t2 = t3;
+        q0 = q1;
+    }
+    out[2 + M] = acc_c;
+    out[0] = acc_a;
+    out[1] = acc_b;
+}
+
+template <bool LUMP>
+__device__ __forceinline__ void unit_eval_any(int m, const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
+                                              const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
+                                              float2 *__restrict__ out) {
+    switch (m) {
+        case 6: unit_eval<6, LUMP>(s_node, s_val, rec, bd, out); break;
+        case 5: unit_eval<5, LUMP>(s_node, s_val, rec, bd, out); break;
+        case 4: unit_eval<4, LUMP>(s_node, s_val, rec, bd, out); break;
+        case 3: unit_eval<3, LUMP>(s_node, s_val, rec, bd, out); break;
+        case 2: unit_eval<2, LUMP>(s_node, s_val, rec, bd, out); break;
+        default: unit_eval<1, LUMP>(s_node, s_val, rec, bd, out); break;
+    }
+}
+
+__device__ __forceinline__ void load_unit(const MeshDev &m, int64_t u, uint32_t (&rec)[kURecWords],
+                                          float2 (&bd)[kPatchMax]) {
+    const uint2 *r2 = reinterpret_cast<const uint2 *>(m.urec + u * kURecWords);
+#pragma unroll
+    for (int k = 0; k < kURecWords / 2; ++k) {
+        const uint2 v = __ldg(r2 + k);
+        rec[2 * k] = v.x;
+        rec[2 * k + 1] = v.y;
+    }
+    const float4 *b4 = reinterpret_cast<const float4 *>(m.ubd + u * kPatchMax * 2);
+#pragma unroll
+    for (int k = 0; k < kPatchMax / 2; ++k) {
+        const float4 v = __ldg(b4 + k);
+        bd[2 * k] = make_float2(v.x, v.y);
+        bd[2 * k + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// K1 on paired patches: one block of NT threads (128 or 256) per chunk.
+template <bool LUMP, int NT>
+__global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const UnitSmem &L = m.smu;
+    NodeF *s_node = reinterpret_cast<NodeF *>(smem + L.node);
+    float *s_val = reinterpret_cast<float *>(smem + L.val);
+    uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
+    float *s_con = reinterpret_cast<float *>(smem + L.contrib);
+    float2 *s_dot = reinterpret_cast<float2 *>(smem + L.dot);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    __shared__ float s_beta;
+    __shared__ int s_done;
+    __shared__ bool s_last;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_done = a.st->done;
+        s_beta = (float)a.st->beta;
+        mbar_init(s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_done) return;
+    const ChunkDesc cd = m.chunks[blockIdx.x];
+    const ChunkUnits cu = m.chunks_u[blockIdx.x];
+    if (tid == 0) {
+        const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
+        const uint32_t b_inc = (uint32_t)cu.uinc_n * 2u;
+        mbar_arrive_expect_tx(s_bar, b_node + b_inc);
+        bulk_g2s(s_node, m.node32 + cd.node_off, b_node, s_bar);
+        bulk_g2s(s_inc, m.uinc + cu.uinc_off, b_inc, s_bar);
+    }
+    const float beta = s_beta;
+    const int n_loc = cd.n_loc, n_int = cd.n_int;
+    // the thread's first unit, in registers before the staging wait
+    uint32_t rec[kURecWords];
+    float2 bd[kPatchMax];
+    const bool has_unit = tid < cu.n_unit;
+    if (has_unit) load_unit(m, (int64_t)cu.unit_off + tid, rec, bd);
+    // p = D^-1 r + beta p on the chunk's nodes (loads of four nodes before any
+    // store: the stores to p could alias them); no Dirichlet mask is needed
+    // (D^-1 = 0 and r = 0 there and p starts at 0)
+    for (int l0 = tid; l0 < n_loc; l0 += 4 * NT) {
+        int gg[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * NT;
+            gg[k] = l < n_int ? cd.int_begin + l : (l < n_loc ? __ldg(m.sh_ids + cd.sh_off + (l - n_int)) : -1);
+        }
+        float dv[4], rv[4], pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dv[k] = rv[k] = pv[k] = 0.f;
+            if (gg[k] >= 0) {
+                dv[k] = a.dinv[gg[k]];
+                rv[k] = a.r[gg[k]];
+                pv[k] = a.p[gg[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * NT;
+            if (gg[k] >= 0) {
+                const float v = cg_dir(dv[k], rv[k], beta, pv[k]);
+                s_val[l] = v;
+                if (l < n_int) a.p[gg[k]] = v;
+            }
+        }
+    }
+    uint32_t ph = 0;
+    {
+        bool ok = mbar_wait_bounded(s_bar, ph);
+        ok = __syncthreads_and(ok);   // also publishes s_val
+        if (!ok) {
+            if (tid == 0) atomicOr(m.err, kErrMbarTimeout);
+            mbar_wait_bounded(s_bar, ph);
+            return;
+        }
+    }
+    // ---- element phase: one unit per thread and round
+    float2 *s_con2 = reinterpret_cast<float2 *>(s_con);
+    if (tid == 0) s_con[cu.n_unit * 2 * kUnitSlots] = 0.f;   // the zero slot
+    if (has_unit) {
+        if (rec[0] == 6)
+            unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_con2 + tid * kUnitSlots);
+        else
+            unit_eval_any<LUMP>((int)rec[0], s_node, s_val, rec, bd, s_con2 + tid * kUnitSlots);
+    }
+    for (int u = tid + NT; u < cu.n_unit; u += NT) {
+        load_unit(m, (int64_t)cu.unit_off + u, rec, bd);
+        unit_eval_any<LUMP>((int)rec[0], s_node, s_val, rec, bd, s_con2 + u * kUnitSlots);
+    }
+    __syncthreads();
+    // ---- node phase: groups of 32 nodes (one warp), transposed entries
+    const uint16_t *hdr = s_inc;
+    const uint16_t *ord = s_inc + cu.order_off;
+    const uint16_t *ent = s_inc + cu.ent_off;
+    DotF acc;
+    const int lane = tid & 31;
+    for (int idx = tid; idx < cu.n_grp * 32; idx += NT) {
+        const int g = idx >> 5;
+        const int l = ord[idx];
+        const int first = hdr[2 * g], deg = hdr[2 * g + 1];
+        const uint16_t *e = ent + first + lane;
+        float s0 = 0.f, s1 = 0.f;
+        int k = 0;
+        for (; k + 1 < deg; k += 2) {
+            s0 += s_con[e[32 * k]];
+            s1 += s_con[e[32 * (k + 1)]];
+        }
+        if (k < deg) s0 += s_con[e[32 * k]];
+        if (l == kNoNode) continue;
+        float s = s0 + s1;
+        acc.add_prod(s_val[l], s);                 // element-wise p^T A_e p over the chunk
+        if (is_dirichlet(s_node[l].w)) s = 0.f;
+        if (l < n_int)
+            a.q[cd.int_begin + l] = s;
+        else
+            a.partial[__ldg(m.sh_dest + cd.sh_off + (l - n_int))] = s;
+    }
+    // ---- the chunk's share of p.Ap: one warp sums the threads' partials in order
+    s_dot[tid] = make_float2(acc.hi, acc.lo);
+    __syncthreads();
+    if (tid >= 32) return;
+    DotF t;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) {
+        const float2 v = s_dot[k * 32 + tid];
+        t.merge(v.x, v.y);
+    }
+    t = warp_merge(t);
+    if (tid == 0) {
+        a.pq[blockIdx.x] = part_pack((double)t.hi + (double)t.lo);
+        const unsigned int c = atomic_add_acq_rel(&a.st->cnt_a, 1u);
+        s_last = (c == gridDim.x - 1);
+    }
+    __syncwarp();
+    if (!s_last) return;
+    // last chunk to finish: alpha = rz / p.Ap (one warp; lane i sums chunks
+    // i, i + 32, ... into eight accumulators by turn, merged in a fixed order)
+    constexpr int kAcc = 8;
+    DotF part[kAcc];
+    for (int i0 = tid; i0 < (int)gridDim.x; i0 += 32 * kAcc) {
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) {
+            const int i = i0 + 32 * k;
+            if (i < (int)gridDim.x) {
+                const float2 v = __ldcg(a.pq + i);
+                part[k].merge(v.x, v.y);
+            }
+        }
+    }
+    DotF tot = part[0];
+#pragma unroll
+    for (int k = 1; k < kAcc; ++k) tot.merge(part[k].hi, part[k].lo);
+    tot = warp_merge(tot);
+    if (tid == 0) {
+        const double pq = (double)tot.hi + (double)tot.lo;
+        CgState *st = a.st;
+        st->cnt_a = 0;
+        st->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            st->status = kCgBreakdown;
+            st->done = 1;
+        } else {
+            st->alpha = st->rz / pq;
+        }
+    }
+}
+
+// beta*dt^2/6 of every (unit, element, half) slot from the caller's beta
+// (0 on slots without an element).
+static __global__ void k_set_beta_units(int64_t n, const int32_t *__restrict__ uelem, const double *__restrict__ beta,
+                                        double dt2, float *__restrict__ ubd) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int e = uelem[k];
+        ubd[k] = e >= 0 ? (float)(beta[e] * dt2 * (1.0 / 6.0)) : 0.f;
+    }
+}
+
+}  // namespace ps

@@ -67,6 +67,9 @@ double inner_reduction(double itol, double tol, double bb, double rr);
 // projection.cu
 void projection_release(ps_mesh *m);
 
+// apply_noalloc.cu
+int noalloc_setup(int device);
+
 // batched.cu
 int batched_set_attrs();
 void batched_release_mesh(ps_mesh *m);
@@ -101,7 +104,11 @@ struct ps_mesh {
     int pipe_grid = 0;                 // its persistent grid (0 = not used)
     int pipeline = 0;                  // ps_mesh_opts::pipeline
     int update_bps = 0;                // ps_mesh_opts::update_blocks_per_sm
+    int k1_variant = 0;                // ps_mesh_opts::operator_kernel
     bool k1_pre = false;               // FP32 operator kernel variant (beta prefetch)
+    bool use_units = false;            // FP32 CG operator kernel on paired patches (3D)
+    int unit_threads = 256;            // its threads per block (ps_mesh_opts::operator_threads)
+    int32_t *d_uelem = nullptr;        // element of each (unit, element, half) slot, -1 none
     bool coeff_ok = false, alpha_set = false;
     bool alpha_newton = false;         // alpha last set by the general-EOS Newton iteration
     double dt2 = 0.0;

@@ -53,7 +53,19 @@ struct PrepMesh {
     // [sh_total * 4] per chunk slot: node id, begin and end of the node's
     // partial-sum range, 1 on the owner slot (the node's first chunk); pads -1, 0, 0, 0
     std::vector<int32_t> sh_info;
+
+    // paired-patch layout (layout.h; 3D only, empty in 2D)
+    std::vector<ChunkUnits> chunks_u;              // [n_chunks]
+    std::vector<uint32_t> urec;                    // [unit_total * kURecWords]
+    std::vector<int32_t> uelem;                    // [unit_total * kPatchMax * 2] element of (tet j, half h), -1 none
+    std::vector<uint16_t> uinc;                    // incidence segments of all chunks
+    int64_t unit_total = 0;
+    int max_unit = 0, max_uinc = 0;
 };
+
+// Build the paired-patch layout from a prepared 3D mesh (its patch records
+// and element map).  Returns "" on success.
+std::string build_units(PrepMesh &m);
 
 // Returns "" on success, else an error message (bad input).
 std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t n_elems,

@@ -26,6 +26,13 @@ struct SmemLayout {
     uint32_t node, val, aux, pids, incp, inc, shid, contrib, red, bar, total;
 };
 
+// Shared memory of the paired-patch CG operator kernel (cg2u.cuh): node
+// records | values | incidence segment | contributions (+ the zero slot) |
+// per-thread dot partials | mbarrier.
+struct UnitSmem {
+    uint32_t node, val, inc, contrib, dot, bar, total;
+};
+
 struct MeshDev {
     int dim, n_chunks;
     int64_t n_nodes, n_int, n_shared, n_pad;
@@ -45,6 +52,12 @@ struct MeshDev {
     int *err;
     int lumped;              // 1: mass term by vertex quadrature (mass-lumped variant)
     SmemLayout sm32, sm64;
+    // paired-patch layout (3D; null in 2D)
+    const ChunkUnits *chunks_u;
+    const uint32_t *urec;    // [unit_total * kURecWords]
+    const float *ubd;        // [unit_total * kPatchMax * 2] beta*dt^2/6 per (unit, element, half)
+    const uint16_t *uinc;    // incidence segments
+    UnitSmem smu;
 };
 
 // Scalars of one CG run, kept on the device.

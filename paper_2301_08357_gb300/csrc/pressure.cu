@@ -22,6 +22,7 @@
 #include "internal.h"
 #include "cg1.cuh"
 #include "cg2.cuh"
+#include "cg2u.cuh"
 
 using namespace ps;
 
@@ -236,6 +237,10 @@ static int set_smem_attrs() {
     CK(set_max_dyn_smem(k_cg2_chunks<3, double>));
     CK(set_max_dyn_smem(k_cg2_chunks_pipe<2>));
     CK(set_max_dyn_smem(k_cg2_chunks_pipe<3>));
+    CK(set_max_dyn_smem(k_cg2_units<false, 256>));
+    CK(set_max_dyn_smem(k_cg2_units<true, 256>));
+    CK(set_max_dyn_smem(k_cg2_units<false, 128>));
+    CK(set_max_dyn_smem(k_cg2_units<true, 128>));
     return batched_set_attrs();
 }
 
@@ -288,6 +293,7 @@ extern "C" int ps_ctx_create(ps_ctx **out, int device, size_t budget) {
     if (device < 0 || device >= n) return PS_EINVAL;
     CK(cudaSetDevice(device));
     RC(set_smem_attrs());
+    RC(noalloc_setup(device));
     ps_ctx *c = new (std::nothrow) ps_ctx();
     if (!c) return PS_ENOMEM;
     c->device = device;
@@ -422,6 +428,36 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     RC(upload(c, m, &g, nullptr, d.n_pad * 8));
     CK(cudaMemset(g, 0, d.n_pad * 8));
     d.dinv64 = g;
+    if (pm.dim == 3 && pm.unit_total > 0 && m->k1_variant == 2) {
+        ChunkUnits *cu;
+        RC(upload(c, m, &cu, pm.chunks_u.data(), pm.chunks_u.size() * sizeof(ChunkUnits)));
+        d.chunks_u = cu;
+        uint32_t *ur;
+        RC(upload(c, m, &ur, pm.urec.data(), pm.urec.size() * 4));
+        d.urec = ur;
+        RC(upload(c, m, &m->d_uelem, pm.uelem.data(), pm.uelem.size() * 4));
+        RC(upload(c, m, &u, pm.uinc.data(), pm.uinc.size() * 2));
+        d.uinc = u;
+        float *ub;
+        RC(upload(c, m, &ub, nullptr, pm.uelem.size() * 4));
+        CK(cudaMemset(ub, 0, pm.uelem.size() * 4));
+        d.ubd = ub;
+        UnitSmem &U = d.smu;
+        uint32_t off = 0;
+        auto take = [&](uint64_t bytes) {
+            const uint32_t at = off;
+            off = align128(off + bytes);
+            return at;
+        };
+        U.node = take((uint64_t)pm.max_loc * sizeof(NodeF));
+        U.val = take((uint64_t)pm.max_loc * 4);
+        U.inc = take((uint64_t)pm.max_uinc * 2);
+        U.contrib = take((uint64_t)pm.max_unit * 2 * kUnitSlots * 4 + 16);
+        U.dot = take((uint64_t)kChunkThreads * 8);
+        U.bar = take(8);
+        U.total = off;
+        m->use_units = U.total <= 200 * 1024;
+    }
     d.err = c->d_err;
     d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
     d.sm64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
@@ -496,7 +532,11 @@ extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, cons
     m->ctx = c;
     m->pipeline = opts ? opts->pipeline : 0;
     m->update_bps = opts ? opts->update_blocks_per_sm : 0;
-    if (m->update_bps < 0 || m->update_bps > 64) {
+    m->k1_variant = opts ? opts->operator_kernel : 0;
+    const int ot = opts ? opts->operator_threads : 0;
+    m->unit_threads = ot == 128 ? 128 : 256;
+    if (m->update_bps < 0 || m->update_bps > 64 || m->k1_variant < 0 || m->k1_variant > 2 ||
+        (ot != 0 && ot != 128 && ot != 256)) {
         delete m;
         return PS_EINVAL;
     }
@@ -589,6 +629,11 @@ static int coeff_upload(ps_mesh *m, const double *alpha, const double *beta, dou
         k_set_beta<<<grid_for(nslots, c->sms), kBlock>>>(nslots, m->d_elem_src, (const double *)dbeta, dt2,
                                                                  const_cast<float *>(d.bdt2_32),
                                                                  const_cast<double *>(d.bdt2_64));
+        if (d.ubd) {
+            const int64_t nu = (int64_t)p.uelem.size();
+            k_set_beta_units<<<grid_for(nu, c->sms), kBlock>>>(nu, m->d_uelem, (const double *)dbeta, dt2,
+                                                               const_cast<float *>(d.ubd));
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && alpha) {
@@ -706,6 +751,11 @@ int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStrea
     k_set_beta<<<grid_for(nslots, m->ctx->sms), kBlock, 0, s>>>(nslots, m->d_elem_src, beta_dev, dt2,
                                                                  const_cast<float *>(d.bdt2_32),
                                                                  const_cast<double *>(d.bdt2_64));
+    if (d.ubd) {
+        const int64_t nu = (int64_t)p.uelem.size();
+        k_set_beta_units<<<grid_for(nu, m->ctx->sms), kBlock, 0, s>>>(nu, m->d_uelem, beta_dev, dt2,
+                                                                      const_cast<float *>(d.ubd));
+    }
     CK(cudaGetLastError());
     m->dt2 = dt2;
     return diag ? diag_update_device(m, s) : PS_OK;
@@ -811,7 +861,15 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
 // 15-55% slower than 256-thread blocks capped at 64 registers.)
 static void launch_k1_f32(ps_mesh *m, const Cg2Args<float> &a, cudaStream_t s) {
     const MeshDev &d = m->dev;
-    if (m->k1_pre) {
+    if (m->use_units) {
+        if (m->unit_threads == 128) {
+            if (d.lumped) k_cg2_units<true, 128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
+        } else {
+            if (d.lumped) k_cg2_units<true, 256><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 256><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
+        }
+    } else if (m->k1_pre) {
         if (d.dim == 2) k_cg2_chunks<2, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
         else k_cg2_chunks<3, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
     } else {
@@ -1228,6 +1286,44 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
 }
 
 // ---------------------------------------------------------------- debug hooks (host only)
+extern "C" int ps_debug_cg_apply(ps_mesh *m, const void *x, void *y, double *pap, void *stream) {
+    if (!m || !x || !y || x == y) return PS_EINVAL;
+    if (!m->coeff_ok) return PS_ESTATE;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    CK(cudaSetDevice(m->ctx->device));
+    RC(ensure_workspace(m));
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace &w = m->ws;
+    const int64_t n = m->dev.n_nodes, nu = m->prep.n_nodes;
+    const int g = grid_for(n, m->ctx->sms), gu = grid_for(nu, m->ctx->sms);
+    // p_old = x, r = 0 and beta = 1: the kernel's direction p = D^-1 r + beta p is x itself
+    k_perm_in<float, float><<<g, kBlock, 0, s>>>(n, (const float *)x, w.p32, m->d_old_of_new, m->dev.dirichlet);
+    CK(cudaMemsetAsync(w.r32, 0, m->dev.n_pad * sizeof(float), s));
+    CgState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.beta = 1.0;
+    hs.rz = 1.0;
+    CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    launch_k1_f32(m, cg2_args<float>(m), s);
+    VecArgs<float> va;
+    std::memset(&va, 0, sizeof(va));
+    va.y = w.q32;
+    va.partial = w.part32;
+    k_shared<float, kApply><<<m->grid2, kBlock, 0, s>>>(m->dev, va, 0);
+    k_perm_out<float, float><<<gu, kBlock, 0, s>>>(nu, w.q32, (float *)y, m->d_new_of_old);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&hs, w.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, m->ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        cudaMemset(m->ctx->d_err, 0, sizeof(int));
+        return PS_ETIMEOUT;
+    }
+    if (pap) *pap = hs.pq;
+    return PS_OK;
+}
+
 extern "C" int ps_mesh_get_jacobi(const ps_mesh *m, int precision, void *dinv_host, void *stream) {
     if (!m || !dinv_host || (precision != PS_F32 && precision != PS_F64)) return PS_EINVAL;
     if (!m->coeff_ok) return PS_ESTATE;

@@ -45,13 +45,14 @@ class PressureError(RuntimeError):
 
 class ps_mesh_opts(C.Structure):
     _fields_ = [("chunk_elems", C.c_int32), ("chunk_nodes_max", C.c_int32), ("pipeline", C.c_int32),
-                ("update_blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("update_blocks_per_sm", C.c_int32), ("operator_kernel", C.c_int32),
+                ("operator_threads", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class ps_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int64), ("mode", C.c_int32), ("precond", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("graph_iters", C.c_int32),
-                ("engine", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("engine", C.c_int32), ("grid_spin_limit", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class ps_projection_opts(C.Structure):
@@ -141,6 +142,7 @@ SIGNATURES = {
     "ps_server_get_stats": (C.c_int, [_vp, C.POINTER(ps_server_stats)]),
     "ps_profile_kernel": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_double)]),
     "ps_mesh_get_jacobi": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "ps_debug_cg_apply": (C.c_int, [_vp, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "ps_debug_prepare": (C.c_int, [C.c_int, _i64, _vp, _i64, _vp, _vp, _vp, C.POINTER(ps_mesh_opts),
                                    C.POINTER(ps_mesh_stats)]),
 }
@@ -216,7 +218,7 @@ def ps_ctx_bytes_in_use(ctx):
 
 
 def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, pipeline=0,
-                   update_blocks_per_sm=0, periodic=None):
+                   update_blocks_per_sm=0, periodic=None, operator_kernel=0, operator_threads=0):
     """periodic: optional [n_nodes] master map (ps_mesh_upload_periodic)."""
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
@@ -224,7 +226,8 @@ def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_
     pd = None
     if dirichlet is not None:
         dirichlet, pd = _host(dirichlet, np.uint8)
-    o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline, update_blocks_per_sm)
+    o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline, update_blocks_per_sm, operator_kernel,
+                     operator_threads)
     h = _vp()
     if periodic is None:
         _check(_lib.ps_mesh_upload(ctx, int(dim), n, pc, conn.shape[0], pe, pd, C.byref(o), C.byref(h)),
@@ -436,6 +439,15 @@ def ps_mesh_get_jacobi(mesh, precision=PS_F64, stream=None):
     _check(_lib.ps_mesh_get_jacobi(mesh, int(precision), out.ctypes.data_as(C.c_void_p), _stream(stream)),
            "ps_mesh_get_jacobi")
     return out
+
+
+def ps_debug_cg_apply(mesh, x_dev, y_dev, stream=None):
+    """One pass of the FP32 CG operator kernel with direction x: fills y = A x
+    (device float tensors) and returns x^T A x as the kernel accumulates it."""
+    pap = C.c_double()
+    _check(_lib.ps_debug_cg_apply(mesh, _dev(x_dev), _dev(y_dev), C.byref(pap), _stream(stream)),
+           "ps_debug_cg_apply")
+    return float(pap.value)
 
 
 def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, periodic=None):
