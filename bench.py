@@ -71,6 +71,9 @@ def parse():
                          "baseline), for a profiler's launch list; the line then has no roofline or e2e")
     ap.add_argument("--chunk", type=int, default=0, help="elements per chunk (0 = library default)")
     ap.add_argument("--pipeline", type=int, default=0, help="persistent double-buffered operator kernel")
+    ap.add_argument("--operator-kernel", type=int, default=0,
+                    help="FP32 CG operator kernel of 3D meshes: 0 auto, 1 one patch per thread, 2 paired patches")
+    ap.add_argument("--operator-threads", type=int, default=0, help="threads per block of the paired-patch kernel")
     ap.add_argument("--engine", default="auto", choices=["auto", "graph", "persistent", "fused"])
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "c1", "c2", "c3", "c4", "c5", "projection", "periodic", "eos"],
@@ -389,7 +392,8 @@ def run_ours(args):
     case = S.make_c2(args.n)
     ctx = P.ps_ctx_create(local)
     m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
-                         pipeline=args.pipeline)
+                         pipeline=args.pipeline, operator_kernel=args.operator_kernel,
+                         operator_threads=args.operator_threads)
     P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()
@@ -592,14 +596,17 @@ def run_single(args, which):
     P.ps_ctx_destroy(ctx)
 
 
-def batch_chunk(args, autotune, P, ctx, cases):
-    """Chunk size for the batched / served workloads: --chunk if given, else the
-    batch autotuner on every 8th case (outside any timed region)."""
+def batch_tuning(args, autotune, P, ctx, cases):
+    """Chunk size, persistent-kernel threads per block and task order for the
+    batched / served workloads: --chunk if given (library defaults for the
+    rest), else the batch autotuner on every 8th case (outside any timed
+    region).  Returns (chunk_elems, {"batch_threads", "batch_order"}, record)."""
     if args.chunk or args.no_tune:
-        return args.chunk, None
+        return args.chunk, {"batch_threads": 0, "batch_order": 0}, None
     sample = cases[::8]
     res = autotune.tune_batch(P, ctx, sample)
-    return res["chunk_elems"], {"sample_meshes": len(sample), "table": res["table"]}
+    return (res["chunk_elems"], {"batch_threads": res["batch_threads"], "batch_order": res["batch_order"]},
+            {"sample_meshes": len(sample), "table": res["table"]})
 
 
 def bench_batch(args, P, S, autotune, torch):
@@ -610,7 +617,7 @@ def bench_batch(args, P, S, autotune, torch):
     meshes, bs, xs, n_free = [], [], [], []
     t0 = time.perf_counter()
     cases = [S.make_batch_case(i, lo=2e3 * args.size_scale, hi=2e5 * args.size_scale) for i in range(args.meshes)]
-    chunk, tune = batch_chunk(args, autotune, P, ctx, cases)
+    chunk, knobs, tune = batch_tuning(args, autotune, P, ctx, cases)
     for c in cases:
         m = P.ps_mesh_upload(ctx, c.dim, c.coords, c.conn, c.dirichlet, chunk_elems=chunk)
         P.ps_coeff_set(m, c.alpha, c.beta, c.dt2)
@@ -619,7 +626,7 @@ def bench_batch(args, P, S, autotune, torch):
         xs.append(torch.zeros(c.n_nodes, dtype=torch.float64, device="cuda"))
         n_free.append(c.n_free)
     setup_s = time.perf_counter() - t0
-    opts = P.make_opts(tol=1e-10)
+    opts = P.make_opts(tol=1e-10, **knobs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
@@ -665,7 +672,7 @@ def bench_batch(args, P, S, autotune, torch):
            "oracle_check": check,
            "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
            "iters_inner_max": int(max(inf.iters_inner for inf in infos)),
-           "chunk_elems": chunk, "chunk_tuning": tune, "setup_s": setup_s, "gpu_launches": launches,
+           "chunk_elems": chunk, **knobs, "tuning": tune, "setup_s": setup_s, "gpu_launches": launches,
            "l2": "flushed between steps (256 MB write)", "clocks": clk}
     for m in meshes:
         P.ps_mesh_free(m)
@@ -718,7 +725,7 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
     meshes = []
     cases = [S.make_served_case(c, lo=5e3 * args.size_scale, hi=2e6 * args.size_scale, median=1e5 * args.size_scale)
              for c in range(args.cases)]
-    chunk, tune = batch_chunk(args, autotune, P, ctx, cases)
+    chunk, knobs, tune = batch_tuning(args, autotune, P, ctx, cases)
     for cs in cases:
         m = P.ps_mesh_upload(ctx, cs.dim, cs.coords, cs.conn, cs.dirichlet, chunk_elems=chunk)
         P.ps_coeff_set(m, cs.alpha, cs.beta, cs.dt2)
@@ -732,7 +739,8 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
         """rate None = closed loop (each case submits its next step when the last completes);
         budget: the server's HBM cap on in-flight solver workspaces (0 = the context's)."""
         steps = steps or args.case_steps
-        srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32, hbm_budget_bytes=budget)
+        srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32, hbm_budget_bytes=budget,
+                                 opts=P.make_opts(tol=1e-10, **knobs))
         ids = [P.ps_server_add_case(srv, m) for m in meshes]
         state = [(c.beta.copy(), c.b.copy()) for c in cases]
         lat, qwait, req_size, done_iters, worst = [], [], [], 0, 0.0
@@ -860,7 +868,7 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
            "per_bucket": sat["per_bucket"], "max_rel_res": sat["max_rel_res"], "oracle_check": sat["oracle_check"],
            "served_vs_fp64_single_solves_per_s": sat["solves_per_s"] / singles[0]["solves_per_s"],
-           "chunk_elems": chunk, "chunk_tuning": tune, "runs": runs, "single_solves": singles,
+           "chunk_elems": chunk, **knobs, "tuning": tune, "runs": runs, "single_solves": singles,
            "clocks": sat["clocks"]}
     for m in meshes:
         P.ps_mesh_free(m)
@@ -951,7 +959,8 @@ def run_headline(args):
     case = S.make_c3(args.n or 160)
     ctx = P.ps_ctx_create(local)
     m = P.ps_mesh_upload(ctx, 3, case.coords, case.conn, case.dirichlet, chunk_elems=args.chunk,
-                         pipeline=args.pipeline)
+                         pipeline=args.pipeline, operator_kernel=args.operator_kernel,
+                         operator_threads=args.operator_threads)
     P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
     stats = P.ps_mesh_get_stats(m)
     stream = torch.cuda.current_stream()

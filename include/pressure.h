@@ -125,7 +125,13 @@ typedef struct {
                              /* barrier before it gives up and the call returns     */
                              /* PS_ETIMEOUT (batched, persistent and served solves; */
                              /* 0 = 2^26 polls, each at least 32 ns apart)          */
-    int32_t reserved[4];
+    int32_t batch_threads;   /* batched / persistent / served solves: threads per   */
+                             /* block of the persistent kernel (0 = 256, 128, 256)  */
+    int32_t batch_order;     /* their task order per pass: 0 = the (mesh, chunk)    */
+                             /* list in mesh order, static round robin over blocks; */
+                             /* 1 = only the chunks of meshes still running,        */
+                             /* compacted each pass, static round robin             */
+    int32_t reserved[2];
 } ps_solve_opts;
 
 #define PS_ENGINE_AUTO        0
@@ -531,6 +537,9 @@ int ps_debug_cg_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, double *pap
  *   PS_KERNEL_CG1_F32    FP32 fused one-reduction CG pass (node updates of x, r, s, p,
  *                        u = D^-1 r, w = A u, gamma, delta, rho): the whole inner
  *                        iteration of the default mixed-precision solve
+ *   PS_KERNEL_HALO_F32   the paired-patch kernel's halo gather ((D^-1 r, p) of every
+ *                        shared node into its chunks' slots), the third kernel of
+ *                        that iteration (nothing runs for the other kernel variants)
  * Errors: PS_EINVAL, PS_ESTATE (coefficients not set). */
 #define PS_KERNEL_CG_F32     0
 #define PS_KERNEL_UPDATE_F32 1
@@ -538,6 +547,7 @@ int ps_debug_cg_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, double *pap
 #define PS_KERNEL_RESID_F64  3
 #define PS_KERNEL_CG_F64     4
 #define PS_KERNEL_CG1_F32    5
+#define PS_KERNEL_HALO_F32   6
 int ps_profile_kernel(ps_mesh *mesh, int which, int reps, void *stream, double *avg_ms);
 
 #ifdef __cplusplus

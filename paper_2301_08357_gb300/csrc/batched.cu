@@ -77,6 +77,7 @@ struct PcgArgs {
     int *err;
     int max_it;
     uint32_t spin_limit;           // polls of the grid barrier before it gives up
+    int order;                     // task order: 0 = (mesh, chunk) list, 1 = running meshes' chunks, compacted
     SmemLayout L;                  // chunk layout; the scalar cache follows at L.total
 };
 
@@ -107,6 +108,11 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
     const ChunkSmem<float> S = chunk_smem<float>(smem, A.L);
     float2 *c_ab = reinterpret_cast<float2 *>(smem + A.L.total);          // [n_meshes]
     int *c_par = reinterpret_cast<int *>(c_ab + A.n_meshes);               // [n_meshes], -1 = idle
+    // compacted order: chunks of each mesh (cached) and the first compacted
+    // task of each mesh this pass (running meshes only), + scan scratch
+    int *c_nch = c_par + A.n_meshes;                                       // [n_meshes]
+    int *c_off = c_nch + A.n_meshes;                                       // [n_meshes + 1]
+    int *c_scan = c_off + A.n_meshes + 1;                                  // [blockDim]
     __shared__ int s_stop;
     __shared__ bool s_last;
     // the current task's mesh descriptor and buffers, copied into shared
@@ -124,6 +130,8 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
         // the grid barrier
         s_stop = ld_acquire_i32(A.active_cnt) <= 0;
     }
+    if (A.order == 1)
+        for (int i = threadIdx.x; i < A.n_meshes; i += blockDim.x) c_nch[i] = A.meshes[i].d.n_chunks;
     __syncthreads();
     uint32_t phase = 0;
     bool failed = false;
@@ -135,8 +143,44 @@ __global__ void __launch_bounds__(256) k_batch_pcg(PcgArgs A) {
             c_ab[i] = make_float2((float)__ldcg(&st->in.alpha), (float)__ldcg(&st->in.beta));
         }
         __syncthreads();
-        for (int t = blockIdx.x; t < A.n_t1; t += gridDim.x) {
-            const int2 tk = A.t1[t];
+        int n_tasks = A.n_t1;
+        if (A.order == 1) {
+            // exclusive scan of the running meshes' chunk counts: thread t
+            // sums a contiguous range of meshes, the block scans the sums
+            const int per = (A.n_meshes + blockDim.x - 1) / blockDim.x;
+            const int i0 = threadIdx.x * per, i1 = min(A.n_meshes, i0 + per);
+            int sum = 0;
+            for (int i = i0; i < i1; ++i) sum += c_par[i] >= 0 ? c_nch[i] : 0;
+            c_scan[threadIdx.x] = sum;
+            __syncthreads();
+            for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+                const int v = threadIdx.x >= (unsigned)d ? c_scan[threadIdx.x - d] : 0;
+                __syncthreads();
+                c_scan[threadIdx.x] += v;
+                __syncthreads();
+            }
+            int off = c_scan[threadIdx.x] - sum;
+            for (int i = i0; i < i1; ++i) {
+                c_off[i] = off;
+                off += c_par[i] >= 0 ? c_nch[i] : 0;
+            }
+            if (threadIdx.x == blockDim.x - 1) c_off[A.n_meshes] = c_scan[threadIdx.x];
+            __syncthreads();
+            n_tasks = c_off[A.n_meshes];
+        }
+        for (int t = blockIdx.x; t < n_tasks; t += gridDim.x) {
+            int2 tk;
+            if (A.order == 1) {
+                // the running mesh whose compacted range holds task t
+                int lo = 0, hi = A.n_meshes;       // c_off[lo] <= t < c_off[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (c_off[mid] <= t) lo = mid; else hi = mid;
+                }
+                tk = make_int2(lo, t - c_off[lo]);
+            } else {
+                tk = A.t1[t];
+            }
             const int par = c_par[tk.x];
             if (par < 0) continue;                 // block-uniform
             const BMesh &M = A.meshes[tk.x];
@@ -459,8 +503,17 @@ static SmemLayout max_layout(const std::vector<ps_mesh *> &meshes, bool fp64) {
                 : make_layout(4, sizeof(NodeF), max_loc, max_patch, max_inc, max_sh);
 }
 
-int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, BatchPlan &plan) {
+int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, const ps_solve_opts &o,
+                     BatchPlan &plan) {
     batch_plan_free(plan);
+    if ((o.batch_threads != 0 && o.batch_threads != 128 && o.batch_threads != 256) || o.batch_order < 0 ||
+        o.batch_order > 1) {
+        ps_set_last_error("batch: batch_threads must be 0, 128 or 256 and batch_order 0 or 1");
+        return PS_EINVAL;
+    }
+    plan.threads = o.batch_threads ? o.batch_threads : 256;
+    plan.order = o.batch_order;
+    plan.spin_limit = o.grid_spin_limit > 0 ? (uint32_t)o.grid_spin_limit : kGridSpinLimit;
     if (n < 1 || n > kMaxBatch) {
         ps_set_last_error("batch: between 1 and 4096 meshes per batch");
         return PS_EINVAL;
@@ -536,15 +589,19 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
     std::memset(plan.h_st, 0, (size_t)n * sizeof(BState));
     plan.L32 = max_layout(plan.meshes, false);
     plan.L64 = max_layout(plan.meshes, true);
-    plan.pcg_smem = plan.L32.total + (uint32_t)n * (sizeof(float2) + sizeof(int));
+    // scalar cache (alpha, beta; parity) per mesh, then the compacted order's
+    // chunk counts, offsets and scan scratch
+    plan.pcg_smem = plan.L32.total + (uint32_t)n * (sizeof(float2) + sizeof(int)) +
+                    (uint32_t)(2 * n + 1 + plan.threads) * sizeof(int);
     int per_sm = 0;
-    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, 256, plan.pcg_smem));
+    rc = cuda_rc(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, plan.threads, plan.pcg_smem));
     if (rc != PS_OK) return rc;
     if (per_sm < 1) {
         ps_set_last_error("batch: shared-memory layout too large for the persistent kernel");
         return PS_EINVAL;
     }
-    plan.grid_pcg = std::max(1, std::min(ctx->sms * std::min(per_sm, 4), std::max(plan.n_t1, 1)));
+    const int cap = plan.threads == 128 ? 8 : 4;   // resident blocks per SM used
+    plan.grid_pcg = std::max(1, std::min(ctx->sms * std::min(per_sm, cap), std::max(plan.n_t1, 1)));
     return PS_OK;
 }
 
@@ -602,12 +659,13 @@ static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
     A.err = plan.ctx->d_err;
     A.max_it = plan.epoch_iters;
     A.spin_limit = plan.spin_limit;
+    A.order = plan.order;
     A.L = plan.L32;
     void *args[] = {&A};
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(plan.grid_pcg);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3(plan.threads);
     cfg.dynamicSmemBytes = plan.pcg_smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -685,13 +743,12 @@ int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev
     auto t0 = std::chrono::steady_clock::now();
     BatchPlan plan;
     const int epoch = o.graph_iters > 0 ? o.graph_iters * 8 : 256;
-    int rc = batch_plan_build(ctx, meshes, n, epoch, plan);
+    int rc = batch_plan_build(ctx, meshes, n, epoch, o, plan);
     if (rc == PS_OK) {
         for (int i = 0; i < n; ++i) batch_arm(plan, i, b_dev[i], x_dev[i], o);
         rc = batch_upload_states(plan, s);
     }
     if (rc == PS_OK && o.graph_iters < 0) plan.graph_ok = false;
-    plan.spin_limit = o.grid_spin_limit > 0 ? (uint32_t)o.grid_spin_limit : kGridSpinLimit;
     // every epoch advances each unfinished mesh by at least one phase step;
     // bound the number of epochs by the iteration and outer-step caps
     long long max_epochs = 8;

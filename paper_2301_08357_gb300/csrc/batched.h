@@ -83,6 +83,8 @@ struct BatchPlan {
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = true;
     uint32_t spin_limit = kGridSpinLimit;   // grid-barrier polls before giving up
+    int threads = 256;                      // threads per block of the persistent kernel
+    int order = 0;                          // task order (PcgArgs::order)
 };
 
 // Per-mesh batch workspace beyond ps_mesh::ws (FP64 reduction partials).
@@ -94,7 +96,8 @@ struct BatchMeshWs {
 
 // Build the plan for `n` distinct meshes of one context (workspaces allocated
 // on first use); states start in kPhIdle.
-int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, BatchPlan &plan);
+int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, const ps_solve_opts &o,
+                     BatchPlan &plan);
 void batch_plan_free(BatchPlan &plan);
 // Start a solve of mesh i: caller-numbering device vectors b (read) and x
 // (first guess in, solution out), options; state -> kPhPrepare.  Takes effect

@@ -79,6 +79,9 @@ struct Cg2Args {
     PT *z2;            // [2][g3]: block shares of rz and rr
     int g3;            // grid of K2 (and of the start kernel)
     CgState *st;
+    // paired-patch operator kernel only (else null): per chunk-major shared
+    // slot, (D^-1 r, p) of the slot's node, gathered after K2 for the next K1
+    float2 *halo;
 };
 
 // K1: one block per chunk.  PRE: fetch the element phase's beta*dt^2 and the

@@ -42,6 +42,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (the range is trimmed inward to
+// 16-byte boundaries, so nothing outside it is touched).
+__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes) {
+    const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > b)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
+}
+
 struct P3 {
     float2 x, y, z;
 };
@@ -189,6 +197,7 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     NodeF *s_node = reinterpret_cast<NodeF *>(smem + L.node);
     float *s_val = reinterpret_cast<float *>(smem + L.val);
     uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
+    int32_t *s_shd = reinterpret_cast<int32_t *>(smem + L.shd);
     float *s_con = reinterpret_cast<float *>(smem + L.contrib);
     float2 *s_dot = reinterpret_cast<float2 *>(smem + L.dot);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -209,9 +218,11 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     if (tid == 0) {
         const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
         const uint32_t b_inc = (uint32_t)cu.uinc_n * 2u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_inc);
+        const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
+        mbar_arrive_expect_tx(s_bar, b_node + b_inc + b_shd);
         bulk_g2s(s_node, m.node32 + cd.node_off, b_node, s_bar);
         bulk_g2s(s_inc, m.uinc + cu.uinc_off, b_inc, s_bar);
+        if (b_shd) bulk_g2s(s_shd, m.sh_dest + cd.sh_off, b_shd, s_bar);
     }
     const float beta = s_beta;
     const int n_loc = cd.n_loc, n_int = cd.n_int;
@@ -224,31 +235,50 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     // store: the stores to p could alias them); no Dirichlet mask is needed
     // (D^-1 = 0 and r = 0 there and p starts at 0)
     for (int l0 = tid; l0 < n_loc; l0 += 4 * NT) {
-        int gg[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int l = l0 + k * NT;
-            gg[k] = l < n_int ? cd.int_begin + l : (l < n_loc ? __ldg(m.sh_ids + cd.sh_off + (l - n_int)) : -1);
-        }
+        // interior nodes: D^-1, r, p contiguous from int_begin; shared
+        // nodes: (D^-1 r, p) from the chunk's contiguous halo slots
         float dv[4], rv[4], pv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+            const int l = l0 + k * NT;
             dv[k] = rv[k] = pv[k] = 0.f;
-            if (gg[k] >= 0) {
-                dv[k] = a.dinv[gg[k]];
-                rv[k] = a.r[gg[k]];
-                pv[k] = a.p[gg[k]];
+            if (l < n_int) {
+                const int g = cd.int_begin + l;
+                dv[k] = __ldg(a.dinv + g);
+                rv[k] = a.r[g];
+                pv[k] = a.p[g];
+            } else if (l < n_loc) {
+                const float2 h = a.halo[cd.sh_off + (l - n_int)];
+                dv[k] = 1.f;
+                rv[k] = h.x;
+                pv[k] = h.y;
             }
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int l = l0 + k * NT;
-            if (gg[k] >= 0) {
+            if (l < n_loc) {
+                // shared nodes: fma(beta, p, 1 * z) = fma(beta, p, z), the value K2 stores
                 const float v = cg_dir(dv[k], rv[k], beta, pv[k]);
                 s_val[l] = v;
-                if (l < n_int) a.p[gg[k]] = v;
+                if (l < n_int) a.p[cd.int_begin + l] = v;
             }
         }
+    }
+    // the data of a chunk that a block launched later will process, into L2
+    if (tid == 0 && m.prefetch_ahead > 0 && blockIdx.x + m.prefetch_ahead < (unsigned)m.n_chunks) {
+        const int fc = blockIdx.x + m.prefetch_ahead;
+        const ChunkDesc fd = m.chunks[fc];
+        const ChunkUnits fu = m.chunks_u[fc];
+        l2_prefetch(m.node32 + fd.node_off, (size_t)fd.n_loc * sizeof(NodeF));
+        l2_prefetch(m.uinc + fu.uinc_off, (size_t)fu.uinc_n * 2);
+        l2_prefetch(m.urec + (size_t)fu.unit_off * kURecWords, (size_t)fu.n_unit * kURecWords * 4);
+        l2_prefetch(m.ubd + (size_t)fu.unit_off * kPatchMax * 2, (size_t)fu.n_unit * kPatchMax * 8);
+        l2_prefetch(a.dinv + fd.int_begin, (size_t)fd.n_int * 4);
+        l2_prefetch(a.r + fd.int_begin, (size_t)fd.n_int * 4);
+        l2_prefetch(a.p + fd.int_begin, (size_t)fd.n_int * 4);
+        l2_prefetch(a.halo + fd.sh_off, (size_t)fd.n_sh * 8);
+        l2_prefetch(m.sh_dest + fd.sh_off, (size_t)fd.n_sh * 4);
     }
     uint32_t ph = 0;
     {
@@ -299,7 +329,7 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
         if (l < n_int)
             a.q[cd.int_begin + l] = s;
         else
-            a.partial[__ldg(m.sh_dest + cd.sh_off + (l - n_int))] = s;
+            a.partial[s_shd[l - n_int]] = s;
     }
     // ---- the chunk's share of p.Ap: one warp sums the threads' partials in order
     s_dot[tid] = make_float2(acc.hi, acc.lo);
@@ -348,6 +378,21 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
         } else {
             st->alpha = st->rz / pq;
         }
+    }
+}
+
+// The halo of the paired-patch kernel: every chunk-major shared slot j (node
+// i = sh_ids[j]) gets (D^-1_i r_i, p_i) -- after each update kernel (the next
+// operator pass reads it contiguously per chunk), at the start of a CG run
+// and before ps_debug_cg_apply.  Pads (sh_ids = -1) are skipped.
+static __global__ void k_halo_gather(int64_t n_slots, const int32_t *__restrict__ sh_ids, const float *__restrict__ r,
+                                     const float *__restrict__ p, const float *__restrict__ dinv,
+                                     float2 *__restrict__ halo, const CgState *st) {
+    if (st && ld_flag(&st->done)) return;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_slots;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int i = __ldg(sh_ids + j);
+        if (i >= 0) halo[j] = make_float2(__fmul_rn(__ldg(dinv + i), r[i]), p[i]);
     }
 }
 

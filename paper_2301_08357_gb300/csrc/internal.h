@@ -41,6 +41,7 @@ struct Workspace {
     float *x32b = nullptr, *r32b = nullptr, *p32b = nullptr, *q32b = nullptr;
     float *s32a = nullptr, *s32b = nullptr, *part32b = nullptr;
     double *dots1 = nullptr;
+    float2 *halo32 = nullptr;   // paired-patch CG: (D^-1 r, p) per chunk-major shared slot
     CgState *st = nullptr;
     CgState *h_st = nullptr;
     float *one32 = nullptr;
@@ -107,7 +108,7 @@ struct ps_mesh {
     int k1_variant = 0;                // ps_mesh_opts::operator_kernel
     bool k1_pre = false;               // FP32 operator kernel variant (beta prefetch)
     bool use_units = false;            // FP32 CG operator kernel on paired patches (3D)
-    int unit_threads = 256;            // its threads per block (ps_mesh_opts::operator_threads)
+    int unit_threads = 128;            // its threads per block (ps_mesh_opts::operator_threads)
     int32_t *d_uelem = nullptr;        // element of each (unit, element, half) slot, -1 none
     bool coeff_ok = false, alpha_set = false;
     bool alpha_newton = false;         // alpha last set by the general-EOS Newton iteration

@@ -27,10 +27,11 @@ struct SmemLayout {
 };
 
 // Shared memory of the paired-patch CG operator kernel (cg2u.cuh): node
-// records | values | incidence segment | contributions (+ the zero slot) |
-// per-thread dot partials | mbarrier.
+// records | values | incidence segment | partial-sum destinations of the
+// shared nodes | contributions (+ the zero slot) | per-thread dot partials |
+// mbarrier.
 struct UnitSmem {
-    uint32_t node, val, inc, contrib, dot, bar, total;
+    uint32_t node, val, inc, shd, contrib, dot, bar, total;
 };
 
 struct MeshDev {
@@ -58,6 +59,7 @@ struct MeshDev {
     const float *ubd;        // [unit_total * kPatchMax * 2] beta*dt^2/6 per (unit, element, half)
     const uint16_t *uinc;    // incidence segments
     UnitSmem smu;
+    int prefetch_ahead;      // chunks between a block and the chunk whose data it prefetches into L2
 };
 
 // Scalars of one CG run, kept on the device.

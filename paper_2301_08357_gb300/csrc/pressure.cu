@@ -452,11 +452,24 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         U.node = take((uint64_t)pm.max_loc * sizeof(NodeF));
         U.val = take((uint64_t)pm.max_loc * 4);
         U.inc = take((uint64_t)pm.max_uinc * 2);
+        U.shd = take((uint64_t)round_up(pm.max_sh, kShPad) * 4);
         U.contrib = take((uint64_t)pm.max_unit * 2 * kUnitSlots * 4 + 16);
         U.dot = take((uint64_t)kChunkThreads * 8);
         U.bar = take(8);
         U.total = off;
         m->use_units = U.total <= 200 * 1024;
+        if (m->use_units) {
+            // L2 prefetch distance: the chunks resident at once (a block
+            // prefetches the data of the block about one wave after it)
+            int per_sm = 0;
+            cudaError_t oe = m->unit_threads == 128
+                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 128>, 128,
+                                                                                 U.total)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 256>, 256,
+                                                                                 U.total);
+            cudaGetLastError();
+            d.prefetch_ahead = (oe == cudaSuccess && per_sm > 0) ? per_sm * c->sms : 0;
+        }
     }
     d.err = c->d_err;
     d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
@@ -476,7 +489,9 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
                                                                                       kBlock, m->pipe_L0.total);
         if (oe != cudaSuccess || m->pipe_L0.total > 200 * 1024) per_sm = 0;
         cudaGetLastError();
-        m->pipe_grid = (per_sm > 0 && m->pipeline) ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm) : 0;
+        m->pipe_grid = (per_sm > 0 && m->pipeline && !m->use_units)
+                           ? (int)std::min<int64_t>(pm.n_chunks, (int64_t)c->sms * per_sm)
+                           : 0;
     }
     {
         // FP32 operator kernel: prefetch beta*dt^2 into registers when that
@@ -818,6 +833,7 @@ int ensure_workspace(ps_mesh *m) {
     WA(s32b, float, np);
     WA(part32b, float, sh);
     WA(dots1, double, 3 * m->dev.n_chunks + 8);
+    if (m->use_units) WA(halo32, float2, sh);
 #undef WA
     if (rc != PS_OK) {
         dfree_all(c, w.allocs);
@@ -853,6 +869,7 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
     a.z2 = (typename PartOf<T>::type *)w.z3;
     a.g3 = m->g3c;
     a.st = w.st;
+    a.halo = (sizeof(T) == 4 && m->use_units) ? w.halo32 : nullptr;
     return a;
 }
 
@@ -937,6 +954,12 @@ static int enqueue_cg_iters(ps_mesh *m, int iters, bool fused, cudaStream_t s) {
             k_cg2_chunks<3, T><<<m->dev.n_chunks, kBlock, L.total, s>>>(m->dev, a);
         k_cg2_update<T><<<m->g3c, kBlock, 0, s>>>(m->dev, a);
         m->launches += 2;
+        if (sizeof(T) == 4 && a.halo) {
+            const Cg2Args<float> &af = reinterpret_cast<const Cg2Args<float> &>(a);
+            k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
+                m->prep.sh_total, m->dev.sh_ids, af.r, af.p, af.dinv, af.halo, af.st);
+            m->launches += 1;
+        }
         CK(cudaGetLastError());
     }
     return PS_OK;
@@ -950,7 +973,7 @@ static int run_cg_until_done(ps_mesh *m, int gi, bool jac, bool fused, cudaStrea
     Workspace &w = m->ws;
     fused = fused && sizeof(T) == 4;
     const int kind = (sizeof(T) == 4 ? 0 : 1) + (jac ? 0 : 2) + (fused ? 4 : 0);
-    const int per_iter = fused ? 1 : 2;
+    const int per_iter = fused ? 1 : (sizeof(T) == 4 && m->use_units ? 3 : 2);
     if (gi <= 0) {
         const int batch = 15;
         for (;;) {
@@ -1163,6 +1186,11 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
                 k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, it_k * it_k, 1,
                                                              max_it - used);
                 m->launches += 1;
+                if (a.halo) {
+                    k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
+                        m->prep.sh_total, m->dev.sh_ids, a.r, a.p, a.dinv, a.halo, nullptr);
+                    m->launches += 1;
+                }
             }
             if ((rc = cuda_status(cudaGetLastError())) != PS_OK) break;
             if ((rc = run_cg_until_done<float>(m, gi, jac, fused, s)) != PS_OK) break;
@@ -1304,7 +1332,11 @@ extern "C" int ps_debug_cg_apply(ps_mesh *m, const void *x, void *y, double *pap
     hs.beta = 1.0;
     hs.rz = 1.0;
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
-    launch_k1_f32(m, cg2_args<float>(m), s);
+    const Cg2Args<float> ca = cg2_args<float>(m);
+    if (ca.halo)
+        k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
+            m->prep.sh_total, m->dev.sh_ids, ca.r, ca.p, ca.dinv, ca.halo, nullptr);
+    launch_k1_f32(m, ca, s);
     VecArgs<float> va;
     std::memset(&va, 0, sizeof(va));
     va.y = w.q32;
@@ -1382,7 +1414,7 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
 
 // ---------------------------------------------------------------- kernel timing
 extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, double *avg_ms) {
-    if (!m || !avg_ms || reps < 1 || which < 0 || which > 5) return PS_EINVAL;
+    if (!m || !avg_ms || reps < 1 || which < 0 || which > 6) return PS_EINVAL;
     if (!m->coeff_ok) return PS_ESTATE;
     std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
@@ -1456,6 +1488,13 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
             case 5:
                 launch_cg1(m, cg1_vec(m), s);
                 break;
+            case 6: {
+                const Cg2Args<float> a = cg2_args<float>(m);
+                if (a.halo)
+                    k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
+                        m->prep.sh_total, d.sh_ids, a.r, a.p, a.dinv, a.halo, nullptr);
+                break;
+            }
         }
     };
     one();  // warm-up

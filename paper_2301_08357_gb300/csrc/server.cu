@@ -183,8 +183,8 @@ static void worker_main(ps_server *s) {
                 if (cur.empty()) {
                     batch_plan_free(s->plan);
                 } else {
-                    rc = batch_plan_build(s->ctx, ms.data(), (int)ms.size(), s->opts.epoch_iters, s->plan);
-                    if (s->opts.opts.grid_spin_limit > 0) s->plan.spin_limit = (uint32_t)s->opts.opts.grid_spin_limit;
+                    rc = batch_plan_build(s->ctx, ms.data(), (int)ms.size(), s->opts.epoch_iters, s->opts.opts,
+                                          s->plan);
                     for (size_t k = 0; k < cur.size() && rc == PS_OK; ++k) {
                         Case &c = s->cases[cur[k]];
                         batch_arm(s->plan, (int)k, c.b_dev, c.x_dev, s->opts.opts);

@@ -52,7 +52,8 @@ class ps_mesh_opts(C.Structure):
 class ps_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int64), ("mode", C.c_int32), ("precond", C.c_int32),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("graph_iters", C.c_int32),
-                ("engine", C.c_int32), ("grid_spin_limit", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("engine", C.c_int32), ("grid_spin_limit", C.c_int32), ("batch_threads", C.c_int32),
+                ("batch_order", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class ps_projection_opts(C.Structure):
@@ -422,6 +423,7 @@ def ps_server_get_stats(srv):
 
 PS_KERNEL_CG_F32, PS_KERNEL_UPDATE_F32, PS_KERNEL_APPLY_F32, PS_KERNEL_RESID_F64, PS_KERNEL_CG_F64 = 0, 1, 2, 3, 4
 PS_KERNEL_CG1_F32 = 5
+PS_KERNEL_HALO_F32 = 6
 
 
 def ps_profile_kernel(mesh, which, reps=20, stream=None):

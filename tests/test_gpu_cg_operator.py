@@ -157,3 +157,61 @@ def test_cg_operator_full_size_c3_sampled_rows(env):
         assert abs(pap - float(xs @ ax)) <= TOL * bound
     finally:
         P.ps_mesh_free(m)
+
+
+SOLVES = [
+    ("c2_12", lambda: S.make_c2(12), 0, False),
+    ("c3_12_stiff_warm", lambda: S.make_c3(12), 0, False),
+    ("c2_10_shuffled_chunk77", lambda: S.shuffle_case(S.make_c2(10), seed=5), 77, False),
+    ("c2_9_lumped", lambda: S.make_c2(9), 0, True),
+    ("periodic_3d_8", lambda: S.make_periodic_case(3, 8), 0, False),
+]
+
+
+@pytest.mark.parametrize("name,make,chunk,lumped", SOLVES, ids=[c[0] for c in SOLVES])
+@pytest.mark.parametrize("threads", [128, 256])
+def test_paired_kernel_solves_match_oracle(env, name, make, chunk, lumped, threads):
+    """Mixed-precision two-kernel solves with the paired-patch operator kernel
+    (its update kernel then keeps the shared nodes' inputs in the chunk-major
+    halo): the oracle's residual gate at 1e-10, the error gate at 1e-13, and
+    two runs bitwise equal."""
+    P, torch, ctx = env
+    case = make()
+    master = case.extra.get("master")
+    if master is not None:
+        A = PeriodicMatrix(3, case.coords, case.conn, case.dirichlet, master, case.alpha, case.beta, case.dt2)
+        resid = A.residual
+        ref = A.solve(case.b)
+    elif lumped:
+        A = L.LumpedMatrix(case.dim, case.coords, case.conn, case.dirichlet, case.alpha, case.beta, case.dt2)
+        resid = A.residual
+        ref = A.solve(case.b)
+    else:
+        A = oracle.PressureMatrix.from_case(case)
+        resid = A.residual
+        ref = None
+    b = A.apply(case.extra["xstar"]) if "xstar" in case.extra else case.b
+    if ref is None:
+        ref, _, _, _ = A.cg(b, x0_full=case.x0, precond=1, tol=1e-13)
+    m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=chunk,
+                         periodic=master, operator_kernel=2, operator_threads=threads)
+    try:
+        P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
+        if lumped:
+            P.ps_mesh_set_mass(m, P.PS_MASS_LUMPED)
+        bd = torch.as_tensor(b, device="cuda")
+        xs = []
+        for _ in range(2):
+            x = torch.as_tensor(case.x0, device="cuda").clone()
+            st, info = P.ps_pressure_solve(m, bd, x, P.make_opts(mode=1, tol=1e-10, engine=P.PS_ENGINE_GRAPH))
+            assert st == P.PS_OK
+            xs.append(x.cpu().numpy())
+        assert np.array_equal(xs[0], xs[1])
+        assert resid(b, xs[0]) <= 1.05e-10
+        x = torch.as_tensor(case.x0, device="cuda").clone()
+        st, info = P.ps_pressure_solve(m, bd, x, P.make_opts(mode=1, tol=1e-13, max_outer=12,
+                                                            engine=P.PS_ENGINE_GRAPH))
+        xt = x.cpu().numpy()
+        assert np.linalg.norm(xt - ref) <= 1e-9 * np.linalg.norm(ref)
+    finally:
+        P.ps_mesh_free(m)
