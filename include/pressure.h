@@ -89,10 +89,11 @@ typedef struct {
     int32_t update_blocks_per_sm; /* grid of the CG update kernel in blocks per SM */
                              /* (0 = auto)                                          */
     int32_t operator_kernel; /* FP32 CG operator kernel of 3D meshes: 0 = auto     */
-                             /* (one patch per thread), 1 = one patch per thread,  */
-                             /* 2 = paired patches (packed FP32x2 arithmetic)      */
+                             /* (paired patches), 1 = one patch per thread,        */
+                             /* 2 = paired patches (packed FP32x2 arithmetic,      */
+                             /* fixed-point node sums)                              */
     int32_t operator_threads; /* threads per block of the paired-patch kernel:     */
-                             /* 0 = auto (256), 128 or 256                          */
+                             /* 0 = auto (128), 128 or 256                          */
     int32_t reserved[2];
 } ps_mesh_opts;
 
@@ -163,7 +164,9 @@ typedef struct {
     int32_t max_chunk_elems, max_chunk_nodes;
     int64_t solve_bytes;     /* device bytes of this mesh's solver state while a solve
                                 is in flight (the serving loop's admission unit)    */
-    int64_t reserved[3];
+    int64_t operator_kernel; /* FP32 CG operator kernel in use: 1 one patch per
+                                thread, 2 paired patches (ps_mesh_opts)             */
+    int64_t reserved[2];
 } ps_mesh_stats;
 
 /* ---- library --------------------------------------------------------- */

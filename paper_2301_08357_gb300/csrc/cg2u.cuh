@@ -9,13 +9,26 @@
 //   * unit records and beta*dt^2/6 are read straight into registers
 //     (coalesced, before the staging wait); only node records and the
 //     incidence segment are staged into shared memory by bulk copies;
-//   * contributions of a unit are stored as float2 pairs (one 8-byte store
-//     per slot), and node sums run over a degree-sorted, transposed incidence
-//     list (lanes of a warp read consecutive entries, the loop count is the
-//     group's degree: no divergence);
+//   * contributions are added into per-node fixed-point sums in shared
+//     memory (32-bit integer atomics: exact, so the result does not depend on
+//     the order of the additions -- no incidence list, bitwise reproducible);
+//     the chunk's scale comes from a bound on every partial sum (below), and
+//     each node sum is rounded to FP32 once;
+//   * shared nodes' inputs come from a chunk-major halo, contiguous per chunk;
 //   * the p.Ap share is summed by one warp after the node phase (no block
 //     reduction tree).
-// Results are deterministic: every sum has a fixed order.  The element
+// Scale of the fixed-point sums: element matrices are positive semidefinite
+// (mass with alpha >= 0, stiffness with beta > 0), so |A^e_ij| <=
+// sqrt(A^e_ii A^e_jj) <= Dmax, the largest diagonal entry D_jj over the
+// chunk's free nodes (Dirichlet columns carry v = 0); a node in at most
+// n_star of the chunk's elements therefore has every partial sum bounded by
+// B = 4 n_star Dmax vmax, vmax = max |v| over the chunk.  Contributions are
+// scaled by 2^(47 - ceil(log2 B)), so every partial sum stays below 2^47 (a
+// factor of two below the 2^48 the split into two 32-bit sums allows); the
+// resolution, 2^-47 B ~ 7e-15 B, is far below the FP32 rounding of a row for
+// any dynamic range below ~1e8 between the chunk's largest and a row's own
+// scale.  Each node sum is rounded to FP32 at the end (2^24 h + l in one
+// FMA).  Dirichlet rows are masked to 0 whatever their sums.  The element
 // arithmetic is that of patch_eval (device.cuh): with e1 = b - a and
 // d_j = r_j - a, element j of a patch has the cofactor vectors
 // c1 = d_j x d_{j+1}, c2 = -(e1 x d_{j+1}), c3 = e1 x d_j and c0 = -(c1+c2+c3),
@@ -81,13 +94,34 @@ __device__ __forceinline__ PNode pnode(const NodeF *__restrict__ s_node, const f
     return r;
 }
 
-// One unit of M tetrahedra per half: contributions into out[slot] (float2,
-// slot 0 -> a, 1 -> b, 2 + j -> r_j).  rec: the unit record; bd: beta*dt^2/6
-// of element j of each half.
+// Fixed-point node sums: the scaled contribution t (|t| < 2^48, a multiple of
+// the resolution after rounding) is split exactly into t = 2^24 h + l with
+// integers h = rint(t / 2^24) and |l| <= 2^23; h and l are added to the
+// node's two 32-bit integer sums (a node takes at most a few dozen
+// contributions, so neither overflows).  Only 32-bit conversions and integer
+// atomics: all fast paths.
+__device__ __forceinline__ void acc_add1(int *__restrict__ s_acc, int i, float t) {
+    const float hf = rintf(t * (1.0f / 16777216.0f));
+    const float lf = fmaf(-hf, 16777216.0f, t);   // exact: t and 2^24 hf differ by at most 2^23
+    atomicAdd(s_acc + 2 * i, __float2int_rn(hf));
+    atomicAdd(s_acc + 2 * i + 1, __float2int_rn(lf));
+}
+// Add a contribution of each half to its node's sums (scale S); a duplicate
+// second half adds nothing.
+__device__ __forceinline__ void acc_add(int *__restrict__ s_acc, uint32_t w, float2 v, float2 S, bool dup) {
+    const float2 t = p_mul(v, S);
+    acc_add1(s_acc, (int)(w & 0xffffu), t.x);
+    if (!dup) acc_add1(s_acc, (int)(w >> 16), t.y);
+}
+
+// One unit of M tetrahedra per half: contributions of node slots a, b and
+// r_j (j = 0..M) into the fixed-point sums.  rec: the unit record; bd:
+// beta*dt^2/6 of element j of each half; S: the chunk's scale (both halves).
 template <int M, bool LUMP>
 __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
                                           const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
-                                          float2 *__restrict__ out) {
+                                          int *__restrict__ s_acc, float2 S) {
+    const bool dup = (rec[0] & kUnitDup) != 0;
     const PNode A = pnode(s_node, s_val, rec[1]);
     const PNode B = pnode(s_node, s_val, rec[2]);
     const P3 e1 = p3_sub(B.p, A.p);
@@ -144,7 +178,7 @@ __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, cons
         }
         acc_a = p_add(acc_a, o0);
         acc_b = p_add(acc_b, o1);
-        out[2 + j] = p_add(acc_c, o2);
+        acc_add(s_acc, rec[3 + j], p_add(acc_c, o2), S, dup);
         acc_c = o3;
         d0 = d1;
         w0 = w1;
@@ -152,22 +186,22 @@ __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, cons
         t2 = t3;
         q0 = q1;
     }
-    out[2 + M] = acc_c;
-    out[0] = acc_a;
-    out[1] = acc_b;
+    acc_add(s_acc, rec[3 + M], acc_c, S, dup);
+    acc_add(s_acc, rec[1], acc_a, S, dup);
+    acc_add(s_acc, rec[2], acc_b, S, dup);
 }
 
 template <bool LUMP>
-__device__ __forceinline__ void unit_eval_any(int m, const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
+__device__ __forceinline__ void unit_eval_any(const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
                                               const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
-                                              float2 *__restrict__ out) {
-    switch (m) {
-        case 6: unit_eval<6, LUMP>(s_node, s_val, rec, bd, out); break;
-        case 5: unit_eval<5, LUMP>(s_node, s_val, rec, bd, out); break;
-        case 4: unit_eval<4, LUMP>(s_node, s_val, rec, bd, out); break;
-        case 3: unit_eval<3, LUMP>(s_node, s_val, rec, bd, out); break;
-        case 2: unit_eval<2, LUMP>(s_node, s_val, rec, bd, out); break;
-        default: unit_eval<1, LUMP>(s_node, s_val, rec, bd, out); break;
+                                              int *__restrict__ s_acc, float2 S) {
+    switch (rec[0] & 0xffu) {
+        case 6: unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        case 5: unit_eval<5, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        case 4: unit_eval<4, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        case 3: unit_eval<3, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        case 2: unit_eval<2, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        default: unit_eval<1, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
     }
 }
 
@@ -191,23 +225,24 @@ __device__ __forceinline__ void load_unit(const MeshDev &m, int64_t u, uint32_t 
 
 // K1 on paired patches: one block of NT threads (128 or 256) per chunk.
 template <bool LUMP, int NT>
-__global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
+__global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2)) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const UnitSmem &L = m.smu;
     NodeF *s_node = reinterpret_cast<NodeF *>(smem + L.node);
     float *s_val = reinterpret_cast<float *>(smem + L.val);
-    uint16_t *s_inc = reinterpret_cast<uint16_t *>(smem + L.inc);
+    int *s_acc = reinterpret_cast<int *>(smem + L.acc);                // two ints per node
     int32_t *s_shd = reinterpret_cast<int32_t *>(smem + L.shd);
-    float *s_con = reinterpret_cast<float *>(smem + L.contrib);
     float2 *s_dot = reinterpret_cast<float2 *>(smem + L.dot);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-    __shared__ float s_beta;
+    __shared__ float s_beta, s_scale[2];
+    __shared__ unsigned int s_vmax;
     __shared__ int s_done;
     __shared__ bool s_last;
     const int tid = threadIdx.x;
     if (tid == 0) {
         s_done = a.st->done;
         s_beta = (float)a.st->beta;
+        s_vmax = 0u;
         mbar_init(s_bar, 1);
         fence_mbar_init();
     }
@@ -217,11 +252,9 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     const ChunkUnits cu = m.chunks_u[blockIdx.x];
     if (tid == 0) {
         const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
-        const uint32_t b_inc = (uint32_t)cu.uinc_n * 2u;
         const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_inc + b_shd);
+        mbar_arrive_expect_tx(s_bar, b_node + b_shd);
         bulk_g2s(s_node, m.node32 + cd.node_off, b_node, s_bar);
-        bulk_g2s(s_inc, m.uinc + cu.uinc_off, b_inc, s_bar);
         if (b_shd) bulk_g2s(s_shd, m.sh_dest + cd.sh_off, b_shd, s_bar);
     }
     const float beta = s_beta;
@@ -233,7 +266,8 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     if (has_unit) load_unit(m, (int64_t)cu.unit_off + tid, rec, bd);
     // p = D^-1 r + beta p on the chunk's nodes (loads of four nodes before any
     // store: the stores to p could alias them); no Dirichlet mask is needed
-    // (D^-1 = 0 and r = 0 there and p starts at 0)
+    // (D^-1 = 0 and r = 0 there and p starts at 0); the node sums start at 0
+    float vmax = 0.f;
     for (int l0 = tid; l0 < n_loc; l0 += 4 * NT) {
         // interior nodes: D^-1, r, p contiguous from int_begin; shared
         // nodes: (D^-1 r, p) from the chunk's contiguous halo slots
@@ -261,9 +295,15 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
                 // shared nodes: fma(beta, p, 1 * z) = fma(beta, p, z), the value K2 stores
                 const float v = cg_dir(dv[k], rv[k], beta, pv[k]);
                 s_val[l] = v;
+                reinterpret_cast<int2 *>(s_acc)[l] = make_int2(0, 0);
+                vmax = fmaxf(vmax, fabsf(v));
                 if (l < n_int) a.p[cd.int_begin + l] = v;
             }
         }
+    }
+    {   // chunk maximum of |v| (non-negative floats order as their bit patterns)
+        const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+        if ((tid & 31) == 0 && wmax) atomicMax(&s_vmax, wmax);
     }
     // the data of a chunk that a block launched later will process, into L2
     if (tid == 0 && m.prefetch_ahead > 0 && blockIdx.x + m.prefetch_ahead < (unsigned)m.n_chunks) {
@@ -271,7 +311,6 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
         const ChunkDesc fd = m.chunks[fc];
         const ChunkUnits fu = m.chunks_u[fc];
         l2_prefetch(m.node32 + fd.node_off, (size_t)fd.n_loc * sizeof(NodeF));
-        l2_prefetch(m.uinc + fu.uinc_off, (size_t)fu.uinc_n * 2);
         l2_prefetch(m.urec + (size_t)fu.unit_off * kURecWords, (size_t)fu.n_unit * kURecWords * 4);
         l2_prefetch(m.ubd + (size_t)fu.unit_off * kPatchMax * 2, (size_t)fu.n_unit * kPatchMax * 8);
         l2_prefetch(a.dinv + fd.int_begin, (size_t)fd.n_int * 4);
@@ -283,47 +322,48 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     uint32_t ph = 0;
     {
         bool ok = mbar_wait_bounded(s_bar, ph);
-        ok = __syncthreads_and(ok);   // also publishes s_val
+        ok = __syncthreads_and(ok);   // also publishes s_val, s_acc and s_vmax
         if (!ok) {
             if (tid == 0) atomicOr(m.err, kErrMbarTimeout);
             mbar_wait_bounded(s_bar, ph);
             return;
         }
     }
-    // ---- element phase: one unit per thread and round
-    float2 *s_con2 = reinterpret_cast<float2 *>(s_con);
-    if (tid == 0) s_con[cu.n_unit * 2 * kUnitSlots] = 0.f;   // the zero slot
-    if (has_unit) {
-        if (rec[0] == 6)
-            unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_con2 + tid * kUnitSlots);
-        else
-            unit_eval_any<LUMP>((int)rec[0], s_node, s_val, rec, bd, s_con2 + tid * kUnitSlots);
-    }
-    for (int u = tid + NT; u < cu.n_unit; u += NT) {
-        load_unit(m, (int64_t)cu.unit_off + u, rec, bd);
-        unit_eval_any<LUMP>((int)rec[0], s_node, s_val, rec, bd, s_con2 + u * kUnitSlots);
+    // ---- the chunk's fixed-point scale (one thread; FP64 once per block)
+    if (tid == 0) {
+        const double bnd = 4.0 * (double)cu.max_star * (double)__ldg(m.dmax + blockIdx.x) *
+                           (double)__uint_as_float(s_vmax);
+        int e = 0;
+        if (bnd > 0.0 && isfinite(bnd)) {
+            frexp(bnd, &e);                     // bnd < 2^e
+            e = max(-60, min(180, e));
+        }
+        const int sx = 47 - e;                  // S = 2^sx, inv = 2^-sx (within the float range here)
+        s_scale[0] = bnd > 0.0 ? ldexpf(1.0f, max(-126, min(127, sx))) : 0.f;
+        s_scale[1] = ldexpf(1.0f, max(-126, min(127, -sx)));
     }
     __syncthreads();
-    // ---- node phase: groups of 32 nodes (one warp), transposed entries
-    const uint16_t *hdr = s_inc;
-    const uint16_t *ord = s_inc + cu.order_off;
-    const uint16_t *ent = s_inc + cu.ent_off;
-    DotF acc;
-    const int lane = tid & 31;
-    for (int idx = tid; idx < cu.n_grp * 32; idx += NT) {
-        const int g = idx >> 5;
-        const int l = ord[idx];
-        const int first = hdr[2 * g], deg = hdr[2 * g + 1];
-        const uint16_t *e = ent + first + lane;
-        float s0 = 0.f, s1 = 0.f;
-        int k = 0;
-        for (; k + 1 < deg; k += 2) {
-            s0 += s_con[e[32 * k]];
-            s1 += s_con[e[32 * (k + 1)]];
+    const float2 S = p_set(s_scale[0]);
+    // ---- element phase: one unit per thread and round (nothing to add when v = 0)
+    if (s_scale[0] != 0.f) {
+        if (has_unit) {
+            if ((rec[0] & 0xffu) == 6)
+                unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_acc, S);
+            else
+                unit_eval_any<LUMP>(s_node, s_val, rec, bd, s_acc, S);
         }
-        if (k < deg) s0 += s_con[e[32 * k]];
-        if (l == kNoNode) continue;
-        float s = s0 + s1;
+        for (int u = tid + NT; u < cu.n_unit; u += NT) {
+            load_unit(m, (int64_t)cu.unit_off + u, rec, bd);
+            unit_eval_any<LUMP>(s_node, s_val, rec, bd, s_acc, S);
+        }
+    }
+    __syncthreads();
+    // ---- node phase: each node's sum, rounded to FP32 once
+    const float inv = s_scale[1];
+    DotF acc;
+    for (int l = tid; l < n_loc; l += NT) {
+        const int2 hl = reinterpret_cast<const int2 *>(s_acc)[l];
+        float s = fmaf((float)hl.x, 16777216.0f, (float)hl.y) * inv;
         acc.add_prod(s_val[l], s);                 // element-wise p^T A_e p over the chunk
         if (is_dirichlet(s_node[l].w)) s = 0.f;
         if (l < n_int)
@@ -379,6 +419,27 @@ __global__ void __launch_bounds__(NT) k_cg2_units(MeshDev m, Cg2Args<float> a) {
             st->alpha = st->rz / pq;
         }
     }
+}
+
+// Largest diagonal entry D_jj = 1 / D^-1_jj over each chunk's free local nodes
+// (the fixed-point bound of k_cg2_units); one block per chunk, after every
+// diagonal update.
+static __global__ void k_chunk_dmax(MeshDev m, float *__restrict__ dmax) {
+    const ChunkDesc cd = m.chunks[blockIdx.x];
+    float mx = 0.f;
+    for (int l = threadIdx.x; l < cd.n_loc; l += blockDim.x) {
+        const int g = l < cd.n_int ? cd.int_begin + l : m.sh_ids[cd.sh_off + (l - cd.n_int)];
+        const float di = m.dinv32[g];
+        if (di > 0.f) mx = fmaxf(mx, 1.0f / di);
+    }
+    const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+    __shared__ unsigned int s_mx;
+    if (threadIdx.x == 0) s_mx = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_mx, wmax);
+    __syncthreads();
+    // a little above the FP32 value: the bound must hold for the exact D
+    if (threadIdx.x == 0) dmax[blockIdx.x] = __uint_as_float(s_mx) * 1.0001f;
 }
 
 // The halo of the paired-patch kernel: every chunk-major shared slot j (node

@@ -45,32 +45,22 @@ constexpr int kChunkThreads = 256;  // threads of a block that processes a chunk
 // star patches of a chunk are taken two at a time ("units"), two patches of
 // the same size m, so that one thread evaluates both with packed FP32x2
 // arithmetic (one half per patch).  Units are ordered by m, largest first; a
-// size class with an odd count pairs its last patch with itself (the second
-// half's contributions are never read).
-//   unit record (u32): [0] = m, [1] = (a | a' << 16), [2] = (b | b' << 16),
+// size class with an odd count pairs its last patch with itself, and that
+// unit's second half is flagged so its contributions are dropped.
+//   unit record (u32): [0] = m | kUnitDup (second half duplicate),
+//                      [1] = (a | a' << 16), [2] = (b | b' << 16),
 //                      [3 + j] = (r_j | r'_j << 16), j = 0..m; local node ids
-//   contributions: float index u * 18 + 2 * slot + half (slot 0 -> a, 1 -> b,
-//                  2 + j -> r_j), one float2 per slot; index n_unit * 18 is a
-//                  slot that always holds 0
-//   per-chunk incidence segment (u16, parts padded to 8 entries):
-//     headers [n_grp][2] = (first entry, degree) of each group of 32 nodes,
-//     order [n_grp * 32] = local node of each position (0xffff: none; nodes
-//     sorted by degree, most first), entries: group g's entry k of lane i at
-//     first + 32 k + i = the contribution index (or the zero slot).
+// Node sums are fixed-point shared-memory integer atomics (exact additions:
+// the result does not depend on their order), so no incidence list is needed.
 constexpr int kURecWords = 10;
-constexpr int kUnitSlots = 9;
-constexpr uint16_t kNoNode = 0xffff;
+constexpr uint32_t kUnitDup = 0x100u;
 struct ChunkUnits {
     int32_t unit_off;   // first unit of the chunk
     int32_t n_unit;
-    int32_t uinc_off;   // first u16 of the chunk's incidence segment
-    int32_t uinc_n;     // its length (u16, a multiple of 8)
-    int32_t n_grp;      // groups of 32 nodes
-    int32_t order_off;  // u16 offset of the order part inside the segment
-    int32_t ent_off;    // u16 offset of the entries inside the segment
+    int32_t max_star;   // most elements of the chunk around one of its nodes
     int32_t pad;
 };
-static_assert(sizeof(ChunkUnits) == 32, "ChunkUnits layout");
+static_assert(sizeof(ChunkUnits) == 16, "ChunkUnits layout");
 
 struct ChunkDesc {
     int32_t patch_off;  // first (padded) patch of the chunk

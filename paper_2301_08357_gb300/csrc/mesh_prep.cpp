@@ -617,13 +617,11 @@ std::string build_units(PrepMesh &m) {
     m.chunks_u.assign(m.n_chunks, ChunkUnits{});
     m.urec.clear();
     m.uelem.clear();
-    m.uinc.clear();
     m.unit_total = 0;
-    m.max_unit = m.max_uinc = 0;
+    m.max_unit = 0;
     struct Ref { int p, m; };
     std::vector<Ref> ps;
-    std::vector<std::vector<int32_t>> lists;
-    std::vector<int32_t> nodes;
+    std::vector<int> star;
     for (int c = 0; c < m.n_chunks; ++c) {
         const ChunkDesc &cd = m.chunks[c];
         ChunkUnits &cu = m.chunks_u[c];
@@ -642,74 +640,42 @@ std::string build_units(PrepMesh &m) {
             }
         }
         const int nu = (int)units.size();
-        if ((int64_t)nu * 2 * kUnitSlots + 2 > 65535) return "paired-patch layout: too many units in a chunk";
         cu.unit_off = (int32_t)m.unit_total;
         cu.n_unit = nu;
-        lists.assign(cd.n_loc, {});
+        star.assign(cd.n_loc, 0);
         for (int u = 0; u < nu; ++u) {
             uint32_t w[kURecWords] = {0};
             int32_t el[kPatchMax * 2];
             for (int k = 0; k < kPatchMax * 2; ++k) el[k] = -1;
             int pm = 0;
             for (int h = 0; h < 2; ++h) {
-                const int q = units[u][h] >= 0 ? units[u][h] : units[u][0];
+                const bool dup = units[u][h] < 0;
+                const int q = dup ? units[u][0] : units[u][h];
                 const uint16_t *rec = &m.pids[(size_t)(cd.patch_off + q) * kPatchIds];
                 pm = rec[0];
                 const int shift = 16 * h;
-                w[0] = (uint32_t)pm;
+                w[0] = (uint32_t)pm | (dup ? kUnitDup : 0u);
                 w[1] |= (uint32_t)rec[1] << shift;
                 w[2] |= (uint32_t)rec[2] << shift;
                 for (int j = 0; j <= pm; ++j) w[3 + j] |= (uint32_t)rec[3 + j] << shift;
-                for (int j = 0; j < pm; ++j) el[2 * j + h] = m.elem_src[(size_t)(cd.patch_off + q) * kPatchMax + j];
-                if (units[u][h] < 0) continue;   // the duplicate half feeds no node
-                const int base = u * 2 * kUnitSlots + h;
-                lists[rec[1]].push_back(base + 0);
-                lists[rec[2]].push_back(base + 2);
-                for (int j = 0; j <= pm; ++j) lists[rec[3 + j]].push_back(base + 2 * (2 + j));
+                if (dup) continue;   // no element behind the duplicate half
+                for (int j = 0; j < pm; ++j) {
+                    el[2 * j + h] = m.elem_src[(size_t)(cd.patch_off + q) * kPatchMax + j];
+                    // elements around each of the element's vertices (a, b, r_j, r_{j+1})
+                    star[rec[1]]++;
+                    star[rec[2]]++;
+                    star[rec[3 + j]]++;
+                    star[rec[4 + j]]++;
+                }
             }
-            if (units[u][1] < 0)
-                for (int j = 0; j < pm; ++j) el[2 * j + 1] = -1;   // no element behind the duplicate half
             for (int k = 0; k < kURecWords; ++k) m.urec.push_back(w[k]);
             for (int k = 0; k < kPatchMax * 2; ++k) m.uelem.push_back(el[k]);
         }
-        // incidence: nodes by degree (most first, stable), groups of 32
-        nodes.resize(cd.n_loc);
-        for (int l = 0; l < cd.n_loc; ++l) nodes[l] = l;
-        std::stable_sort(nodes.begin(), nodes.end(),
-                         [&](int32_t x, int32_t y) { return lists[x].size() > lists[y].size(); });
-        const int n_grp = (cd.n_loc + 31) / 32;
-        const int hdr_n = (int)round_up(2 * n_grp, 8), ord_n = n_grp * 32;
-        std::vector<uint16_t> seg(hdr_n + ord_n, 0);
-        const uint16_t zero = (uint16_t)(nu * 2 * kUnitSlots);
-        int ent = 0;
-        for (int g = 0; g < n_grp; ++g) {
-            int deg = 0;
-            for (int i = 0; i < 32; ++i) {
-                const int idx = g * 32 + i;
-                seg[hdr_n + idx] = idx < cd.n_loc ? (uint16_t)nodes[idx] : kNoNode;
-                if (idx < cd.n_loc) deg = std::max(deg, (int)lists[nodes[idx]].size());
-            }
-            if (hdr_n + ord_n + ent + 32 * deg > 65535) return "paired-patch layout: incidence segment too large";
-            seg[2 * g] = (uint16_t)ent;
-            seg[2 * g + 1] = (uint16_t)deg;
-            for (int k = 0; k < deg; ++k)
-                for (int i = 0; i < 32; ++i) {
-                    const int idx = g * 32 + i;
-                    const std::vector<int32_t> *L = idx < cd.n_loc ? &lists[nodes[idx]] : nullptr;
-                    seg.push_back(L && k < (int)L->size() ? (uint16_t)(*L)[k] : zero);
-                }
-            ent += 32 * deg;
-        }
-        seg.resize(round_up(seg.size(), 8), zero);
-        cu.uinc_off = (int32_t)m.uinc.size();
-        cu.uinc_n = (int32_t)seg.size();
-        cu.n_grp = n_grp;
-        cu.order_off = hdr_n;
-        cu.ent_off = hdr_n + ord_n;
-        m.uinc.insert(m.uinc.end(), seg.begin(), seg.end());
+        int ms = 1;
+        for (int l = 0; l < cd.n_loc; ++l) ms = std::max(ms, star[l]);
+        cu.max_star = ms;
         m.unit_total += nu;
         m.max_unit = std::max(m.max_unit, nu);
-        m.max_uinc = std::max(m.max_uinc, (int)seg.size());
     }
     return "";
 }

@@ -58,9 +58,8 @@ struct PrepMesh {
     std::vector<ChunkUnits> chunks_u;              // [n_chunks]
     std::vector<uint32_t> urec;                    // [unit_total * kURecWords]
     std::vector<int32_t> uelem;                    // [unit_total * kPatchMax * 2] element of (tet j, half h), -1 none
-    std::vector<uint16_t> uinc;                    // incidence segments of all chunks
     int64_t unit_total = 0;
-    int max_unit = 0, max_uinc = 0;
+    int max_unit = 0;
 };
 
 // Build the paired-patch layout from a prepared 3D mesh (its patch records

@@ -27,11 +27,10 @@ struct SmemLayout {
 };
 
 // Shared memory of the paired-patch CG operator kernel (cg2u.cuh): node
-// records | values | incidence segment | partial-sum destinations of the
-// shared nodes | contributions (+ the zero slot) | per-thread dot partials |
-// mbarrier.
+// records | values | fixed-point node sums | partial-sum destinations of the
+// shared nodes | per-thread dot partials | mbarrier.
 struct UnitSmem {
-    uint32_t node, val, inc, shd, contrib, dot, bar, total;
+    uint32_t node, val, acc, shd, dot, bar, total;
 };
 
 struct MeshDev {
@@ -57,7 +56,7 @@ struct MeshDev {
     const ChunkUnits *chunks_u;
     const uint32_t *urec;    // [unit_total * kURecWords]
     const float *ubd;        // [unit_total * kPatchMax * 2] beta*dt^2/6 per (unit, element, half)
-    const uint16_t *uinc;    // incidence segments
+    const float *dmax;       // [n_chunks] largest diagonal entry over each chunk's free nodes
     UnitSmem smu;
     int prefetch_ahead;      // chunks between a block and the chunk whose data it prefetches into L2
 };

@@ -428,7 +428,7 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
     RC(upload(c, m, &g, nullptr, d.n_pad * 8));
     CK(cudaMemset(g, 0, d.n_pad * 8));
     d.dinv64 = g;
-    if (pm.dim == 3 && pm.unit_total > 0 && m->k1_variant == 2) {
+    if (pm.dim == 3 && pm.unit_total > 0 && m->k1_variant != 1) {
         ChunkUnits *cu;
         RC(upload(c, m, &cu, pm.chunks_u.data(), pm.chunks_u.size() * sizeof(ChunkUnits)));
         d.chunks_u = cu;
@@ -436,12 +436,14 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         RC(upload(c, m, &ur, pm.urec.data(), pm.urec.size() * 4));
         d.urec = ur;
         RC(upload(c, m, &m->d_uelem, pm.uelem.data(), pm.uelem.size() * 4));
-        RC(upload(c, m, &u, pm.uinc.data(), pm.uinc.size() * 2));
-        d.uinc = u;
         float *ub;
         RC(upload(c, m, &ub, nullptr, pm.uelem.size() * 4));
         CK(cudaMemset(ub, 0, pm.uelem.size() * 4));
         d.ubd = ub;
+        float *dm;
+        RC(upload(c, m, &dm, nullptr, (size_t)pm.n_chunks * 4));
+        CK(cudaMemset(dm, 0, (size_t)pm.n_chunks * 4));
+        d.dmax = dm;
         UnitSmem &U = d.smu;
         uint32_t off = 0;
         auto take = [&](uint64_t bytes) {
@@ -451,9 +453,8 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         };
         U.node = take((uint64_t)pm.max_loc * sizeof(NodeF));
         U.val = take((uint64_t)pm.max_loc * 4);
-        U.inc = take((uint64_t)pm.max_uinc * 2);
+        U.acc = take((uint64_t)pm.max_loc * 8);
         U.shd = take((uint64_t)round_up(pm.max_sh, kShPad) * 4);
-        U.contrib = take((uint64_t)pm.max_unit * 2 * kUnitSlots * 4 + 16);
         U.dot = take((uint64_t)kChunkThreads * 8);
         U.bar = take(8);
         U.total = off;
@@ -549,7 +550,7 @@ extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, cons
     m->update_bps = opts ? opts->update_blocks_per_sm : 0;
     m->k1_variant = opts ? opts->operator_kernel : 0;
     const int ot = opts ? opts->operator_threads : 0;
-    m->unit_threads = ot == 128 ? 128 : 256;
+    m->unit_threads = ot == 256 ? 256 : 128;
     if (m->update_bps < 0 || m->update_bps > 64 || m->k1_variant < 0 || m->k1_variant > 2 ||
         (ot != 0 && ot != 128 && ot != 256)) {
         delete m;
@@ -626,6 +627,7 @@ extern "C" int ps_mesh_get_stats(const ps_mesh *m, ps_mesh_stats *o) {
     o->max_chunk_elems = p.max_elem;
     o->max_chunk_nodes = p.max_loc;
     o->solve_bytes = batch_ws_bytes(m);
+    o->operator_kernel = m->use_units ? 2 : 1;
     return PS_OK;
 }
 
@@ -684,6 +686,7 @@ static int coeff_upload(ps_mesh *m, const double *alpha, const double *beta, dou
         else
             k_chunks<3, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total>>>(d, a);
         k_shared<double, kDiag><<<m->grid2, kBlock>>>(d, a, d.n_chunks);
+        if (d.dmax) k_chunk_dmax<<<d.n_chunks, 128>>>(d, const_cast<float *>(d.dmax));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
@@ -741,7 +744,7 @@ namespace ps {
 // stream s (FP64 element arithmetic, both precisions stored).  The caller
 // holds the context mutex and the workspace exists.
 static int diag_update_device(ps_mesh *m, cudaStream_t s) {
-    MeshDev &d = m->dev;
+    const MeshDev &d = m->dev;
     VecArgs<double> a;
     std::memset(&a, 0, sizeof(a));
     a.partial = m->ws.part64;
@@ -750,6 +753,27 @@ static int diag_update_device(ps_mesh *m, cudaStream_t s) {
     else
         k_chunks<3, double, kDiag><<<d.n_chunks, kBlock, d.sm64.total, s>>>(d, a);
     k_shared<double, kDiag><<<m->grid2, kBlock, 0, s>>>(d, a, d.n_chunks);
+    if (d.dmax) k_chunk_dmax<<<d.n_chunks, 128, 0, s>>>(d, const_cast<float *>(d.dmax));
+    CK(cudaGetLastError());
+    return PS_OK;
+}
+
+// Coefficients changed while the preconditioner keeps its diagonal: the
+// paired-patch kernel's fixed-point bound still needs the current diagonal,
+// so it is computed into scratch (two free workspace vectors) and only its
+// chunk maxima are kept (dmax).  No-op for the other kernels.
+static int dmax_refresh(ps_mesh *m, cudaStream_t s) {
+    const MeshDev &d = m->dev;
+    if (!d.dmax) return PS_OK;
+    MeshDev d2 = d;
+    d2.dinv64 = m->ws.q64;
+    d2.dinv32 = m->ws.q32;
+    VecArgs<double> a;
+    std::memset(&a, 0, sizeof(a));
+    a.partial = m->ws.part64;
+    k_chunks<3, double, kDiag><<<d2.n_chunks, kBlock, d2.sm64.total, s>>>(d2, a);
+    k_shared<double, kDiag><<<m->grid2, kBlock, 0, s>>>(d2, a, d2.n_chunks);
+    k_chunk_dmax<<<d2.n_chunks, 128, 0, s>>>(d2, const_cast<float *>(d.dmax));
     CK(cudaGetLastError());
     return PS_OK;
 }
@@ -773,7 +797,7 @@ int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStrea
     }
     CK(cudaGetLastError());
     m->dt2 = dt2;
-    return diag ? diag_update_device(m, s) : PS_OK;
+    return diag ? diag_update_device(m, s) : dmax_refresh(m, s);
 }
 
 // Nodal alpha (caller's numbering, device; each unknown takes its master
@@ -788,7 +812,7 @@ int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s, boo
         p.loc_total, m->d_loc_node, m->d_old_of_new, alpha_dev, d.dirichlet, const_cast<NodeF *>(d.node32),
         const_cast<NodeD *>(d.node64));
     CK(cudaGetLastError());
-    return diag ? diag_update_device(m, s) : PS_OK;
+    return diag ? diag_update_device(m, s) : dmax_refresh(m, s);
 }
 
 int ensure_workspace(ps_mesh *m) {
@@ -1406,7 +1430,6 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
         SmemLayout l64 = make_layout(8, sizeof(NodeD), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
         stats->reserved[0] = pm.n_patches;
         stats->reserved[1] = pm.inc_total;
-        stats->reserved[2] = pm.loc_total;
         stats->device_bytes = l64.total;  // shared memory per block of the FP64 pass
     }
     return PS_OK;

@@ -75,7 +75,7 @@ class ps_mesh_stats(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_free", C.c_int64), ("dim", C.c_int32),
                 ("n_chunks", C.c_int32), ("n_shared", C.c_int64), ("chunk_node_refs", C.c_int64),
                 ("device_bytes", C.c_int64), ("max_chunk_elems", C.c_int32), ("max_chunk_nodes", C.c_int32),
-                ("solve_bytes", C.c_int64), ("reserved", C.c_int64 * 3)]
+                ("solve_bytes", C.c_int64), ("operator_kernel", C.c_int64), ("reserved", C.c_int64 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
