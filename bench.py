@@ -755,10 +755,15 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
         order = [(k, ci) for k in range(steps) for ci in range(len(cases))]
         pending = {}
 
-        def finish(t, ci, k):
+        def finish(t, ci, k, polled=None):
             want_x = ci in check_cases and k + 1 == steps
             xo = np.empty(cases[ci].n_nodes) if want_x else None
-            st, info = P.ps_solve_wait(srv, t, 600.0, x_out=xo)
+            if polled is None:
+                st, info = P.ps_solve_wait(srv, t, 600.0, x_out=xo)
+            else:
+                st, info = polled
+                if want_x:
+                    P.ps_solve_poll(srv, t, x_out=xo)
             P.ps_server_release(srv, t)
             if st != P.PS_OK:
                 raise RuntimeError("served solve failed: %s" % P.ps_status_str(st))
@@ -770,18 +775,27 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
             return info
 
         if rate is None:
+            # every case resubmits as soon as its request completes: all
+            # pending tickets are polled, none is waited on in order
             for ci in range(len(cases)):
                 pending[P.ps_solve_submit(srv, ids[ci], state[ci][1])] = (ci, 0)
             while pending:
-                t = next(iter(pending))
-                ci, k = pending.pop(t)
-                info = finish(t, ci, k)
-                worst = max(worst, info.rel_res)
-                done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
-                if k + 1 < steps:
-                    beta, b = S.served_step_drift(cases[ci], *state[ci])
-                    state[ci] = (beta, b)
-                    pending[P.ps_solve_submit(srv, ids[ci], b, beta)] = (ci, k + 1)
+                progressed = False
+                for t in list(pending):
+                    polled = P.ps_solve_poll(srv, t)
+                    if polled[0] == P.PS_PENDING:
+                        continue
+                    ci, k = pending.pop(t)
+                    info = finish(t, ci, k, polled)
+                    progressed = True
+                    worst = max(worst, info.rel_res)
+                    done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
+                    if k + 1 < steps:
+                        beta, b = S.served_step_drift(cases[ci], *state[ci])
+                        state[ci] = (beta, b)
+                        pending[P.ps_solve_submit(srv, ids[ci], b, beta)] = (ci, k + 1)
+                if not progressed:
+                    time.sleep(0.0002)
         else:
             next_t = time.perf_counter()
             for k, ci in order:
