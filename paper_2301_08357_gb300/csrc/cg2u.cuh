@@ -6,9 +6,14 @@
 //   * one thread evaluates one unit -- two star patches of equal size -- with
 //     packed FP32x2 arithmetic (FFMA2 / FADD2 / FMUL2: one instruction for both
 //     patches), so each element costs about half the issue slots;
-//   * unit records and beta*dt^2/6 are read straight into registers
-//     (coalesced, before the staging wait); only node records and the
-//     incidence segment are staged into shared memory by bulk copies;
+//   * the chunk's node records, unit records, beta*dt^2/6 values and
+//     shared-node destinations are staged into shared memory by bulk copies
+//     (one mbarrier); a thread reads its unit's record words and
+//     coefficients from there as its elements need them, so they hold no
+//     registers across the unit;
+//   * coordinates enter the arithmetic as differences to the unit's node a
+//     (scalar subtractions into the packed operands), and a duplicate second
+//     half is dropped by a zero scale, not a branch;
 //   * contributions are added into per-node fixed-point sums in shared
 //     memory (32-bit integer atomics: exact, so the result does not depend on
 //     the order of the additions -- no incidence list, bitwise reproducible);
@@ -66,9 +71,6 @@ __device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes) {
 struct P3 {
     float2 x, y, z;
 };
-__device__ __forceinline__ P3 p3_sub(const P3 &a, const P3 &b) {
-    return {p_sub(a.x, b.x), p_sub(a.y, b.y), p_sub(a.z, b.z)};
-}
 // a x b
 __device__ __forceinline__ P3 p3_cross(const P3 &a, const P3 &b) {
     return {p_fma(a.y, b.z, p_neg(p_mul(a.z, b.y))), p_fma(a.z, b.x, p_neg(p_mul(a.x, b.z))),
@@ -78,17 +80,21 @@ __device__ __forceinline__ float2 p3_dot(const P3 &a, const P3 &b) {
     return p_fma(a.z, b.z, p_fma(a.y, b.y, p_mul(a.x, b.x)));
 }
 
-// Node of both halves: coordinates, alpha (absolute value: the sign bit marks
-// Dirichlet nodes) and the input value.
-struct PNode {
-    P3 p;
+// Node of both halves relative to the unit's node a of each half: the
+// coordinate differences p - a (one scalar subtraction per half, written
+// straight into the packed operand), alpha (absolute value: the sign bit
+// marks Dirichlet nodes) and the input value.
+struct PRel {
+    P3 d;
     float2 al, v;
 };
-__device__ __forceinline__ PNode pnode(const NodeF *__restrict__ s_node, const float *__restrict__ s_val, uint32_t w) {
+__device__ __forceinline__ PRel prel(const NodeF *__restrict__ s_node, const float *__restrict__ s_val, uint32_t w,
+                                     const float3 &a0, const float3 &a1) {
     const int i0 = (int)(w & 0xffffu), i1 = (int)(w >> 16);
     const NodeF n0 = s_node[i0], n1 = s_node[i1];
-    PNode r;
-    r.p = {make_float2(n0.x, n1.x), make_float2(n0.y, n1.y), make_float2(n0.z, n1.z)};
+    PRel r;
+    r.d = {make_float2(n0.x - a0.x, n1.x - a1.x), make_float2(n0.y - a0.y, n1.y - a1.y),
+           make_float2(n0.z - a0.z, n1.z - a1.z)};
     r.al = make_float2(fabsf(n0.w), fabsf(n1.w));
     r.v = make_float2(s_val[i0], s_val[i1]);
     return r;
@@ -106,46 +112,51 @@ __device__ __forceinline__ void acc_add1(int *__restrict__ s_acc, int i, float t
     atomicAdd(s_acc + 2 * i, __float2int_rn(hf));
     atomicAdd(s_acc + 2 * i + 1, __float2int_rn(lf));
 }
-// Add a contribution of each half to its node's sums (scale S); a duplicate
-// second half adds nothing.
-__device__ __forceinline__ void acc_add(int *__restrict__ s_acc, uint32_t w, float2 v, float2 S, bool dup) {
+// Add a contribution of each half to its node's sums.  S is the chunk's
+// scale for both halves, with S.y = 0 on a unit whose second half duplicates
+// the first: that half then adds exact zeros (no branch).
+__device__ __forceinline__ void acc_add(int *__restrict__ s_acc, uint32_t w, float2 v, float2 S) {
     const float2 t = p_mul(v, S);
     acc_add1(s_acc, (int)(w & 0xffffu), t.x);
-    if (!dup) acc_add1(s_acc, (int)(w >> 16), t.y);
+    acc_add1(s_acc, (int)(w >> 16), t.y);
 }
 
 // One unit of M tetrahedra per half: contributions of node slots a, b and
-// r_j (j = 0..M) into the fixed-point sums.  rec: the unit record; bd:
-// beta*dt^2/6 of element j of each half; S: the chunk's scale (both halves).
+// r_j (j = 0..M) into the fixed-point sums.  rec: the unit record and bd:
+// beta*dt^2/6 of element j of each half, both in shared memory (read as the
+// elements need them); S: the scale of each half.
 template <int M, bool LUMP>
 __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
-                                          const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
+                                          const uint32_t *__restrict__ rec, const float2 *__restrict__ bd,
                                           int *__restrict__ s_acc, float2 S) {
-    const bool dup = (rec[0] & kUnitDup) != 0;
-    const PNode A = pnode(s_node, s_val, rec[1]);
-    const PNode B = pnode(s_node, s_val, rec[2]);
-    const P3 e1 = p3_sub(B.p, A.p);
-    PNode R0 = pnode(s_node, s_val, rec[3]);
-    P3 d0 = p3_sub(R0.p, A.p);
+    const uint32_t wa = rec[1];
+    const NodeF na0 = s_node[wa & 0xffffu], na1 = s_node[wa >> 16];
+    const float3 a0 = make_float3(na0.x, na0.y, na0.z), a1 = make_float3(na1.x, na1.y, na1.z);
+    const float2 Aal = make_float2(fabsf(na0.w), fabsf(na1.w));
+    const float2 Av = make_float2(s_val[wa & 0xffffu], s_val[wa >> 16]);
+    const PRel B = prel(s_node, s_val, rec[2], a0, a1);
+    const P3 e1 = B.d;
+    PRel R0 = prel(s_node, s_val, rec[3], a0, a1);
+    P3 d0 = R0.d;
     P3 w0 = p3_cross(e1, d0);
-    const float2 t1 = p_sub(B.v, A.v);
-    float2 t2 = p_sub(R0.v, A.v);
-    const float2 sAB = p_add(A.al, B.al);
-    const float2 xAB = p_add(A.v, B.v);
-    const float2 qa = p_mul(A.al, A.v), qb = p_mul(B.al, B.v);
+    const float2 t1 = p_sub(B.v, Av);
+    float2 t2 = p_sub(R0.v, Av);
+    const float2 sAB = p_add(Aal, B.al);
+    const float2 xAB = p_add(Av, B.v);
+    const float2 qa = p_mul(Aal, Av), qb = p_mul(B.al, B.v);
     const float2 qAB = p_add(qa, qb);
     float2 q0 = p_mul(R0.al, R0.v);
     float2 acc_a = p_set(0.f), acc_b = p_set(0.f), acc_c = p_set(0.f);
     const float2 two = p_set(2.f);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-        const PNode R1 = pnode(s_node, s_val, rec[4 + j]);
-        const P3 d1 = p3_sub(R1.p, A.p);
+        const PRel R1 = prel(s_node, s_val, rec[4 + j], a0, a1);
+        const P3 d1 = R1.d;
         const P3 w1 = p3_cross(e1, d1);
         const P3 c1 = p3_cross(d0, d1);
         const float2 ad = p_abs(p3_dot(e1, c1));
         const float2 kc = p_mul(bd[j], make_float2(rcp_approx(ad.x), rcp_approx(ad.y)));
-        const float2 t3 = p_sub(R1.v, A.v);
+        const float2 t3 = p_sub(R1.v, Av);
         // g = t1 c1 - t2 w1 + t3 w0, scaled by kc
         const float2 nt2 = p_neg(t2);
         P3 g;
@@ -165,20 +176,20 @@ __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, cons
             o2 = p_fma(cl, q0, k2);
             o3 = p_fma(cl, q1, k3);
         } else {
-            const float2 S = p_add(sAB, p_add(R0.al, R1.al));
+            const float2 Ssum = p_add(sAB, p_add(R0.al, R1.al));
             const float2 X = p_add(xAB, p_add(R0.v, R1.v));
             const float2 Q = p_add(qAB, p_add(q0, q1));
-            const float2 base = p_fma(S, X, Q);
+            const float2 base = p_fma(Ssum, X, Q);
             const float2 cm = p_mul(ad, p_set(1.0f / 720.0f));
             // o_i = cm (base + S v_i + alpha_i (X + 2 v_i)) + k_i
-            o0 = p_fma(cm, p_fma(A.al, p_fma(two, A.v, X), p_fma(S, A.v, base)), k0);
-            o1 = p_fma(cm, p_fma(B.al, p_fma(two, B.v, X), p_fma(S, B.v, base)), k1);
-            o2 = p_fma(cm, p_fma(R0.al, p_fma(two, R0.v, X), p_fma(S, R0.v, base)), k2);
-            o3 = p_fma(cm, p_fma(R1.al, p_fma(two, R1.v, X), p_fma(S, R1.v, base)), k3);
+            o0 = p_fma(cm, p_fma(Aal, p_fma(two, Av, X), p_fma(Ssum, Av, base)), k0);
+            o1 = p_fma(cm, p_fma(B.al, p_fma(two, B.v, X), p_fma(Ssum, B.v, base)), k1);
+            o2 = p_fma(cm, p_fma(R0.al, p_fma(two, R0.v, X), p_fma(Ssum, R0.v, base)), k2);
+            o3 = p_fma(cm, p_fma(R1.al, p_fma(two, R1.v, X), p_fma(Ssum, R1.v, base)), k3);
         }
         acc_a = p_add(acc_a, o0);
         acc_b = p_add(acc_b, o1);
-        acc_add(s_acc, rec[3 + j], p_add(acc_c, o2), S, dup);
+        acc_add(s_acc, rec[3 + j], p_add(acc_c, o2), S);
         acc_c = o3;
         d0 = d1;
         w0 = w1;
@@ -186,14 +197,14 @@ __device__ __forceinline__ void unit_eval(const NodeF *__restrict__ s_node, cons
         t2 = t3;
         q0 = q1;
     }
-    acc_add(s_acc, rec[3 + M], acc_c, S, dup);
-    acc_add(s_acc, rec[1], acc_a, S, dup);
-    acc_add(s_acc, rec[2], acc_b, S, dup);
+    acc_add(s_acc, rec[3 + M], acc_c, S);
+    acc_add(s_acc, wa, acc_a, S);
+    acc_add(s_acc, rec[2], acc_b, S);
 }
 
 template <bool LUMP>
 __device__ __forceinline__ void unit_eval_any(const NodeF *__restrict__ s_node, const float *__restrict__ s_val,
-                                              const uint32_t (&rec)[kURecWords], const float2 (&bd)[kPatchMax],
+                                              const uint32_t *__restrict__ rec, const float2 *__restrict__ bd,
                                               int *__restrict__ s_acc, float2 S) {
     switch (rec[0] & 0xffu) {
         case 6: unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
@@ -201,40 +212,49 @@ __device__ __forceinline__ void unit_eval_any(const NodeF *__restrict__ s_node, 
         case 4: unit_eval<4, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
         case 3: unit_eval<3, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
         case 2: unit_eval<2, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
-        default: unit_eval<1, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        case 1: unit_eval<1, LUMP>(s_node, s_val, rec, bd, s_acc, S); break;
+        default: break;                  // pad unit (m = 0): no element
     }
 }
 
-__device__ __forceinline__ void load_unit(const MeshDev &m, int64_t u, uint32_t (&rec)[kURecWords],
-                                          float2 (&bd)[kPatchMax]) {
-    const uint2 *r2 = reinterpret_cast<const uint2 *>(m.urec + u * kURecWords);
-#pragma unroll
-    for (int k = 0; k < kURecWords / 2; ++k) {
-        const uint2 v = __ldg(r2 + k);
-        rec[2 * k] = v.x;
-        rec[2 * k + 1] = v.y;
-    }
-    const float4 *b4 = reinterpret_cast<const float4 *>(m.ubd + u * kPatchMax * 2);
-#pragma unroll
-    for (int k = 0; k < kPatchMax / 2; ++k) {
-        const float4 v = __ldg(b4 + k);
-        bd[2 * k] = make_float2(v.x, v.y);
-        bd[2 * k + 1] = make_float2(v.z, v.w);
-    }
+// The chunk's fixed-point scale S = 2^(47 - e) and 1/S (as a pair), with
+// B = 4 n_star Dmax vmax < 2^e: e from the binary exponents of Dmax and vmax
+// and that of the product of their mantissas with 4 n_star (raised by a
+// relative 2^-20, more than the two roundings of that product can lower
+// it).  S = 0 when Dmax or vmax is 0 (no free node or every input 0: nothing
+// to add) or not finite.  Every thread of the block computes the same pair.
+__device__ __forceinline__ float2 unit_scale(float dmax, float vmax, int n_star) {
+    if (!(dmax > 0.f) || !(vmax > 0.f) || !isfinite(dmax) || !isfinite(vmax)) return make_float2(0.f, 1.f);
+    int ed, ev, ep;
+    const float md = frexpf(dmax, &ed), mv = frexpf(vmax, &ev);     // mantissas in [0.5, 1)
+    frexpf(md * mv * (4.0f * (float)n_star) * (1.0f + 0x1p-20f), &ep);
+    const int e = max(-60, min(180, ed + ev + ep));
+    const int sx = 47 - e;
+    return make_float2(ldexpf(1.0f, max(-126, min(127, sx))), ldexpf(1.0f, max(-126, min(127, -sx))));
 }
 
-// K1 on paired patches: one block of NT threads (128 or 256) per chunk.
-template <bool LUMP, int NT>
-__global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2)) k_cg2_units(MeshDev m, Cg2Args<float> a) {
+// Resident 128-thread blocks per SM the operator kernel is compiled for: it
+// sets the register budget of a thread (65536 / (128 * 5) -> 96 registers,
+// a few bytes of spills) and, with ~45 KB of shared memory per 3,072-tet
+// chunk, five blocks (20 warps) fit an SM.  Measured on 160^3 Kuhn: 169.7 us
+// per pass against 175.1 us with four blocks (128 registers).
+constexpr int kUnitBlocks128 = 5;
+
+// K1 on paired patches: one block of NT threads (128 or 256) per chunk,
+// MINB blocks per SM (the register budget of a thread).
+template <bool LUMP, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const UnitSmem &L = m.smu;
     NodeF *s_node = reinterpret_cast<NodeF *>(smem + L.node);
     float *s_val = reinterpret_cast<float *>(smem + L.val);
     int *s_acc = reinterpret_cast<int *>(smem + L.acc);                // two ints per node
     int32_t *s_shd = reinterpret_cast<int32_t *>(smem + L.shd);
-    float2 *s_dot = reinterpret_cast<float2 *>(smem + L.dot);
+    uint32_t *s_urec = reinterpret_cast<uint32_t *>(smem + L.urec);     // the chunk's unit records
+    float2 *s_ubd = reinterpret_cast<float2 *>(smem + L.ubd);           // beta*dt^2/6 per (element, half)
+    float2 *s_dot = reinterpret_cast<float2 *>(smem + L.urec);          // after the element phase
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-    __shared__ float s_beta, s_scale[2];
+    __shared__ float s_beta;
     __shared__ unsigned int s_vmax;
     __shared__ int s_done;
     __shared__ bool s_last;
@@ -251,19 +271,22 @@ __global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2)) k_cg2_units(MeshDev m
     const ChunkDesc cd = m.chunks[blockIdx.x];
     const ChunkUnits cu = m.chunks_u[blockIdx.x];
     if (tid == 0) {
+        // node records, shared-node destinations and the unit records with
+        // their beta*dt^2/6 (even unit counts: 16-byte multiples)
         const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
         const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_shd);
+        const uint32_t b_rec = (uint32_t)cu.n_unit * kURecWords * 4u;
+        const uint32_t b_bd = (uint32_t)cu.n_unit * kPatchMax * 8u;
+        mbar_arrive_expect_tx(s_bar, b_node + b_shd + b_rec + b_bd);
         bulk_g2s(s_node, m.node32 + cd.node_off, b_node, s_bar);
         if (b_shd) bulk_g2s(s_shd, m.sh_dest + cd.sh_off, b_shd, s_bar);
+        if (b_rec) {
+            bulk_g2s(s_urec, m.urec + (int64_t)cu.unit_off * kURecWords, b_rec, s_bar);
+            bulk_g2s(s_ubd, m.ubd + (int64_t)cu.unit_off * kPatchMax * 2, b_bd, s_bar);
+        }
     }
     const float beta = s_beta;
     const int n_loc = cd.n_loc, n_int = cd.n_int;
-    // the thread's first unit, in registers before the staging wait
-    uint32_t rec[kURecWords];
-    float2 bd[kPatchMax];
-    const bool has_unit = tid < cu.n_unit;
-    if (has_unit) load_unit(m, (int64_t)cu.unit_off + tid, rec, bd);
     // p = D^-1 r + beta p on the chunk's nodes (loads of four nodes before any
     // store: the stores to p could alias them); no Dirichlet mask is needed
     // (D^-1 = 0 and r = 0 there and p starts at 0); the node sums start at 0
@@ -319,6 +342,7 @@ __global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2)) k_cg2_units(MeshDev m
         l2_prefetch(a.halo + fd.sh_off, (size_t)fd.n_sh * 8);
         l2_prefetch(m.sh_dest + fd.sh_off, (size_t)fd.n_sh * 4);
     }
+    const float dmax = __ldg(m.dmax + blockIdx.x);
     uint32_t ph = 0;
     {
         bool ok = mbar_wait_bounded(s_bar, ph);
@@ -329,37 +353,18 @@ __global__ void __launch_bounds__(NT, (NT == 128 ? 4 : 2)) k_cg2_units(MeshDev m
             return;
         }
     }
-    // ---- the chunk's fixed-point scale (one thread; FP64 once per block)
-    if (tid == 0) {
-        const double bnd = 4.0 * (double)cu.max_star * (double)__ldg(m.dmax + blockIdx.x) *
-                           (double)__uint_as_float(s_vmax);
-        int e = 0;
-        if (bnd > 0.0 && isfinite(bnd)) {
-            frexp(bnd, &e);                     // bnd < 2^e
-            e = max(-60, min(180, e));
-        }
-        const int sx = 47 - e;                  // S = 2^sx, inv = 2^-sx (within the float range here)
-        s_scale[0] = bnd > 0.0 ? ldexpf(1.0f, max(-126, min(127, sx))) : 0.f;
-        s_scale[1] = ldexpf(1.0f, max(-126, min(127, -sx)));
-    }
-    __syncthreads();
-    const float2 S = p_set(s_scale[0]);
     // ---- element phase: one unit per thread and round (nothing to add when v = 0)
-    if (s_scale[0] != 0.f) {
-        if (has_unit) {
-            if ((rec[0] & 0xffu) == 6)
-                unit_eval<6, LUMP>(s_node, s_val, rec, bd, s_acc, S);
-            else
-                unit_eval_any<LUMP>(s_node, s_val, rec, bd, s_acc, S);
-        }
-        for (int u = tid + NT; u < cu.n_unit; u += NT) {
-            load_unit(m, (int64_t)cu.unit_off + u, rec, bd);
-            unit_eval_any<LUMP>(s_node, s_val, rec, bd, s_acc, S);
+    const float2 sc = unit_scale(dmax, __uint_as_float(s_vmax), cu.max_star);
+    if (sc.x != 0.f) {
+        for (int u = tid; u < cu.n_unit; u += NT) {
+            const uint32_t *rec = s_urec + u * kURecWords;
+            const float2 S = make_float2(sc.x, (rec[0] & kUnitDup) ? 0.f : sc.x);
+            unit_eval_any<LUMP>(s_node, s_val, rec, s_ubd + u * kPatchMax, s_acc, S);
         }
     }
     __syncthreads();
     // ---- node phase: each node's sum, rounded to FP32 once
-    const float inv = s_scale[1];
+    const float inv = sc.y;
     DotF acc;
     for (int l = tid; l < n_loc; l += NT) {
         const int2 hl = reinterpret_cast<const int2 *>(s_acc)[l];

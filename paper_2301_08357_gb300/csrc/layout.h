@@ -46,7 +46,10 @@ constexpr int kChunkThreads = 256;  // threads of a block that processes a chunk
 // the same size m, so that one thread evaluates both with packed FP32x2
 // arithmetic (one half per patch).  Units are ordered by m, largest first; a
 // size class with an odd count pairs its last patch with itself, and that
-// unit's second half is flagged so its contributions are dropped.
+// unit's second half is flagged so its contributions are dropped.  Each
+// chunk holds an even number of units (a pad unit with m = 0 and no element
+// makes it even), so that a chunk's unit records (40 bytes each) and
+// beta*dt^2/6 values (48 bytes each) start and end on 16-byte boundaries.
 //   unit record (u32): [0] = m | kUnitDup (second half duplicate),
 //                      [1] = (a | a' << 16), [2] = (b | b' << 16),
 //                      [3 + j] = (r_j | r'_j << 16), j = 0..m; local node ids

@@ -639,6 +639,9 @@ std::string build_units(PrepMesh &m) {
                 i += 1;
             }
         }
+        // an even count per chunk: every chunk's records start and end on a
+        // 16-byte boundary (bulk copies); the pad unit has no element (m = 0)
+        if (units.size() & 1) units.push_back({-1, -1});
         const int nu = (int)units.size();
         cu.unit_off = (int32_t)m.unit_total;
         cu.n_unit = nu;
@@ -648,7 +651,7 @@ std::string build_units(PrepMesh &m) {
             int32_t el[kPatchMax * 2];
             for (int k = 0; k < kPatchMax * 2; ++k) el[k] = -1;
             int pm = 0;
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < 2 && units[u][0] >= 0; ++h) {
                 const bool dup = units[u][h] < 0;
                 const int q = dup ? units[u][0] : units[u][h];
                 const uint16_t *rec = &m.pids[(size_t)(cd.patch_off + q) * kPatchIds];

@@ -30,7 +30,7 @@ struct SmemLayout {
 // records | values | fixed-point node sums | partial-sum destinations of the
 // shared nodes | per-thread dot partials | mbarrier.
 struct UnitSmem {
-    uint32_t node, val, acc, shd, dot, bar, total;
+    uint32_t node, val, acc, shd, urec, ubd, bar, total;   // the p.Ap partials reuse the urec region
 };
 
 struct MeshDev {

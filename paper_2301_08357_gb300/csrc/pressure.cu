@@ -237,10 +237,10 @@ static int set_smem_attrs() {
     CK(set_max_dyn_smem(k_cg2_chunks<3, double>));
     CK(set_max_dyn_smem(k_cg2_chunks_pipe<2>));
     CK(set_max_dyn_smem(k_cg2_chunks_pipe<3>));
-    CK(set_max_dyn_smem(k_cg2_units<false, 256>));
-    CK(set_max_dyn_smem(k_cg2_units<true, 256>));
-    CK(set_max_dyn_smem(k_cg2_units<false, 128>));
-    CK(set_max_dyn_smem(k_cg2_units<true, 128>));
+    CK(set_max_dyn_smem(k_cg2_units<false, 256, 2>));
+    CK(set_max_dyn_smem(k_cg2_units<true, 256, 2>));
+    CK(set_max_dyn_smem(k_cg2_units<false, 128, kUnitBlocks128>));
+    CK(set_max_dyn_smem(k_cg2_units<true, 128, kUnitBlocks128>));
     return batched_set_attrs();
 }
 
@@ -455,7 +455,8 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         U.val = take((uint64_t)pm.max_loc * 4);
         U.acc = take((uint64_t)pm.max_loc * 8);
         U.shd = take((uint64_t)round_up(pm.max_sh, kShPad) * 4);
-        U.dot = take((uint64_t)kChunkThreads * 8);
+        U.urec = take(std::max<uint64_t>((uint64_t)pm.max_unit * kURecWords * 4, (uint64_t)kChunkThreads * 8));
+        U.ubd = take((uint64_t)pm.max_unit * kPatchMax * 8);
         U.bar = take(8);
         U.total = off;
         m->use_units = U.total <= 200 * 1024;
@@ -464,9 +465,9 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
             // prefetches the data of the block about one wave after it)
             int per_sm = 0;
             cudaError_t oe = m->unit_threads == 128
-                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 128>, 128,
+                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 128, kUnitBlocks128>, 128,
                                                                                  U.total)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 256>, 256,
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 256, 2>, 256,
                                                                                  U.total);
             cudaGetLastError();
             d.prefetch_ahead = (oe == cudaSuccess && per_sm > 0) ? per_sm * c->sms : 0;
@@ -904,11 +905,11 @@ static void launch_k1_f32(ps_mesh *m, const Cg2Args<float> &a, cudaStream_t s) {
     const MeshDev &d = m->dev;
     if (m->use_units) {
         if (m->unit_threads == 128) {
-            if (d.lumped) k_cg2_units<true, 128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
-            else k_cg2_units<false, 128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
+            if (d.lumped) k_cg2_units<true, 128, kUnitBlocks128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 128, kUnitBlocks128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
         } else {
-            if (d.lumped) k_cg2_units<true, 256><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
-            else k_cg2_units<false, 256><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
+            if (d.lumped) k_cg2_units<true, 256, 2><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 256, 2><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
         }
     } else if (m->k1_pre) {
         if (d.dim == 2) k_cg2_chunks<2, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
