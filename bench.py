@@ -360,6 +360,9 @@ def kernel_roofline(P, m, stats, mode, fused, stream, workload, lumped=False):
     update = {"kernel": "k_cg2_update<float>", "bound": "hbm", "unit": "GB/s", "kernel_ms": upd_ms,
               "alg_bytes_per_launch": upd_bytes, "achieved": upd_bytes / (upd_ms / 1e3) / 1e9,
               "peak": peak, "frac": upd_bytes / (upd_ms / 1e3) / 1e9 / peak}
+    if stats.operator_kernel == 2:
+        update["note"] = ("blocks store their rz, rr shares only; the halo gather (halo_f32) sums them in its "
+                          "first block and ends the iteration")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": tr["bytes"] if tr else None,
             "traffic_source": tr["source"] if tr else "not captured for the kernel as it stands",

@@ -534,6 +534,8 @@ int ps_debug_cg_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, double *pap
  *   PS_KERNEL_CG_F32     FP32 CG operator kernel: chunk staging, p = D^-1 r + beta p,
  *                        q = A p, chunk shares of p.Ap (the solver's dominant kernel)
  *   PS_KERNEL_UPDATE_F32 FP32 CG update kernel: shared-node rows, x and r update, rz, rr
+ *                        (with the paired-patch kernel its blocks only store their
+ *                        rz, rr shares: the halo gather sums them)
  *   PS_KERNEL_APPLY_F32  FP32 operator apply alone (chunk kernel + shared-node sums)
  *   PS_KERNEL_RESID_F64  FP64 true-residual chunk kernel
  *   PS_KERNEL_CG_F64     FP64 CG operator kernel
@@ -541,8 +543,10 @@ int ps_debug_cg_apply(ps_mesh *mesh, const void *x_dev, void *y_dev, double *pap
  *                        u = D^-1 r, w = A u, gamma, delta, rho): the whole inner
  *                        iteration of the default mixed-precision solve
  *   PS_KERNEL_HALO_F32   the paired-patch kernel's halo gather ((D^-1 r, p) of every
- *                        shared node into its chunks' slots), the third kernel of
- *                        that iteration (nothing runs for the other kernel variants)
+ *                        shared node into its chunks' slots) with, in its first block,
+ *                        the sum of the update kernel's rz, rr shares and the end of
+ *                        the iteration: the third kernel of that iteration (nothing
+ *                        runs for the other kernel variants)
  * Errors: PS_EINVAL, PS_ESTATE (coefficients not set). */
 #define PS_KERNEL_CG_F32     0
 #define PS_KERNEL_UPDATE_F32 1

@@ -465,6 +465,33 @@ __device__ __forceinline__ void k2_f32(const MeshDev &m, const Cg2Args<float> &a
     }
 }
 
+// End of a CG iteration (one thread): rz, rr of the updated residual, the
+// iteration count, the stop tests and beta.
+__device__ __forceinline__ void cg2_update_tail(CgState *st, double rz, double rr) {
+    st->cnt_b = 0;
+    st->iters += 1;
+    st->rr = rr;
+    int done = 0;
+    if (!isfinite(rz) || !isfinite(rr)) {
+        st->status = kCgBreakdown;
+        done = 1;
+    } else if (rr <= st->stop_rr) {
+        st->status = kCgConverged;
+        done = 1;
+    } else if (st->iters >= st->max_iters) {
+        st->status = kCgMaxIter;
+        done = 1;
+    } else {
+        st->beta = rz / st->rz;
+        st->rz = rz;
+    }
+    if (done) st->done = 1;
+}
+
+// K2.  With the paired-patch operator kernel (a.halo set) the blocks only
+// store their shares of rz and rr: the halo gather that follows in the same
+// iteration sums them in its first block (k_halo_gather), concurrently with
+// its gather, so no block of K2 waits for the others.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     __shared__ double red[34];
@@ -484,37 +511,21 @@ __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
                (int64_t)gridDim.x * blockDim.x, arz, arr);
         double vrz, vrr;
         block_sum2(arz, arr, red, vrz, vrr);
+        const bool deferred = a.halo != nullptr;
         if (threadIdx.x == 0) {
             part_pack(vrz, a.z2[blockIdx.x]);
             part_pack(vrr, a.z2[a.g3 + blockIdx.x]);
-            const unsigned int t = atomic_add_acq_rel(&a.st->cnt_b, 1u);
-            s_last = (t == gridDim.x - 1);
+            if (!deferred) {
+                const unsigned int t = atomic_add_acq_rel(&a.st->cnt_b, 1u);
+                s_last = (t == gridDim.x - 1);
+            }
         }
+        if (deferred) return;
         __syncthreads();
         if (!s_last) return;
         double rz, rr;
         part_sum2(a.z2, a.z2 + a.g3, gridDim.x, red, rz, rr);
-        if (threadIdx.x == 0) {
-            CgState *st = a.st;
-            st->cnt_b = 0;
-            st->iters += 1;
-            st->rr = rr;
-            int done = 0;
-            if (!isfinite(rz) || !isfinite(rr)) {
-                st->status = kCgBreakdown;
-                done = 1;
-            } else if (rr <= st->stop_rr) {
-                st->status = kCgConverged;
-                done = 1;
-            } else if (st->iters >= st->max_iters) {
-                st->status = kCgMaxIter;
-                done = 1;
-            } else {
-                st->beta = rz / st->rz;
-                st->rz = rz;
-            }
-            if (done) st->done = 1;
-        }
+        if (threadIdx.x == 0) cg2_update_tail(a.st, rz, rr);
         return;
     }
     const int64_t n4 = m.n_int / 4;
@@ -602,27 +613,7 @@ __global__ void __launch_bounds__(256) k_cg2_update(MeshDev m, Cg2Args<T> a) {
     if (!s_last) return;
     double rz, rr;
     part_sum2(a.z2, a.z2 + a.g3, gridDim.x, red, rz, rr);
-    if (threadIdx.x == 0) {
-        CgState *st = a.st;
-        st->cnt_b = 0;
-        st->iters += 1;
-        st->rr = rr;
-        int done = 0;
-        if (!isfinite(rz) || !isfinite(rr)) {
-            st->status = kCgBreakdown;
-            done = 1;
-        } else if (rr <= st->stop_rr) {
-            st->status = kCgConverged;
-            done = 1;
-        } else if (st->iters >= st->max_iters) {
-            st->status = kCgMaxIter;
-            done = 1;
-        } else {
-            st->beta = rz / st->rz;
-            st->rz = rz;
-        }
-        if (done) st->done = 1;
-    }
+    if (threadIdx.x == 0) cg2_update_tail(a.st, rz, rr);
 }
 
 // Start of a CG run from the residual in r (FP64 mode) or from r64 * scale

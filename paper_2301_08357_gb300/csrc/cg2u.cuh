@@ -233,70 +233,86 @@ __device__ __forceinline__ float2 unit_scale(float dmax, float vmax, int n_star)
     return make_float2(ldexpf(1.0f, max(-126, min(127, sx))), ldexpf(1.0f, max(-126, min(127, -sx))));
 }
 
-// Resident 128-thread blocks per SM the operator kernel is compiled for: it
+// Resident 128-thread blocks per SM the operator kernels are compiled for: it
 // sets the register budget of a thread (65536 / (128 * 5) -> 96 registers,
 // a few bytes of spills) and, with ~45 KB of shared memory per 3,072-tet
-// chunk, five blocks (20 warps) fit an SM.  Measured on 160^3 Kuhn: 169.7 us
-// per pass against 175.1 us with four blocks (128 registers).
+// chunk, five blocks (20 warps) fit an SM.  Measured on 160^3 Kuhn (one
+// chunk per block): 169.7 us per pass against 175.1 us with four blocks (128
+// registers), 193 us with three and 243 us with two.
 constexpr int kUnitBlocks128 = 5;
 
-// K1 on paired patches: one block of NT threads (128 or 256) per chunk,
-// MINB blocks per SM (the register budget of a thread).
-template <bool LUMP, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float> a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const UnitSmem &L = m.smu;
-    NodeF *s_node = reinterpret_cast<NodeF *>(smem + L.node);
-    float *s_val = reinterpret_cast<float *>(smem + L.val);
-    int *s_acc = reinterpret_cast<int *>(smem + L.acc);                // two ints per node
-    int32_t *s_shd = reinterpret_cast<int32_t *>(smem + L.shd);
-    uint32_t *s_urec = reinterpret_cast<uint32_t *>(smem + L.urec);     // the chunk's unit records
-    float2 *s_ubd = reinterpret_cast<float2 *>(smem + L.ubd);           // beta*dt^2/6 per (element, half)
-    float2 *s_dot = reinterpret_cast<float2 *>(smem + L.urec);          // after the element phase
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + L.bar);
-    __shared__ float s_beta;
-    __shared__ unsigned int s_vmax;
-    __shared__ int s_done;
-    __shared__ bool s_last;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        s_done = a.st->done;
-        s_beta = (float)a.st->beta;
-        s_vmax = 0u;
-        mbar_init(s_bar, 1);
-        fence_mbar_init();
+// ---------------------------------------------------------------- phases of a chunk
+struct UnitShared {
+    NodeF *node;
+    float *val;
+    int *acc;          // two ints per node
+    uint32_t *urec;    // the chunk's unit records
+    float2 *ubd;       // beta*dt^2/6 per (element, half)
+    uint64_t *bar;
+};
+__device__ __forceinline__ UnitShared unit_shared(unsigned char *smem, const UnitSmem &L) {
+    UnitShared S;
+    S.node = reinterpret_cast<NodeF *>(smem + L.node);
+    S.val = reinterpret_cast<float *>(smem + L.val);
+    S.acc = reinterpret_cast<int *>(smem + L.acc);
+    S.urec = reinterpret_cast<uint32_t *>(smem + L.urec);
+    S.ubd = reinterpret_cast<float2 *>(smem + L.ubd);
+    S.bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    return S;
+}
+
+// The fields of a chunk the paired kernels use (ChunkDesc, ChunkUnits).
+struct UnitChunk {
+    int node_off, n_loc, n_int, int_begin, sh_off, n_sh, unit_off, n_unit, max_star;
+};
+__device__ __forceinline__ UnitChunk unit_chunk(const MeshDev &m, int c) {
+    const ChunkDesc cd = m.chunks[c];
+    const ChunkUnits cu = m.chunks_u[c];
+    return UnitChunk{cd.node_off, cd.n_loc, cd.n_int, cd.int_begin, cd.sh_off, cd.n_sh,
+                     cu.unit_off, cu.n_unit, cu.max_star};
+}
+
+// One thread: bulk copies of the chunk's node records, shared-node
+// destinations (into shd) and unit records with their beta*dt^2/6 (even unit
+// counts: 16-byte multiples), all on one mbarrier phase.
+__device__ __forceinline__ void unit_stage(const MeshDev &m, const UnitChunk &cd, const UnitShared &S,
+                                           int32_t *shd) {
+    const UnitChunk &cu = cd;
+    const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
+    const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
+    const uint32_t b_rec = (uint32_t)cu.n_unit * kURecWords * 4u;
+    const uint32_t b_bd = (uint32_t)cu.n_unit * kPatchMax * 8u;
+    fence_proxy_async_smem();      // earlier generic accesses of these buffers before the async writes
+    mbar_arrive_expect_tx(S.bar, b_node + b_shd + b_rec + b_bd);
+    bulk_g2s(S.node, m.node32 + cd.node_off, b_node, S.bar);
+    if (b_shd) bulk_g2s(shd, m.sh_dest + cd.sh_off, b_shd, S.bar);
+    if (b_rec) {
+        bulk_g2s(S.urec, m.urec + (int64_t)cu.unit_off * kURecWords, b_rec, S.bar);
+        bulk_g2s(S.ubd, m.ubd + (int64_t)cu.unit_off * kPatchMax * 2, b_bd, S.bar);
     }
-    __syncthreads();
-    if (s_done) return;
-    const ChunkDesc cd = m.chunks[blockIdx.x];
-    const ChunkUnits cu = m.chunks_u[blockIdx.x];
-    if (tid == 0) {
-        // node records, shared-node destinations and the unit records with
-        // their beta*dt^2/6 (even unit counts: 16-byte multiples)
-        const uint32_t b_node = (uint32_t)cd.n_loc * sizeof(NodeF);
-        const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
-        const uint32_t b_rec = (uint32_t)cu.n_unit * kURecWords * 4u;
-        const uint32_t b_bd = (uint32_t)cu.n_unit * kPatchMax * 8u;
-        mbar_arrive_expect_tx(s_bar, b_node + b_shd + b_rec + b_bd);
-        bulk_g2s(s_node, m.node32 + cd.node_off, b_node, s_bar);
-        if (b_shd) bulk_g2s(s_shd, m.sh_dest + cd.sh_off, b_shd, s_bar);
-        if (b_rec) {
-            bulk_g2s(s_urec, m.urec + (int64_t)cu.unit_off * kURecWords, b_rec, s_bar);
-            bulk_g2s(s_ubd, m.ubd + (int64_t)cu.unit_off * kPatchMax * 2, b_bd, s_bar);
-        }
-    }
-    const float beta = s_beta;
+}
+
+// p = D^-1 r + beta p on the chunk's nodes into val, node sums zeroed, the
+// chunk maximum of |v| into *vmax.  Thread tid handles local nodes
+// l = tid + NT j, up to eight per round, all loads of a round before any
+// store (the stores to p could alias them): one round of loads for chunks of
+// up to 8 NT nodes.  No Dirichlet mask is needed for v (D^-1 = 0 and r = 0
+// there and p starts at 0).  Bit j of the result flags an interior Dirichlet
+// node, D^-1 = 0 (its row of q is masked in the node phase; shared rows are
+// masked by the update kernel).  Requires n_loc <= 32 NT.
+template <int NT>
+__device__ __forceinline__ uint32_t unit_gather(const Cg2Args<float> &a, const UnitChunk &cd, float beta,
+                                                const UnitShared &S, unsigned int *vmax_out, int tid) {
+    constexpr int kG = 8;
     const int n_loc = cd.n_loc, n_int = cd.n_int;
-    // p = D^-1 r + beta p on the chunk's nodes (loads of four nodes before any
-    // store: the stores to p could alias them); no Dirichlet mask is needed
-    // (D^-1 = 0 and r = 0 there and p starts at 0); the node sums start at 0
     float vmax = 0.f;
-    for (int l0 = tid; l0 < n_loc; l0 += 4 * NT) {
+    uint32_t dmask = 0u;
+    for (int l0 = tid, j0 = 0; l0 < n_loc; l0 += kG * NT, j0 += kG) {
         // interior nodes: D^-1, r, p contiguous from int_begin; shared
         // nodes: (D^-1 r, p) from the chunk's contiguous halo slots
-        float dv[4], rv[4], pv[4];
+        float dv[kG], rv[kG], pv[kG];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kG; ++k) {
             const int l = l0 + k * NT;
             dv[k] = rv[k] = pv[k] = 0.f;
             if (l < n_int) {
@@ -312,108 +328,120 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kG; ++k) {
             const int l = l0 + k * NT;
             if (l < n_loc) {
                 // shared nodes: fma(beta, p, 1 * z) = fma(beta, p, z), the value K2 stores
                 const float v = cg_dir(dv[k], rv[k], beta, pv[k]);
-                s_val[l] = v;
-                reinterpret_cast<int2 *>(s_acc)[l] = make_int2(0, 0);
+                S.val[l] = v;
+                reinterpret_cast<int2 *>(S.acc)[l] = make_int2(0, 0);
                 vmax = fmaxf(vmax, fabsf(v));
-                if (l < n_int) a.p[cd.int_begin + l] = v;
+                if (l < n_int) {
+                    a.p[cd.int_begin + l] = v;
+                    if (dv[k] == 0.f) dmask |= 1u << (j0 + k);
+                }
             }
         }
     }
-    {   // chunk maximum of |v| (non-negative floats order as their bit patterns)
-        const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
-        if ((tid & 31) == 0 && wmax) atomicMax(&s_vmax, wmax);
+    // non-negative floats order as their bit patterns
+    const unsigned int wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+    if ((tid & 31) == 0 && wmax) atomicMax(vmax_out, wmax);
+    return dmask;
+}
+
+// Element phase: one unit per thread and round into the node sums (nothing
+// to add when the scale is 0, i.e. every input is 0).
+template <bool LUMP, int NT>
+__device__ __forceinline__ void unit_elements(const UnitChunk &cu, const UnitShared &S, float scale, int tid) {
+    if (scale == 0.f) return;
+    for (int u = tid; u < cu.n_unit; u += NT) {
+        const uint32_t *rec = S.urec + u * kURecWords;
+        const float2 Su = make_float2(scale, (rec[0] & kUnitDup) ? 0.f : scale);
+        unit_eval_any<LUMP>(S.node, S.val, rec, S.ubd + u * kPatchMax, S.acc, Su);
     }
-    // the data of a chunk that a block launched later will process, into L2
-    if (tid == 0 && m.prefetch_ahead > 0 && blockIdx.x + m.prefetch_ahead < (unsigned)m.n_chunks) {
-        const int fc = blockIdx.x + m.prefetch_ahead;
-        const ChunkDesc fd = m.chunks[fc];
-        const ChunkUnits fu = m.chunks_u[fc];
-        l2_prefetch(m.node32 + fd.node_off, (size_t)fd.n_loc * sizeof(NodeF));
-        l2_prefetch(m.urec + (size_t)fu.unit_off * kURecWords, (size_t)fu.n_unit * kURecWords * 4);
-        l2_prefetch(m.ubd + (size_t)fu.unit_off * kPatchMax * 2, (size_t)fu.n_unit * kPatchMax * 8);
-        l2_prefetch(a.dinv + fd.int_begin, (size_t)fd.n_int * 4);
-        l2_prefetch(a.r + fd.int_begin, (size_t)fd.n_int * 4);
-        l2_prefetch(a.p + fd.int_begin, (size_t)fd.n_int * 4);
-        l2_prefetch(a.halo + fd.sh_off, (size_t)fd.n_sh * 8);
-        l2_prefetch(m.sh_dest + fd.sh_off, (size_t)fd.n_sh * 4);
-    }
-    const float dmax = __ldg(m.dmax + blockIdx.x);
-    uint32_t ph = 0;
-    {
-        bool ok = mbar_wait_bounded(s_bar, ph);
-        ok = __syncthreads_and(ok);   // also publishes s_val, s_acc and s_vmax
-        if (!ok) {
-            if (tid == 0) atomicOr(m.err, kErrMbarTimeout);
-            mbar_wait_bounded(s_bar, ph);
-            return;
-        }
-    }
-    // ---- element phase: one unit per thread and round (nothing to add when v = 0)
-    const float2 sc = unit_scale(dmax, __uint_as_float(s_vmax), cu.max_star);
-    if (sc.x != 0.f) {
-        for (int u = tid; u < cu.n_unit; u += NT) {
-            const uint32_t *rec = s_urec + u * kURecWords;
-            const float2 S = make_float2(sc.x, (rec[0] & kUnitDup) ? 0.f : sc.x);
-            unit_eval_any<LUMP>(s_node, s_val, rec, s_ubd + u * kPatchMax, s_acc, S);
-        }
-    }
-    __syncthreads();
-    // ---- node phase: each node's sum, rounded to FP32 once
-    const float inv = sc.y;
+}
+
+// Node phase: each node's sum rounded to FP32 once, into q (interior, masked
+// on Dirichlet rows) or the node's partial slot (shared); the thread's share
+// of p.Ap = sum_e p_e^T A_e p_e over the chunk is returned.
+template <int NT>
+__device__ __forceinline__ DotF unit_nodes(const Cg2Args<float> &a, const UnitChunk &cd, const UnitShared &S,
+                                           const int32_t *shd, float inv, uint32_t dmask, int tid) {
     DotF acc;
-    for (int l = tid; l < n_loc; l += NT) {
-        const int2 hl = reinterpret_cast<const int2 *>(s_acc)[l];
+    for (int l = tid, j = 0; l < cd.n_loc; l += NT, ++j) {
+        const int2 hl = reinterpret_cast<const int2 *>(S.acc)[l];
         float s = fmaf((float)hl.x, 16777216.0f, (float)hl.y) * inv;
-        acc.add_prod(s_val[l], s);                 // element-wise p^T A_e p over the chunk
-        if (is_dirichlet(s_node[l].w)) s = 0.f;
-        if (l < n_int)
-            a.q[cd.int_begin + l] = s;
+        acc.add_prod(S.val[l], s);
+        if (l < cd.n_int)
+            a.q[cd.int_begin + l] = (dmask >> j) & 1u ? 0.f : s;
         else
-            a.partial[s_shd[l - n_int]] = s;
+            a.partial[shd[l - cd.n_int]] = s;
     }
-    // ---- the chunk's share of p.Ap: one warp sums the threads' partials in order
-    s_dot[tid] = make_float2(acc.hi, acc.lo);
-    __syncthreads();
-    if (tid >= 32) return;
-    DotF t;
-#pragma unroll
-    for (int k = 0; k < NT / 32; ++k) {
-        const float2 v = s_dot[k * 32 + tid];
-        t.merge(v.x, v.y);
-    }
-    t = warp_merge(t);
+    return acc;
+}
+
+// Bulk prefetch into L2 of the data of chunk fc (node records, unit records,
+// beta, interior vectors, halo, destinations).
+__device__ __forceinline__ void unit_l2_prefetch(const MeshDev &m, const Cg2Args<float> &a, int fc) {
+    const ChunkDesc fd = m.chunks[fc];
+    const ChunkUnits fu = m.chunks_u[fc];
+    l2_prefetch(m.node32 + fd.node_off, (size_t)fd.n_loc * sizeof(NodeF));
+    l2_prefetch(m.urec + (size_t)fu.unit_off * kURecWords, (size_t)fu.n_unit * kURecWords * 4);
+    l2_prefetch(m.ubd + (size_t)fu.unit_off * kPatchMax * 2, (size_t)fu.n_unit * kPatchMax * 8);
+    l2_prefetch(a.dinv + fd.int_begin, (size_t)fd.n_int * 4);
+    l2_prefetch(a.r + fd.int_begin, (size_t)fd.n_int * 4);
+    l2_prefetch(a.p + fd.int_begin, (size_t)fd.n_int * 4);
+    l2_prefetch(a.halo + fd.sh_off, (size_t)fd.n_sh * 8);
+    l2_prefetch(m.sh_dest + fd.sh_off, (size_t)fd.n_sh * 4);
+}
+
+__device__ __forceinline__ unsigned int unit_ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void unit_red_release_add(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The operator pass's completion, in one extra block launched after the
+// chunk blocks: each chunk block stores its share of p.Ap and counts itself
+// with a release add (it does not wait for the count); this block waits
+// (bounded) until every chunk is counted, sums the shares in chunk order
+// (thread t takes chunks t, t + NT, ...; warps merged in order) and sets
+// alpha = rz / p.Ap.  The chunk blocks never wait for it, so they always
+// complete; on timeout the error flag is set and alpha is left unchanged.
+template <int NT>
+__device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_chunks, int *err, int tid) {
+    __shared__ int s_ok;
+    __shared__ float2 s_w[NT / 32];
     if (tid == 0) {
-        a.pq[blockIdx.x] = part_pack((double)t.hi + (double)t.lo);
-        const unsigned int c = atomic_add_acq_rel(&a.st->cnt_a, 1u);
-        s_last = (c == gridDim.x - 1);
-    }
-    __syncwarp();
-    if (!s_last) return;
-    // last chunk to finish: alpha = rz / p.Ap (one warp; lane i sums chunks
-    // i, i + 32, ... into eight accumulators by turn, merged in a fixed order)
-    constexpr int kAcc = 8;
-    DotF part[kAcc];
-    for (int i0 = tid; i0 < (int)gridDim.x; i0 += 32 * kAcc) {
-#pragma unroll
-        for (int k = 0; k < kAcc; ++k) {
-            const int i = i0 + 32 * k;
-            if (i < (int)gridDim.x) {
-                const float2 v = __ldcg(a.pq + i);
-                part[k].merge(v.x, v.y);
+        int ok = 0;
+        for (uint32_t i = 0; i < kGridSpinLimit; ++i) {
+            if (unit_ld_acquire(&a.st->cnt_a) >= (unsigned int)n_chunks) {
+                ok = 1;
+                break;
             }
+            __nanosleep(64);
         }
+        if (!ok) atomicOr(err, kErrGridTimeout);
+        s_ok = ok;
     }
-    DotF tot = part[0];
-#pragma unroll
-    for (int k = 1; k < kAcc; ++k) tot.merge(part[k].hi, part[k].lo);
-    tot = warp_merge(tot);
+    __syncthreads();
+    if (!s_ok) return;
+    DotF acc;
+    for (int i = tid; i < n_chunks; i += NT) {
+        const float2 v = __ldcg(a.pq + i);
+        acc.merge(v.x, v.y);
+    }
+    acc = warp_merge(acc);
+    if ((tid & 31) == 0) s_w[tid >> 5] = make_float2(acc.hi, acc.lo);
+    __syncthreads();
     if (tid == 0) {
-        const double pq = (double)tot.hi + (double)tot.lo;
+        DotF t;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t.merge(s_w[w].x, s_w[w].y);
+        const double pq = (double)t.hi + (double)t.lo;
         CgState *st = a.st;
         st->cnt_a = 0;
         st->pq = pq;
@@ -423,6 +451,77 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
         } else {
             st->alpha = st->rz / pq;
         }
+    }
+}
+
+// The chunk's share of p.Ap from the threads' accumulators: each warp merges
+// its lanes (fixed tree), warp w writes wdot[w]; after a barrier one thread
+// merges the warps in order (chunk_share).
+template <int NT>
+__device__ __forceinline__ void unit_warp_share(DotF acc, float2 *wdot, int tid) {
+    acc = warp_merge(acc);
+    if ((tid & 31) == 0) wdot[tid >> 5] = make_float2(acc.hi, acc.lo);
+}
+template <int NT>
+__device__ __forceinline__ float2 chunk_share(const float2 *wdot) {
+    DotF t;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) t.merge(wdot[w].x, wdot[w].y);
+    return part_pack((double)t.hi + (double)t.lo);
+}
+
+// K1 on paired patches: one block of NT threads (128 or 256) per chunk and
+// one more block (the last) for the completion, MINB blocks per SM (the
+// register budget of a thread).
+template <bool LUMP, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const UnitShared S = unit_shared(smem, m.smu);
+    int32_t *s_shd = reinterpret_cast<int32_t *>(smem + m.smu.shd);
+    __shared__ float s_beta;
+    __shared__ unsigned int s_vmax;
+    __shared__ int s_done;
+    __shared__ float2 s_wdot[NT / 32];
+    const int tid = threadIdx.x;
+    if (blockIdx.x == (unsigned)m.n_chunks) {
+        if (tid == 0) s_done = ld_flag(&a.st->done);
+        __syncthreads();
+        if (!s_done) unit_reduce_alpha<NT>(a, m.n_chunks, m.err, tid);
+        return;
+    }
+    const UnitChunk uc = unit_chunk(m, blockIdx.x);   // (issued together with the state read)
+    if (tid == 0) {
+        s_done = a.st->done;
+        s_beta = (float)a.st->beta;
+        s_vmax = 0u;
+        mbar_init(S.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (s_done) return;
+    if (tid == 0) unit_stage(m, uc, S, s_shd);
+    const uint32_t dmask = unit_gather<NT>(a, uc, s_beta, S, &s_vmax, tid);
+    // the data of a chunk that a block launched later will process, into L2
+    if (tid == 0 && m.prefetch_ahead > 0 && blockIdx.x + m.prefetch_ahead < (unsigned)m.n_chunks)
+        unit_l2_prefetch(m, a, blockIdx.x + m.prefetch_ahead);
+    const float dmax = __ldg(m.dmax + blockIdx.x);
+    {
+        bool ok = mbar_wait_bounded(S.bar, 0);
+        ok = __syncthreads_and(ok);   // also publishes val, acc and s_vmax
+        if (!ok) {
+            if (tid == 0) atomicOr(m.err, kErrMbarTimeout);
+            mbar_wait_bounded(S.bar, 0);
+            return;
+        }
+    }
+    const float2 sc = unit_scale(dmax, __uint_as_float(s_vmax), uc.max_star);
+    unit_elements<LUMP, NT>(uc, S, sc.x, tid);
+    __syncthreads();
+    unit_warp_share<NT>(unit_nodes<NT>(a, uc, S, s_shd, sc.y, dmask, tid), s_wdot, tid);
+    __syncthreads();
+    if (tid == 0) {
+        a.pq[blockIdx.x] = chunk_share<NT>(s_wdot);
+        unit_red_release_add(&a.st->cnt_a, 1u);
     }
 }
 
@@ -450,15 +549,30 @@ static __global__ void k_chunk_dmax(MeshDev m, float *__restrict__ dmax) {
 // The halo of the paired-patch kernel: every chunk-major shared slot j (node
 // i = sh_ids[j]) gets (D^-1_i r_i, p_i) -- after each update kernel (the next
 // operator pass reads it contiguously per chunk), at the start of a CG run
-// and before ps_debug_cg_apply.  Pads (sh_ids = -1) are skipped.
-static __global__ void k_halo_gather(int64_t n_slots, const int32_t *__restrict__ sh_ids, const float *__restrict__ r,
-                                     const float *__restrict__ p, const float *__restrict__ dinv,
-                                     float2 *__restrict__ halo, const CgState *st) {
-    if (st && ld_flag(&st->done)) return;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_slots;
-         j += (int64_t)gridDim.x * blockDim.x) {
+// and before ps_debug_cg_apply.  Pads (sh_ids = -1) are skipped.  Inside the
+// iteration (reduce = 1) the first block instead sums the update kernel's
+// block shares of rz and rr in block order and ends the iteration
+// (cg2_update_tail), while the other blocks gather; a run that was already
+// done before this iteration's update kernel does nothing.
+static __global__ void __launch_bounds__(256) k_halo_gather(int64_t n_slots, const int32_t *__restrict__ sh_ids,
+                                                            Cg2Args<float> a, int reduce) {
+    if (reduce) {
+        if (ld_flag(&a.st->done)) return;
+        if (blockIdx.x == 0) {
+            __shared__ double red[34];
+            double rz, rr;
+            part_sum2(a.z2, a.z2 + a.g3, a.g3, red, rz, rr);
+            if (threadIdx.x == 0) cg2_update_tail(a.st, rz, rr);
+            return;
+        }
+    }
+    const int64_t b = reduce ? blockIdx.x - 1 : blockIdx.x, nb = reduce ? gridDim.x - 1 : gridDim.x;
+    const float *__restrict__ r = a.r;
+    const float *__restrict__ p = a.p;
+    const float *__restrict__ dinv = a.dinv;
+    for (int64_t j = b * blockDim.x + threadIdx.x; j < n_slots; j += nb * blockDim.x) {
         const int i = __ldg(sh_ids + j);
-        if (i >= 0) halo[j] = make_float2(__fmul_rn(__ldg(dinv + i), r[i]), p[i]);
+        if (i >= 0) a.halo[j] = make_float2(__fmul_rn(__ldg(dinv + i), r[i]), p[i]);
     }
 }
 

@@ -30,7 +30,7 @@ struct SmemLayout {
 // records | values | fixed-point node sums | partial-sum destinations of the
 // shared nodes | per-thread dot partials | mbarrier.
 struct UnitSmem {
-    uint32_t node, val, acc, shd, urec, ubd, bar, total;   // the p.Ap partials reuse the urec region
+    uint32_t node, val, acc, shd, urec, ubd, bar, total;
 };
 
 struct MeshDev {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_shared(MeshDev m, VecArgs<T> a, int n_f
         for (int k = kb; k < ke; ++k) sum += a.partial[k];
         const bool dir = m.dirichlet[g] != 0;
         if (MODE == kApply) {
-            a.y[g] = sum;
+            a.y[g] = dir ? T(0) : sum;   // (partials of Dirichlet rows may be unmasked: paired-patch kernels)
         } else if (MODE == kCG) {
             T v = cg_dir(a.dinv[g], a.r[g], beta_cg, a.p[g]);
             if (dir) v = T(0);

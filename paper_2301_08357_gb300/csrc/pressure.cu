@@ -455,20 +455,22 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         U.val = take((uint64_t)pm.max_loc * 4);
         U.acc = take((uint64_t)pm.max_loc * 8);
         U.shd = take((uint64_t)round_up(pm.max_sh, kShPad) * 4);
-        U.urec = take(std::max<uint64_t>((uint64_t)pm.max_unit * kURecWords * 4, (uint64_t)kChunkThreads * 8));
+        U.urec = take((uint64_t)pm.max_unit * kURecWords * 4);
         U.ubd = take((uint64_t)pm.max_unit * kPatchMax * 8);
         U.bar = take(8);
         U.total = off;
-        m->use_units = U.total <= 200 * 1024;
+        // node ids of the unit records are 16-bit; a thread's Dirichlet mask
+        // covers 32 nodes of the chunk
+        m->use_units = U.total <= 200 * 1024 && pm.max_loc <= 32 * m->unit_threads;
         if (m->use_units) {
             // L2 prefetch distance: the chunks resident at once (a block
             // prefetches the data of the block about one wave after it)
             int per_sm = 0;
             cudaError_t oe = m->unit_threads == 128
-                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 128, kUnitBlocks128>, 128,
-                                                                                 U.total)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg2_units<false, 256, 2>, 256,
-                                                                                 U.total);
+                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                       &per_sm, k_cg2_units<false, 128, kUnitBlocks128>, 128, U.total)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                       &per_sm, k_cg2_units<false, 256, 2>, 256, U.total);
             cudaGetLastError();
             d.prefetch_ahead = (oe == cudaSuccess && per_sm > 0) ? per_sm * c->sms : 0;
         }
@@ -904,12 +906,13 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
 static void launch_k1_f32(ps_mesh *m, const Cg2Args<float> &a, cudaStream_t s) {
     const MeshDev &d = m->dev;
     if (m->use_units) {
+        const int g = d.n_chunks + 1;   // the chunks and the completion block
         if (m->unit_threads == 128) {
-            if (d.lumped) k_cg2_units<true, 128, kUnitBlocks128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
-            else k_cg2_units<false, 128, kUnitBlocks128><<<d.n_chunks, 128, d.smu.total, s>>>(d, a);
+            if (d.lumped) k_cg2_units<true, 128, kUnitBlocks128><<<g, 128, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 128, kUnitBlocks128><<<g, 128, d.smu.total, s>>>(d, a);
         } else {
-            if (d.lumped) k_cg2_units<true, 256, 2><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
-            else k_cg2_units<false, 256, 2><<<d.n_chunks, 256, d.smu.total, s>>>(d, a);
+            if (d.lumped) k_cg2_units<true, 256, 2><<<g, 256, d.smu.total, s>>>(d, a);
+            else k_cg2_units<false, 256, 2><<<g, 256, d.smu.total, s>>>(d, a);
         }
     } else if (m->k1_pre) {
         if (d.dim == 2) k_cg2_chunks<2, float, true><<<d.n_chunks, kBlock, d.sm32.total, s>>>(d, a);
@@ -981,8 +984,8 @@ static int enqueue_cg_iters(ps_mesh *m, int iters, bool fused, cudaStream_t s) {
         m->launches += 2;
         if (sizeof(T) == 4 && a.halo) {
             const Cg2Args<float> &af = reinterpret_cast<const Cg2Args<float> &>(a);
-            k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
-                m->prep.sh_total, m->dev.sh_ids, af.r, af.p, af.dinv, af.halo, af.st);
+            k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms) + 1, kBlock, 0, s>>>(m->prep.sh_total,
+                                                                                        m->dev.sh_ids, af, 1);
             m->launches += 1;
         }
         CK(cudaGetLastError());
@@ -1213,7 +1216,7 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
                 m->launches += 1;
                 if (a.halo) {
                     k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
-                        m->prep.sh_total, m->dev.sh_ids, a.r, a.p, a.dinv, a.halo, nullptr);
+                        m->prep.sh_total, m->dev.sh_ids, a, 0);
                     m->launches += 1;
                 }
             }
@@ -1359,8 +1362,8 @@ extern "C" int ps_debug_cg_apply(ps_mesh *m, const void *x, void *y, double *pap
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     const Cg2Args<float> ca = cg2_args<float>(m);
     if (ca.halo)
-        k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
-            m->prep.sh_total, m->dev.sh_ids, ca.r, ca.p, ca.dinv, ca.halo, nullptr);
+        k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(m->prep.sh_total,
+                                                                                m->dev.sh_ids, ca, 0);
     launch_k1_f32(m, ca, s);
     VecArgs<float> va;
     std::memset(&va, 0, sizeof(va));
@@ -1514,9 +1517,11 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
                 break;
             case 6: {
                 const Cg2Args<float> a = cg2_args<float>(m);
+                // as in the iteration: the gather and, in the first block, the
+                // update kernel's rz, rr reduction and the end of the iteration
                 if (a.halo)
-                    k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(
-                        m->prep.sh_total, d.sh_ids, a.r, a.p, a.dinv, a.halo, nullptr);
+                    k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms) + 1, kBlock, 0, s>>>(m->prep.sh_total,
+                                                                                            d.sh_ids, a, 1);
                 break;
             }
         }

@@ -196,6 +196,7 @@ def test_paired_kernel_solves_match_oracle(env, name, make, chunk, lumped, threa
     m = P.ps_mesh_upload(ctx, case.dim, case.coords, case.conn, case.dirichlet, chunk_elems=chunk,
                          periodic=master, operator_kernel=2, operator_threads=threads)
     try:
+        assert P.ps_mesh_get_stats(m).operator_kernel == 2
         P.ps_coeff_set(m, case.alpha, case.beta, case.dt2)
         if lumped:
             P.ps_mesh_set_mass(m, P.PS_MASS_LUMPED)
