@@ -314,7 +314,7 @@ def kernel_roofline(P, m, stats, mode, fused, stream, workload, lumped=False):
     if fused:
         which, kname = P.PS_KERNEL_CG1_F32, "k_cg1_chunks<%d>" % stats.dim
     elif mode == P.PS_MODE_MIXED and stats.operator_kernel == 2:
-        which, kname = P.PS_KERNEL_CG_F32, "k_cg2_units<%s,128>" % ("true" if lumped else "false")
+        which, kname = P.PS_KERNEL_CG_F32, "k_cg2_units<%s,128,5>" % ("true" if lumped else "false")
     elif mode == P.PS_MODE_MIXED:
         which, kname = P.PS_KERNEL_CG_F32, "k_cg2_chunks<%d,float>" % stats.dim
     else:

@@ -453,8 +453,7 @@ __device__ __forceinline__ void k2_f32(const MeshDev &m, const Cg2Args<float> &a
                     pi = 0.f;
                     qi = 0.f;
                 }
-                a.p[i] = pi;
-                a.q[i] = qi;
+                a.p[i] = pi;   // (a shared row's q is not stored: nothing reads it after this kernel)
             }
             a.x[i] += alpha * pi;
             const float ri = rv[k] - alpha * qi;

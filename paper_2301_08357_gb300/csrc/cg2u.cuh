@@ -60,14 +60,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 (the range is trimmed inward to
-// 16-byte boundaries, so nothing outside it is touched).
-__device__ __forceinline__ void l2_prefetch(const void *p, size_t bytes) {
-    const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
-    if (e > b)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((uint32_t)(e - b)) : "memory");
-}
-
 struct P3 {
     float2 x, y, z;
 };
@@ -380,21 +372,6 @@ __device__ __forceinline__ DotF unit_nodes(const Cg2Args<float> &a, const UnitCh
     return acc;
 }
 
-// Bulk prefetch into L2 of the data of chunk fc (node records, unit records,
-// beta, interior vectors, halo, destinations).
-__device__ __forceinline__ void unit_l2_prefetch(const MeshDev &m, const Cg2Args<float> &a, int fc) {
-    const ChunkDesc fd = m.chunks[fc];
-    const ChunkUnits fu = m.chunks_u[fc];
-    l2_prefetch(m.node32 + fd.node_off, (size_t)fd.n_loc * sizeof(NodeF));
-    l2_prefetch(m.urec + (size_t)fu.unit_off * kURecWords, (size_t)fu.n_unit * kURecWords * 4);
-    l2_prefetch(m.ubd + (size_t)fu.unit_off * kPatchMax * 2, (size_t)fu.n_unit * kPatchMax * 8);
-    l2_prefetch(a.dinv + fd.int_begin, (size_t)fd.n_int * 4);
-    l2_prefetch(a.r + fd.int_begin, (size_t)fd.n_int * 4);
-    l2_prefetch(a.p + fd.int_begin, (size_t)fd.n_int * 4);
-    l2_prefetch(a.halo + fd.sh_off, (size_t)fd.n_sh * 8);
-    l2_prefetch(m.sh_dest + fd.sh_off, (size_t)fd.n_sh * 4);
-}
-
 __device__ __forceinline__ unsigned int unit_ld_acquire(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -429,11 +406,23 @@ __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_ch
     }
     __syncthreads();
     if (!s_ok) return;
-    DotF acc;
-    for (int i = tid; i < n_chunks; i += NT) {
-        const float2 v = __ldcg(a.pq + i);
-        acc.merge(v.x, v.y);
+    // eight loads in flight per thread: thread t takes chunks t + NT (8 i + k)
+    // into accumulator k, merged in k order
+    constexpr int kAcc = 8;
+    DotF part[kAcc];
+    for (int i0 = tid; i0 < n_chunks; i0 += NT * kAcc) {
+        float2 v[kAcc];
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) {
+            const int i = i0 + NT * k;
+            v[k] = i < n_chunks ? __ldcg(a.pq + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) part[k].merge(v[k].x, v[k].y);
     }
+    DotF acc = part[0];
+#pragma unroll
+    for (int k = 1; k < kAcc; ++k) acc.merge(part[k].hi, part[k].lo);
     acc = warp_merge(acc);
     if ((tid & 31) == 0) s_w[tid >> 5] = make_float2(acc.hi, acc.lo);
     __syncthreads();
@@ -482,6 +471,7 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
     __shared__ unsigned int s_vmax;
     __shared__ int s_done;
     __shared__ float2 s_wdot[NT / 32];
+    __shared__ UnitChunk s_uc;
     const int tid = threadIdx.x;
     if (blockIdx.x == (unsigned)m.n_chunks) {
         if (tid == 0) s_done = ld_flag(&a.st->done);
@@ -489,11 +479,14 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
         if (!s_done) unit_reduce_alpha<NT>(a, m.n_chunks, m.err, tid);
         return;
     }
-    const UnitChunk uc = unit_chunk(m, blockIdx.x);   // (issued together with the state read)
+    // the chunk's fields: in registers for the staging and the gather (read
+    // together with the CG state), from shared memory in the later phases
+    const UnitChunk uc = unit_chunk(m, blockIdx.x);
     if (tid == 0) {
         s_done = a.st->done;
         s_beta = (float)a.st->beta;
         s_vmax = 0u;
+        s_uc = uc;
         mbar_init(S.bar, 1);
         fence_mbar_init();
     }
@@ -501,9 +494,6 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
     if (s_done) return;
     if (tid == 0) unit_stage(m, uc, S, s_shd);
     const uint32_t dmask = unit_gather<NT>(a, uc, s_beta, S, &s_vmax, tid);
-    // the data of a chunk that a block launched later will process, into L2
-    if (tid == 0 && m.prefetch_ahead > 0 && blockIdx.x + m.prefetch_ahead < (unsigned)m.n_chunks)
-        unit_l2_prefetch(m, a, blockIdx.x + m.prefetch_ahead);
     const float dmax = __ldg(m.dmax + blockIdx.x);
     {
         bool ok = mbar_wait_bounded(S.bar, 0);
@@ -514,10 +504,10 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
             return;
         }
     }
-    const float2 sc = unit_scale(dmax, __uint_as_float(s_vmax), uc.max_star);
-    unit_elements<LUMP, NT>(uc, S, sc.x, tid);
+    const float2 sc = unit_scale(dmax, __uint_as_float(s_vmax), s_uc.max_star);
+    unit_elements<LUMP, NT>(s_uc, S, sc.x, tid);
     __syncthreads();
-    unit_warp_share<NT>(unit_nodes<NT>(a, uc, S, s_shd, sc.y, dmask, tid), s_wdot, tid);
+    unit_warp_share<NT>(unit_nodes<NT>(a, s_uc, S, s_shd, sc.y, dmask, tid), s_wdot, tid);
     __syncthreads();
     if (tid == 0) {
         a.pq[blockIdx.x] = chunk_share<NT>(s_wdot);

@@ -58,7 +58,6 @@ struct MeshDev {
     const float *ubd;        // [unit_total * kPatchMax * 2] beta*dt^2/6 per (unit, element, half)
     const float *dmax;       // [n_chunks] largest diagonal entry over each chunk's free nodes
     UnitSmem smu;
-    int prefetch_ahead;      // chunks between a block and the chunk whose data it prefetches into L2
 };
 
 // Scalars of one CG run, kept on the device.

@@ -462,18 +462,6 @@ static int mesh_upload_impl(ps_ctx *c, ps_mesh *m, const PrepMesh &pm) {
         // node ids of the unit records are 16-bit; a thread's Dirichlet mask
         // covers 32 nodes of the chunk
         m->use_units = U.total <= 200 * 1024 && pm.max_loc <= 32 * m->unit_threads;
-        if (m->use_units) {
-            // L2 prefetch distance: the chunks resident at once (a block
-            // prefetches the data of the block about one wave after it)
-            int per_sm = 0;
-            cudaError_t oe = m->unit_threads == 128
-                                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                       &per_sm, k_cg2_units<false, 128, kUnitBlocks128>, 128, U.total)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                       &per_sm, k_cg2_units<false, 256, 2>, 256, U.total);
-            cudaGetLastError();
-            d.prefetch_ahead = (oe == cudaSuccess && per_sm > 0) ? per_sm * c->sms : 0;
-        }
     }
     d.err = c->d_err;
     d.sm32 = make_layout(4, sizeof(NodeF), pm.max_loc, pm.max_patch, pm.max_inc, pm.max_sh);
