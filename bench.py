@@ -725,6 +725,30 @@ def _buckets(lat_s, sizes):
     return out
 
 
+class _DriftAhead:
+    """Each case's next time-step inputs (synthetic.served_step_drift from
+    the case's current state), computed in a thread pool while the case's
+    current request is in flight, so that generating the synthetic request
+    stream (numpy over every element of every case) does not stall the
+    requests.  One computation per case is outstanding at a time, so every
+    case draws its seeded random stream in the same order as a sequential
+    loop."""
+
+    def __init__(self, S, cases, workers=8):
+        import concurrent.futures as cf
+        self.ex = cf.ThreadPoolExecutor(max_workers=workers)
+        self.S, self.cases, self.fut = S, cases, {}
+
+    def prime(self, ci, state):
+        self.fut[ci] = self.ex.submit(self.S.served_step_drift, self.cases[ci], *state)
+
+    def take(self, ci):
+        return self.fut.pop(ci).result()
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+
+
 def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, budget_steps=None):
     """c5: time-step solves from simulated cases through the serving loop
     (continuous batching), closed loop with every case in flight; optionally
@@ -760,6 +784,7 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
         clocks = Clocks(0)
         if not args.no_clocks:
             clocks.start()
+        ahead = _DriftAhead(S, cases)
         t_start = time.perf_counter()
         order = [(k, ci) for k in range(steps) for ci in range(len(cases))]
         pending = {}
@@ -788,6 +813,8 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
             # pending tickets are polled, none is waited on in order
             for ci in range(len(cases)):
                 pending[P.ps_solve_submit(srv, ids[ci], state[ci][1])] = (ci, 0)
+                if steps > 1:
+                    ahead.prime(ci, state[ci])
             while pending:
                 progressed = False
                 for t in list(pending):
@@ -800,19 +827,26 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
                     worst = max(worst, info.rel_res)
                     done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
                     if k + 1 < steps:
-                        beta, b = S.served_step_drift(cases[ci], *state[ci])
+                        beta, b = ahead.take(ci)
                         state[ci] = (beta, b)
                         pending[P.ps_solve_submit(srv, ids[ci], b, beta)] = (ci, k + 1)
+                        if k + 2 < steps:
+                            ahead.prime(ci, state[ci])
                 if not progressed:
                     time.sleep(0.0002)
         else:
             next_t = time.perf_counter()
+            for ci in range(len(cases)):
+                if steps > 1:
+                    ahead.prime(ci, state[ci])
             for k, ci in order:
                 next_t += rng.exponential(1.0 / rate)
                 while time.perf_counter() < next_t:
                     time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
                 if k > 0:
-                    state[ci] = S.served_step_drift(cases[ci], *state[ci])
+                    state[ci] = ahead.take(ci)
+                    if k + 1 < steps:
+                        ahead.prime(ci, state[ci])
                 beta = state[ci][0] if k > 0 else None
                 pending[P.ps_solve_submit(srv, ids[ci], state[ci][1], beta)] = (ci, k)
             for t, (ci, k) in list(pending.items()):
@@ -820,6 +854,7 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
                 worst = max(worst, info.rel_res)
                 done_iters += cases[ci].n_free * (info.iters_inner + info.iters_outer)
         wall = time.perf_counter() - t_start
+        ahead.close()
         clk = clocks.stop() if not args.no_clocks else None
         stats = P.ps_server_get_stats(srv).as_dict()
         P.ps_server_destroy(srv)
@@ -852,11 +887,17 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
         clocks = Clocks(0)
         if not args.no_clocks:
             clocks.start()
+        ahead = _DriftAhead(S, cases)
         t_start = time.perf_counter()
+        for ci in range(len(cases)):
+            if steps > 1:
+                ahead.prime(ci, state[ci])
         for k in range(steps):
             for ci, c in enumerate(cases):
                 if k > 0:
-                    state[ci] = S.served_step_drift(c, *state[ci])
+                    state[ci] = ahead.take(ci)
+                    if k + 1 < steps:
+                        ahead.prime(ci, state[ci])
                     P.ps_coeff_set_beta(meshes[ci], state[ci][0])
                 t0 = time.perf_counter()
                 b = torch.as_tensor(state[ci][1], device="cuda")
@@ -867,6 +908,7 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
                 worst = max(worst, info.rel_res)
                 done_iters += c.n_free * (info.iters_inner + info.iters_outer)
         wall = time.perf_counter() - t_start
+        ahead.close()
         clk = clocks.stop() if not args.no_clocks else None
         for ci, c in enumerate(cases):          # restore the case coefficients
             P.ps_coeff_set_beta(meshes[ci], c.beta)

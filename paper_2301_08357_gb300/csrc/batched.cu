@@ -482,10 +482,31 @@ void batched_release_mesh(ps_mesh *m) {
     m->batch_ws = nullptr;
 }
 
+// A plan buffer of at least `bytes` (grown by half again when it is too
+// small; the contents are not kept).
+static int plan_buf(ps_ctx *ctx, DevAlloc &a, size_t bytes) {
+    if (a.p && a.bytes >= bytes) return PS_OK;
+    if (a.p) {
+        cudaFree(a.p);
+        ctx->bytes -= (int64_t)a.bytes;
+        a = DevAlloc{nullptr, 0};
+    }
+    std::vector<DevAlloc> one;
+    const int rc = dalloc(ctx, &a.p, std::max<size_t>(bytes + bytes / 2, 4096), one);
+    if (rc == PS_OK) a.bytes = one[0].bytes;
+    return rc;
+}
+
 void batch_plan_free(BatchPlan &plan) {
     if (plan.graph) cudaGraphExecDestroy(plan.graph);
     if (plan.cap) cudaStreamDestroy(plan.cap);
-    if (plan.ctx) dfree_all(plan.ctx, plan.allocs);
+    if (plan.ctx) {
+        for (DevAlloc *a : {&plan.buf_st, &plan.buf_meshes, &plan.buf_t[0], &plan.buf_t[1], &plan.buf_t[2]})
+            if (a->p) {
+                cudaFree(a->p);
+                plan.ctx->bytes -= (int64_t)a->bytes;
+            }
+    }
     if (plan.h_st) cudaFreeHost(plan.h_st);
     plan = BatchPlan();
 }
@@ -504,8 +525,16 @@ static SmemLayout max_layout(const std::vector<ps_mesh *> &meshes, bool fp64) {
 }
 
 int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, const ps_solve_opts &o,
-                     BatchPlan &plan) {
-    batch_plan_free(plan);
+                     cudaStream_t s, BatchPlan &plan) {
+    if (plan.ctx && plan.ctx != ctx) batch_plan_free(plan);
+    // a rebuild keeps the buffers, the pinned mirror and the capture stream;
+    // the captured epoch belongs to the old task lists
+    if (plan.graph) {
+        cudaGraphExecDestroy(plan.graph);
+        plan.graph = nullptr;
+    }
+    plan.graph_ok = true;
+    plan.epochs = 0;
     if ((o.batch_threads != 0 && o.batch_threads != 128 && o.batch_threads != 256) || o.batch_order < 0 ||
         o.batch_order > 1) {
         ps_set_last_error("batch: batch_threads must be 0, 128 or 256 and batch_order 0 or 1");
@@ -523,12 +552,11 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
     plan.epoch_iters = epoch_iters > 0 ? epoch_iters : 256;
     std::vector<int2> t1, t2, t3;
     plan.h_meshes.resize(n);
-    void *p = nullptr;
-    int rc = dalloc(ctx, &p, (size_t)n * sizeof(BState) + 4096, plan.allocs);
+    int rc = plan_buf(ctx, plan.buf_st, (size_t)n * sizeof(BState) + 4096);
     if (rc != PS_OK) return rc;
-    plan.d_st = (BState *)p;
+    plan.d_st = (BState *)plan.buf_st.p;
     // grid-barrier words and the active-mesh counter live after the states
-    rc = cuda_rc(cudaMemset(p, 0, (size_t)n * sizeof(BState) + 4096));
+    rc = cuda_rc(cudaMemsetAsync(plan.d_st, 0, (size_t)n * sizeof(BState) + 4096, s));
     if (rc != PS_OK) return rc;
     for (int i = 0; i < n; ++i) {
         ps_mesh *m = meshes[i];
@@ -575,16 +603,26 @@ int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters
     plan.n_t1 = (int)t1.size();
     plan.n_t2 = (int)t2.size();
     plan.n_t3 = (int)t3.size();
-    rc = dalloc(ctx, &p, (size_t)n * sizeof(BMesh), plan.allocs);
-    plan.d_meshes = (BMesh *)p;
-    if (rc == PS_OK) rc = dalloc(ctx, &p, t1.size() * sizeof(int2), plan.allocs), plan.d_t1 = (int2 *)p;
-    if (rc == PS_OK) rc = dalloc(ctx, &p, t2.size() * sizeof(int2), plan.allocs), plan.d_t2 = (int2 *)p;
-    if (rc == PS_OK) rc = dalloc(ctx, &p, t3.size() * sizeof(int2), plan.allocs), plan.d_t3 = (int2 *)p;
+    rc = plan_buf(ctx, plan.buf_meshes, (size_t)n * sizeof(BMesh));
+    plan.d_meshes = (BMesh *)plan.buf_meshes.p;
+    if (rc == PS_OK) rc = plan_buf(ctx, plan.buf_t[0], t1.size() * sizeof(int2)), plan.d_t1 = (int2 *)plan.buf_t[0].p;
+    if (rc == PS_OK) rc = plan_buf(ctx, plan.buf_t[1], t2.size() * sizeof(int2)), plan.d_t2 = (int2 *)plan.buf_t[1].p;
+    if (rc == PS_OK) rc = plan_buf(ctx, plan.buf_t[2], t3.size() * sizeof(int2)), plan.d_t3 = (int2 *)plan.buf_t[2].p;
     if (rc != PS_OK) return rc;
-    cudaError_t e = cudaMemcpy(plan.d_t1, t1.data(), t1.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(plan.d_t2, t2.data(), t2.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(plan.d_t3, t3.data(), t3.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&plan.h_st, (size_t)n * sizeof(BState), cudaHostAllocDefault);
+    // pageable sources: staged by the runtime before the calls return
+    cudaError_t e = cudaMemcpyAsync(plan.d_t1, t1.data(), t1.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan.d_t2, t2.data(), t2.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan.d_t3, t3.data(), t3.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && plan.h_st_cap < (size_t)n) {
+        // the pinned mirror grows; no copy of it is in flight (the previous
+        // epoch's read-back completed before its stream synchronisation)
+        if (plan.h_st) cudaFreeHost(plan.h_st);
+        plan.h_st = nullptr;
+        plan.h_st_cap = 0;
+        const size_t cap = std::max<size_t>((size_t)n + n / 2, 16);
+        e = cudaHostAlloc((void **)&plan.h_st, cap * sizeof(BState), cudaHostAllocDefault);
+        if (e == cudaSuccess) plan.h_st_cap = cap;
+    }
     if (e != cudaSuccess) return cuda_rc(e);
     std::memset(plan.h_st, 0, (size_t)n * sizeof(BState));
     plan.L32 = max_layout(plan.meshes, false);
@@ -634,7 +672,8 @@ int batch_upload_states(BatchPlan &plan, cudaStream_t s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(plan.d_st, plan.h_st, n * sizeof(BState), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(active, &plan.h_active, sizeof(int), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // (no synchronisation: the host leaves h_st alone until the next epoch's
+    // read-back has completed; the other two sources are pageable, staged)
     return cuda_rc(e);
 }
 
@@ -683,7 +722,10 @@ static int epoch_enqueue(BatchPlan &plan, cudaStream_t s) {
 }
 
 int batch_epoch(BatchPlan &plan, cudaStream_t s) {
-    if (plan.graph_ok && !plan.graph) {
+    // the first epoch of a (re)built plan runs its launches directly: a plan
+    // that is rebuilt after one epoch (the serving loop's membership
+    // changes) never pays for a capture
+    if (plan.graph_ok && !plan.graph && plan.epochs >= 1) {
         // capture the epoch once per plan; fall back to direct launches if
         // the runtime refuses to capture any of it
         if (!plan.cap && cudaStreamCreateWithFlags(&plan.cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -711,6 +753,7 @@ int batch_epoch(BatchPlan &plan, cudaStream_t s) {
     else
         rc = epoch_enqueue(plan, s);
     if (rc != PS_OK) return rc;
+    plan.epochs++;
     rc = cuda_rc(cudaStreamSynchronize(s));
     if (rc != PS_OK) return rc;
     int herr = 0;
@@ -743,7 +786,7 @@ int batch_solve_locked(ps_mesh *const *meshes, int n, const double *const *b_dev
     auto t0 = std::chrono::steady_clock::now();
     BatchPlan plan;
     const int epoch = o.graph_iters > 0 ? o.graph_iters * 8 : 256;
-    int rc = batch_plan_build(ctx, meshes, n, epoch, o, plan);
+    int rc = batch_plan_build(ctx, meshes, n, epoch, o, s, plan);
     if (rc == PS_OK) {
         for (int i = 0; i < n; ++i) batch_arm(plan, i, b_dev[i], x_dev[i], o);
         rc = batch_upload_states(plan, s);

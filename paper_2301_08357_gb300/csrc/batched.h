@@ -67,7 +67,11 @@ struct BMesh {
 struct BatchPlan {
     ps_ctx *ctx = nullptr;
     std::vector<ps_mesh *> meshes;
-    std::vector<DevAlloc> allocs;
+    // device buffers, kept (and grown) across rebuilds of the plan: states,
+    // mesh records, the three task lists
+    DevAlloc buf_st{nullptr, 0}, buf_meshes{nullptr, 0}, buf_t[3] = {{nullptr, 0}, {nullptr, 0}, {nullptr, 0}};
+    size_t h_st_cap = 0;           // BState entries the pinned mirror holds
+    int epochs = 0;                // epochs run since the plan was (re)built
     BMesh *d_meshes = nullptr;
     int2 *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr;   // chunk, shared-segment, node-range tasks
     int n_t1 = 0, n_t2 = 0, n_t3 = 0;
@@ -94,10 +98,12 @@ struct BatchMeshWs {
     int n_segs = 0, n_vt = 0;
 };
 
-// Build the plan for `n` distinct meshes of one context (workspaces allocated
-// on first use); states start in kPhIdle.
+// Build (or rebuild) the plan for `n` distinct meshes of one context
+// (workspaces allocated on first use); states start in kPhIdle.  A rebuild
+// keeps the plan's buffers when they are large enough; its copies are
+// ordered on stream s (nothing synchronises the device).
 int batch_plan_build(ps_ctx *ctx, ps_mesh *const *meshes, int n, int epoch_iters, const ps_solve_opts &o,
-                     BatchPlan &plan);
+                     cudaStream_t s, BatchPlan &plan);
 void batch_plan_free(BatchPlan &plan);
 // Start a solve of mesh i: caller-numbering device vectors b (read) and x
 // (first guess in, solution out), options; state -> kPhPrepare.  Takes effect

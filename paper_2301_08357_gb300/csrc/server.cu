@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -45,6 +46,7 @@ struct Case {
     ps_mesh *mesh = nullptr;
     std::vector<DevAlloc> allocs;
     double *b_dev = nullptr, *x_dev = nullptr;
+    double *beta_dev = nullptr;      // a request's drifted beta, staged for the on-device update
     std::deque<Req *> queue;
     Req *running = nullptr;
     int64_t ws_bytes = 0;
@@ -141,16 +143,20 @@ static void worker_main(ps_server *s) {
         const double t0 = now_s();
         std::lock_guard<std::mutex> ctx_lk(s->ctx->mu);
         int rc = PS_OK;
-        // stage the admitted requests' inputs
+        // stage the admitted requests' inputs, in stream order on the
+        // worker's stream (no allocation, no device-wide synchronisation)
         for (int ci : admitted) {
             Case &c = s->cases[ci];
             Req *r = c.running;
             if (!r->beta.empty()) {
-                // the enthalpy drifted: new beta (same alpha, dt^2)
-                s->ctx->mu.unlock();
-                int rb = ps_coeff_set_beta(c.mesh, r->beta.data());
-                s->ctx->mu.lock();
-                if (rb != PS_OK) rc = rb;
+                // the enthalpy drifted: new beta (same alpha, dt^2), then the
+                // element coefficients and the Jacobi diagonal on the device
+                // (the same kernels as ps_coeff_set_beta)
+                if (cudaMemcpyAsync(c.beta_dev, r->beta.data(), r->beta.size() * 8, cudaMemcpyHostToDevice,
+                                    s->stream) != cudaSuccess)
+                    rc = PS_ECUDA;
+                else
+                    rc = beta_update_device(c.mesh, c.beta_dev, c.mesh->dt2, s->stream, true);
             }
             if (rc == PS_OK &&
                 cudaMemcpyAsync(c.b_dev, r->b.data(), r->b.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
@@ -184,7 +190,7 @@ static void worker_main(ps_server *s) {
                     batch_plan_free(s->plan);
                 } else {
                     rc = batch_plan_build(s->ctx, ms.data(), (int)ms.size(), s->opts.epoch_iters, s->opts.opts,
-                                          s->plan);
+                                          s->stream, s->plan);
                     for (size_t k = 0; k < cur.size() && rc == PS_OK; ++k) {
                         Case &c = s->cases[cur[k]];
                         batch_arm(s->plan, (int)k, c.b_dev, c.x_dev, s->opts.opts);
@@ -292,6 +298,8 @@ extern "C" int ps_server_add_case(ps_server *s, ps_mesh *mesh, const double *x0,
         int rc = dalloc(s->ctx, &p, bytes, c.allocs);
         c.b_dev = (double *)p;
         if (rc == PS_OK) rc = dalloc(s->ctx, &p, bytes, c.allocs), c.x_dev = (double *)p;
+        if (rc == PS_OK)
+            rc = dalloc(s->ctx, &p, (size_t)mesh->prep.n_elems * 8, c.allocs), c.beta_dev = (double *)p;
         if (rc == PS_OK) {
             cudaError_t e = x0 ? cudaMemcpy(c.x_dev, x0, bytes, cudaMemcpyHostToDevice) : cudaMemset(c.x_dev, 0, bytes);
             if (e == cudaSuccess) e = cudaMemset(c.b_dev, 0, bytes);
@@ -315,24 +323,25 @@ extern "C" int ps_server_add_case(ps_server *s, ps_mesh *mesh, const double *x0,
 
 extern "C" int ps_solve_submit(ps_server *s, int32_t case_id, const double *b, const double *beta, ps_ticket *out) {
     if (!s || !b || !out) return PS_EINVAL;
-    Req *r = new (std::nothrow) Req();
-    if (!r) return PS_ENOMEM;
+    // the case's sizes (cases are only ever appended; their meshes fixed)
+    int64_t n_nodes = 0, n_elems = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (case_id < 0 || case_id >= (int32_t)s->cases.size()) {
-            delete r;
-            return PS_ENOTFOUND;
-        }
+        if (case_id < 0 || case_id >= (int32_t)s->cases.size()) return PS_ENOTFOUND;
+        n_nodes = s->cases[case_id].mesh->prep.n_nodes;
+        n_elems = s->cases[case_id].mesh->prep.n_elems;
+    }
+    // validate and copy the inputs outside the lock (the worker keeps running)
+    if (beta)
+        for (int64_t e = 0; e < n_elems; ++e)
+            if (!(beta[e] > 0.0) || !std::isfinite(beta[e])) return PS_EINVAL;
+    Req *r = new (std::nothrow) Req();
+    if (!r) return PS_ENOMEM;
+    r->b.assign(b, b + n_nodes);
+    if (beta) r->beta.assign(beta, beta + n_elems);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
         Case &c = s->cases[case_id];
-        r->b.assign(b, b + c.mesh->prep.n_nodes);
-        if (beta) {
-            for (int64_t e = 0; e < c.mesh->prep.n_elems; ++e)
-                if (!(beta[e] > 0.0)) {
-                    delete r;
-                    return PS_EINVAL;
-                }
-            r->beta.assign(beta, beta + c.mesh->prep.n_elems);
-        }
         r->id = s->next_ticket++;
         r->case_id = case_id;
         r->t_submit = now_s();
