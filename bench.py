@@ -770,12 +770,14 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
     n_check = 4 if not args.no_cpu_baseline else 0
     check_cases = sorted(range(len(cases)), key=lambda c: sizes[c])[:n_check]   # the smallest cases
 
-    def one_run(rate, budget=0, steps=None):
+    def one_run(rate, budget=0, steps=None, single_nodes=0):
         """rate None = closed loop (each case submits its next step when the last completes);
-        budget: the server's HBM cap on in-flight solver workspaces (0 = the context's)."""
+        budget: the server's HBM cap on in-flight solver workspaces (0 = the context's);
+        single_nodes: cases with at least this many nodes are served by the single-solve
+        engine, one request at a time between epochs (0 = every request batched)."""
         steps = steps or args.case_steps
         srv = P.ps_server_create(ctx, max_slots=64, epoch_iters=32, hbm_budget_bytes=budget,
-                                 opts=P.make_opts(tol=1e-10, **knobs))
+                                 opts=P.make_opts(tol=1e-10, **knobs), single_nodes=single_nodes)
         ids = [P.ps_server_add_case(srv, m) for m in meshes]
         state = [(c.beta.copy(), c.b.copy()) for c in cases]
         lat, qwait, req_size, done_iters, worst = [], [], [], 0, 0.0
@@ -869,7 +871,8 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
             ocheck = {"cases": len(last_x), "max_rel_res_oracle": ow,
                       "note": "last step of the %d smallest cases, recomputed by the FP64 oracle" % len(last_x)}
         n = len(lat)
-        return {"rate": rate, "solves": n, "steps_per_case": steps, "wall_s": wall, "solves_per_s": n / wall,
+        return {"rate": rate, "single_nodes": single_nodes, "single_solves": stats["single_solves"],
+                "solves": n, "steps_per_case": steps, "wall_s": wall, "solves_per_s": n / wall,
                 "dof_iters_per_s": done_iters / wall, "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99),
                 "per_bucket": _buckets(lat, req_size), "queue_p50_ms": 1e3 * _pctl(qwait, 50),
                 "peak_in_flight": stats["peak_in_flight"], "epochs": stats["epochs"], "max_rel_res": worst,
@@ -917,15 +920,20 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
                 "p50_ms": 1e3 * _pctl(lat, 50), "p99_ms": 1e3 * _pctl(lat, 99),
                 "per_bucket": _buckets(lat, req_size), "max_rel_res": worst, "clocks": clk}
 
-    sat = one_run(None)
-    runs = [sat]
+    # closed loop: every request batched, then the larger cases routed to the
+    # single-solve engine (500k and 100k nodes and up); the configuration with
+    # the highest throughput is the line's served figure and runs the rest
+    closed = [one_run(None, single_nodes=t) for t in (0, 500000, 100000)]
+    sat = max(closed, key=lambda r: r["solves_per_s"])
+    route = sat["single_nodes"]
+    runs = list(closed)
     for f in (rates or []):
-        runs.append(dict(one_run(f * sat["solves_per_s"]), rate_x_sat=f))
+        runs.append(dict(one_run(f * sat["solves_per_s"], single_nodes=route), rate_x_sat=f))
     # closed loop under an HBM budget that admits about a quarter of the cases'
     # workspaces at once (never less than the largest): admission queues requests
     ws_bytes = [P.ps_mesh_get_stats(m).solve_bytes for m in meshes]
     budget = int(max(max(ws_bytes), sum(ws_bytes) // 4))
-    runs.append(dict(one_run(None, budget, steps=budget_steps), hbm_budget_bytes=budget,
+    runs.append(dict(one_run(None, budget, steps=budget_steps, single_nodes=route), hbm_budget_bytes=budget,
                      workspace_bytes_total=int(sum(ws_bytes))))
     s_steps = single_steps or args.case_steps
     singles = [single_run(P.PS_MODE_FP64, s_steps), single_run(P.PS_MODE_MIXED, s_steps)]
@@ -935,7 +943,9 @@ def bench_served(args, P, S, autotune, torch, rates=None, single_steps=None, bud
            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
            "per_bucket": sat["per_bucket"], "max_rel_res": sat["max_rel_res"], "oracle_check": sat["oracle_check"],
            "served_vs_fp64_single_solves_per_s": sat["solves_per_s"] / singles[0]["solves_per_s"],
-           "chunk_elems": chunk, **knobs, "tuning": tune, "runs": runs, "single_solves": singles,
+           "served_vs_mixed_single_solves_per_s": sat["solves_per_s"] / singles[1]["solves_per_s"],
+           "single_nodes": route, "chunk_elems": chunk, **knobs, "tuning": tune, "runs": runs,
+           "single_solves": singles,
            "clocks": sat["clocks"]}
     for m in meshes:
         P.ps_mesh_free(m)

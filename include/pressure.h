@@ -440,7 +440,11 @@ typedef struct {
     int32_t epoch_iters;      /* inner iterations per epoch (0 = 64)                */
     size_t hbm_budget_bytes;  /* cap on workspaces of in-flight requests (0 = ctx)  */
     ps_solve_opts opts;       /* solver options for every request                   */
-    int32_t reserved[8];
+    int32_t single_nodes;     /* requests of cases whose mesh has at least this many
+                                 nodes run alone, to convergence, in the single-solve
+                                 engine (ps_pressure_solve with opts) on the worker's
+                                 stream between epochs; 0 = every request batched    */
+    int32_t reserved[7];
 } ps_server_opts;
 
 int ps_server_create(ps_ctx *ctx, const ps_server_opts *opts, ps_server **out);
@@ -478,7 +482,8 @@ typedef struct {
     int64_t peak_in_flight;
     int64_t bytes_in_use;
     double busy_seconds;
-    int64_t reserved[4];
+    int64_t single_solves;    /* requests served alone by the single-solve engine   */
+    int64_t reserved[3];
 } ps_server_stats;
 
 int ps_server_get_stats(ps_server *srv, ps_server_stats *out);

@@ -62,6 +62,9 @@ template <typename T, int MODE>
 int launch_pass(ps_mesh *m, const VecArgs<T> &a, cudaStream_t s);
 
 int beta_update_device(ps_mesh *m, const double *beta_dev, double dt2, cudaStream_t s, bool diag = true);
+// ps_pressure_solve with the context mutex held by the caller.
+int pressure_solve_locked(ps_mesh *m, const double *b, double *x, const ps_solve_opts *opts, ps_solve_info *info,
+                          cudaStream_t s);
 int alpha_update_device(ps_mesh *m, const double *alpha_dev, cudaStream_t s, bool diag = true);
 double inner_reduction(double itol, double tol, double bb, double rr);
 

@@ -1285,6 +1285,13 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
                                  ps_solve_info *info, void *stream) {
     if (!m || !b || !x) return PS_EINVAL;
     if (!m->coeff_ok) return PS_ESTATE;
+    std::lock_guard<std::mutex> lk(m->ctx->mu);
+    return ps::pressure_solve_locked(m, b, x, opts, info, (cudaStream_t)stream);
+}
+
+// ps_pressure_solve with the context mutex held by the caller.
+int ps::pressure_solve_locked(ps_mesh *m, const double *b, double *x, const ps_solve_opts *opts,
+                              ps_solve_info *info, cudaStream_t s) {
     ps_solve_opts o;
     if (opts) o = *opts; else ps_solve_opts_default(&o);
     if (o.mode != PS_MODE_FP64 && o.mode != PS_MODE_MIXED) return PS_EINVAL;
@@ -1293,9 +1300,7 @@ extern "C" int ps_pressure_solve(ps_mesh *m, const double *b, double *x, const p
     ps_solve_info *inf = info ? info : &local;
     std::memset(inf, 0, sizeof(*inf));
     auto t0 = std::chrono::steady_clock::now();
-    std::lock_guard<std::mutex> lk(m->ctx->mu);
     CK(cudaSetDevice(m->ctx->device));
-    cudaStream_t s = (cudaStream_t)stream;
     if (o.mode == PS_MODE_MIXED && o.engine == PS_ENGINE_PERSISTENT && o.precond != PS_PRECOND_NONE) {
         ps_mesh *one[1] = {m};
         const double *bb[1] = {b};

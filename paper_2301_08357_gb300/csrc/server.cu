@@ -47,6 +47,7 @@ struct Case {
     std::vector<DevAlloc> allocs;
     double *b_dev = nullptr, *x_dev = nullptr;
     double *beta_dev = nullptr;      // a request's drifted beta, staged for the on-device update
+    bool single = false;             // requests run alone in the single-solve engine (single_nodes)
     std::deque<Req *> queue;
     Req *running = nullptr;
     int64_t ws_bytes = 0;
@@ -163,14 +164,39 @@ static void worker_main(ps_server *s) {
                 rc = PS_ECUDA;
             membership_changed = true;
         }
-        // (re)build the plan over the in-flight requests, keeping the device
-        // state of requests already running
+        // requests of large meshes: each solved alone, to convergence, by the
+        // single-solve engine on the worker's stream, warm-starting from the
+        // case's resident pressure (no epochs shared with the batch)
+        std::vector<std::pair<int, ps_solve_info>> done;
+        for (int ci : admitted) {
+            Case &c = s->cases[ci];
+            if (!c.single || rc != PS_OK) continue;
+            ps_solve_info inf;
+            const int sr = pressure_solve_locked(c.mesh, c.b_dev, c.x_dev, &s->opts.opts, &inf, s->stream);
+            if (sr != PS_OK && sr != PS_ENOTCONV && sr != PS_EBREAKDOWN) {
+                rc = sr;
+                break;
+            }
+            inf.status = sr;
+            c.running->x.resize(c.running->b.size());
+            if (cudaMemcpyAsync(c.running->x.data(), c.x_dev, c.running->x.size() * 8, cudaMemcpyDeviceToHost,
+                                s->stream) != cudaSuccess ||
+                cudaStreamSynchronize(s->stream) != cudaSuccess) {
+                rc = PS_ECUDA;
+                break;
+            }
+            done.push_back({ci, inf});
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->st.single_solves++;
+        }
+        // (re)build the plan over the in-flight batched requests, keeping the
+        // device state of requests already running
         if (rc == PS_OK) {
             std::vector<int> cur;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 for (size_t ci = 0; ci < s->cases.size(); ++ci)
-                    if (s->cases[ci].running) cur.push_back((int)ci);
+                    if (s->cases[ci].running && !s->cases[ci].single) cur.push_back((int)ci);
             }
             if (cur != s->plan_cases) membership_changed = true;
             if (membership_changed) {
@@ -201,8 +227,7 @@ static void worker_main(ps_server *s) {
             }
         }
         if (rc == PS_OK && !s->plan_cases.empty()) rc = batch_epoch(s->plan, s->stream);
-        // completions
-        std::vector<std::pair<int, ps_solve_info>> done;
+        // completions of the batched requests
         if (rc == PS_OK) {
             for (size_t k = 0; k < s->plan_cases.size(); ++k) {
                 if (s->plan.h_st[k].phase != kPhDone) continue;
@@ -222,8 +247,9 @@ static void worker_main(ps_server *s) {
         s->st.epochs++;
         s->st.busy_seconds += now_s() - t0;
         if (rc != PS_OK) {
-            // fail every in-flight request; keep serving the queue
-            for (int ci : s->plan_cases) {
+            // fail every in-flight request (batched, and single-lane ones
+            // admitted in this round); keep serving the queue
+            for (size_t ci = 0; ci < s->cases.size(); ++ci) {
                 Case &c = s->cases[ci];
                 if (!c.running) continue;
                 s->in_flight_bytes -= c.ws_bytes;
@@ -290,6 +316,7 @@ extern "C" int ps_server_add_case(ps_server *s, ps_mesh *mesh, const double *x0,
     Case c;
     c.mesh = mesh;
     c.ws_bytes = batch_ws_bytes(mesh);
+    c.single = s->opts.single_nodes > 0 && mesh->prep.n_nodes >= (int64_t)s->opts.single_nodes;
     const size_t bytes = (size_t)mesh->prep.n_nodes * 8;
     {
         std::lock_guard<std::mutex> ctx_lk(s->ctx->mu);

@@ -83,14 +83,14 @@ class ps_mesh_stats(C.Structure):
 
 class ps_server_opts(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("epoch_iters", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
-                ("opts", ps_solve_opts), ("reserved", C.c_int32 * 8)]
+                ("opts", ps_solve_opts), ("single_nodes", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class ps_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("in_flight", C.c_int64), ("queued", C.c_int64), ("epochs", C.c_int64),
                 ("peak_in_flight", C.c_int64), ("bytes_in_use", C.c_int64), ("busy_seconds", C.c_double),
-                ("reserved", C.c_int64 * 4)]
+                ("single_solves", C.c_int64), ("reserved", C.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -358,9 +358,10 @@ def ps_batch_solve(meshes, b_devs, x_devs, opts=None, stream=None):
     return _check(st, "ps_batch_solve"), list(infos)
 
 
-def ps_server_create(ctx, max_slots=0, epoch_iters=0, hbm_budget_bytes=0, opts=None):
+def ps_server_create(ctx, max_slots=0, epoch_iters=0, hbm_budget_bytes=0, opts=None, single_nodes=0):
     so = ps_server_opts()
     so.max_slots, so.epoch_iters, so.hbm_budget_bytes = max_slots, epoch_iters, hbm_budget_bytes
+    so.single_nodes = single_nodes
     so.opts = opts if opts is not None else ps_solve_opts_default()
     h = _vp()
     _check(_lib.ps_server_create(ctx, C.byref(so), C.byref(h)), "ps_server_create")

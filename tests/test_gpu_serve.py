@@ -106,6 +106,54 @@ def test_served_results_match_oracle_and_alone(env):
             P.ps_mesh_free(m)
 
 
+def _alone_single(P, torch, case, mesh, steps):
+    """The same sequence of solves through ps_pressure_solve (default options)."""
+    P.ps_coeff_set(mesh, case.alpha, case.beta, case.dt2)
+    x = torch.zeros(case.n_nodes, dtype=torch.float64, device="cuda")
+    outs = []
+    for beta_sub, beta, b in steps:
+        if beta_sub is not None:
+            P.ps_coeff_set_beta(mesh, beta_sub)
+        bd = torch.as_tensor(b, device="cuda")
+        st, info = P.ps_pressure_solve(mesh, bd, x, P.make_opts())
+        assert st == P.PS_OK
+        outs.append(x.cpu().numpy().copy())
+    P.ps_coeff_set(mesh, case.alpha, case.beta, case.dt2)
+    return outs
+
+
+def test_single_lane_for_large_meshes(env):
+    """single_nodes routes the cases with the larger meshes to the
+    single-solve engine (each request alone, between epochs): their results
+    equal the same sequence of ps_pressure_solve calls bitwise, the others equal
+    the batch of one, and every result meets the oracle's gate."""
+    P, torch, ctx = env
+    cases = [S.make_served_case(c, lo=1e3, hi=2e4, median=4e3) for c in range(30, 36)]
+    steps = [_steps(c) for c in cases]
+    meshes = [upload(P, ctx, c) for c in cases]
+    sizes = [c.n_nodes for c in cases]
+    thr = int(np.median(sizes)) + 1
+    single = [n >= thr for n in sizes]
+    assert 0 < sum(single) < len(cases)
+    try:
+        results, stats = _serve(P, ctx, cases, meshes, steps, max_slots=8, epoch_iters=16, single_nodes=thr)
+        assert stats["completed"] == len(cases) * N_STEPS and stats["failed"] == 0
+        assert stats["single_solves"] == sum(single) * N_STEPS
+        for ci, c in enumerate(cases):
+            for k in range(N_STEPS):
+                st, info, x = results[(ci, k)]
+                assert st == P.PS_OK and info["converged"] == 1
+                A = oracle.PressureMatrix.from_case(c, beta=steps[ci][k][1])
+                assert A.residual(steps[ci][k][2], x) <= 1.05e-10, (ci, k)
+        for ci, c in enumerate(cases):
+            alone = (_alone_single if single[ci] else _alone)(P, torch, c, meshes[ci], steps[ci])
+            for k in range(N_STEPS):
+                assert np.array_equal(alone[k], results[(ci, k)][2]), (ci, k, single[ci])
+    finally:
+        for m in meshes:
+            P.ps_mesh_free(m)
+
+
 def test_budget_forces_queueing(env):
     P, torch, ctx = env
     cases = [S.make_served_case(c, lo=3e3, hi=4e3, median=3.5e3) for c in range(10, 13)]
