@@ -406,19 +406,27 @@ __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_ch
     }
     __syncthreads();
     if (!s_ok) return;
-    // eight loads in flight per thread: thread t takes chunks t + NT (8 i + k)
-    // into accumulator k, merged in k order
+    // eight 16-byte loads (two chunk shares each) in flight per thread:
+    // thread t takes the chunk pairs j = t + NT (8 i + k), chunks 2j and
+    // 2j + 1, into accumulator k, merged in k order (the share array holds
+    // at least one entry past the last chunk, so the pair load stays inside)
     constexpr int kAcc = 8;
     DotF part[kAcc];
-    for (int i0 = tid; i0 < n_chunks; i0 += NT * kAcc) {
-        float2 v[kAcc];
+    const float4 *pq4 = reinterpret_cast<const float4 *>(a.pq);
+    const int n_pairs = (n_chunks + 1) / 2;
+    for (int j0 = tid; j0 < n_pairs; j0 += NT * kAcc) {
+        float4 v[kAcc];
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) {
-            const int i = i0 + NT * k;
-            v[k] = i < n_chunks ? __ldcg(a.pq + i) : make_float2(0.f, 0.f);
+            const int j = j0 + NT * k;
+            v[k] = j < n_pairs ? __ldcg(pq4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int k = 0; k < kAcc; ++k) part[k].merge(v[k].x, v[k].y);
+        for (int k = 0; k < kAcc; ++k) {
+            const int j = j0 + NT * k;
+            part[k].merge(v[k].x, v[k].y);
+            if (2 * j + 1 < n_chunks) part[k].merge(v[k].z, v[k].w);
+        }
     }
     DotF acc = part[0];
 #pragma unroll
