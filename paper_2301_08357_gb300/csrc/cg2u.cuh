@@ -372,48 +372,31 @@ __device__ __forceinline__ DotF unit_nodes(const Cg2Args<float> &a, const UnitCh
     return acc;
 }
 
-__device__ __forceinline__ unsigned int unit_ld_acquire(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void unit_red_release_add(unsigned int *p, unsigned int v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+// A chunk share not yet written: both words all ones (a NaN that no
+// arithmetic produces; computed NaNs are 0x7fffffff).
+__device__ __forceinline__ bool unit_unset(float v) { return __float_as_uint(v) == 0xffffffffu; }
 
 // The operator pass's completion, in one extra block launched after the
-// chunk blocks: each chunk block stores its share of p.Ap and counts itself
-// with a release add (it does not wait for the count); this block waits
-// (bounded) until every chunk is counted, sums the shares in chunk order
-// (thread t takes chunks t, t + NT, ...; warps merged in order) and sets
-// alpha = rz / p.Ap.  The chunk blocks never wait for it, so they always
-// complete; on timeout the error flag is set and alpha is left unchanged.
+// chunk blocks: each chunk block stores its share of p.Ap over the share's
+// "unset" pattern and exits (no fence, no counter, no wait).  This block
+// polls the shares in chunk order until each is set (bounded), sums them in
+// a fixed order and sets alpha = rz / p.Ap, and restores the unset pattern
+// for the next launch.  The chunk blocks never wait for it, so they always
+// complete; on timeout the error flag is set, alpha is left unchanged and
+// the shares are reset all the same.
 template <int NT>
 __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_chunks, int *err, int tid) {
-    __shared__ int s_ok;
     __shared__ float2 s_w[NT / 32];
-    if (tid == 0) {
-        int ok = 0;
-        for (uint32_t i = 0; i < kGridSpinLimit; ++i) {
-            if (unit_ld_acquire(&a.st->cnt_a) >= (unsigned int)n_chunks) {
-                ok = 1;
-                break;
-            }
-            __nanosleep(64);
-        }
-        if (!ok) atomicOr(err, kErrGridTimeout);
-        s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return;
     // eight 16-byte loads (two chunk shares each) in flight per thread:
     // thread t takes the chunk pairs j = t + NT (8 i + k), chunks 2j and
     // 2j + 1, into accumulator k, merged in k order (the share array holds
     // at least one entry past the last chunk, so the pair load stays inside)
     constexpr int kAcc = 8;
     DotF part[kAcc];
-    const float4 *pq4 = reinterpret_cast<const float4 *>(a.pq);
+    float4 *pq4 = reinterpret_cast<float4 *>(a.pq);
     const int n_pairs = (n_chunks + 1) / 2;
+    uint32_t polls = 0;
+    bool ok = true;
     for (int j0 = tid; j0 < n_pairs; j0 += NT * kAcc) {
         float4 v[kAcc];
 #pragma unroll
@@ -424,9 +407,30 @@ __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_ch
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) {
             const int j = j0 + NT * k;
+            if (j >= n_pairs) continue;
+            const bool two = 2 * j + 1 < n_chunks;
+            // wait (bounded) for the shares of chunks 2j and 2j + 1
+            while (ok && (unit_unset(v[k].x) || unit_unset(v[k].y) ||
+                          (two && (unit_unset(v[k].z) || unit_unset(v[k].w))))) {
+                if (++polls > kGridSpinLimit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+                v[k] = __ldcg(pq4 + j);
+            }
             part[k].merge(v[k].x, v[k].y);
-            if (2 * j + 1 < n_chunks) part[k].merge(v[k].z, v[k].w);
+            if (two) part[k].merge(v[k].z, v[k].w);
         }
+        if (!ok) break;
+    }
+    ok = __syncthreads_and(ok);   // every share read
+    for (int j = tid; j < n_pairs; j += NT)
+        __stcg(pq4 + j, make_float4(__uint_as_float(0xffffffffu), __uint_as_float(0xffffffffu),
+                                    __uint_as_float(0xffffffffu), __uint_as_float(0xffffffffu)));
+    if (!ok) {
+        if (tid == 0) atomicOr(err, kErrGridTimeout);
+        return;
     }
     DotF acc = part[0];
 #pragma unroll
@@ -440,7 +444,6 @@ __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_ch
         for (int w = 0; w < NT / 32; ++w) t.merge(s_w[w].x, s_w[w].y);
         const double pq = (double)t.hi + (double)t.lo;
         CgState *st = a.st;
-        st->cnt_a = 0;
         st->pq = pq;
         if (!(pq > 0.0) || !isfinite(pq)) {
             st->status = kCgBreakdown;
@@ -517,10 +520,7 @@ __global__ void __launch_bounds__(NT, MINB) k_cg2_units(MeshDev m, Cg2Args<float
     __syncthreads();
     unit_warp_share<NT>(unit_nodes<NT>(a, s_uc, S, s_shd, sc.y, dmask, tid), s_wdot, tid);
     __syncthreads();
-    if (tid == 0) {
-        a.pq[blockIdx.x] = chunk_share<NT>(s_wdot);
-        unit_red_release_add(&a.st->cnt_a, 1u);
-    }
+    if (tid == 0) a.pq[blockIdx.x] = chunk_share<NT>(s_wdot);   // one 8-byte store over the unset pattern
 }
 
 // Largest diagonal entry D_jj = 1 / D^-1_jj over each chunk's free local nodes

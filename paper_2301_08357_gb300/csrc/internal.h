@@ -36,6 +36,9 @@ struct Workspace {
     double *part64 = nullptr;
     double *dot1 = nullptr, *dot2 = nullptr;
     double *pq2 = nullptr, *z3 = nullptr;   // two-kernel CG partials
+    // paired-patch operator kernel: chunk shares of p.Ap, all bits set
+    // (0xffffffff, a NaN no arithmetic produces) while not yet written
+    float2 *pqu = nullptr;
     // fused CG (FP32): second buffers of x, r, p, w (first: x32, r32, p32,
     // q32), both buffers of s, second partial buffer, per-chunk dot triples
     float *x32b = nullptr, *r32b = nullptr, *p32b = nullptr, *q32b = nullptr;

@@ -849,11 +849,13 @@ int ensure_workspace(ps_mesh *m) {
     WA(part32b, float, sh);
     WA(dots1, double, 3 * m->dev.n_chunks + 8);
     if (m->use_units) WA(halo32, float2, sh);
+    if (m->use_units) WA(pqu, float2, m->dev.n_chunks + 8);
 #undef WA
     if (rc != PS_OK) {
         dfree_all(c, w.allocs);
         return rc;
     }
+    if (w.pqu) CK(cudaMemset(w.pqu, 0xff, ((size_t)m->dev.n_chunks + 8) * sizeof(float2)));
     CK(cudaHostAlloc((void **)&w.h_st, sizeof(CgState), cudaHostAllocDefault));
     CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
     w.ready = true;
@@ -881,6 +883,7 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
         a.partial = (T *)w.part64;
     }
     a.pq = (typename PartOf<T>::type *)w.pq2;
+    if (sizeof(T) == 4 && m->use_units) a.pq = (typename PartOf<T>::type *)w.pqu;
     a.z2 = (typename PartOf<T>::type *)w.z3;
     a.g3 = m->g3c;
     a.st = w.st;
