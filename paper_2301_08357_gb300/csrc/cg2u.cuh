@@ -266,7 +266,8 @@ __device__ __forceinline__ UnitChunk unit_chunk(const MeshDev &m, int c) {
 
 // One thread: bulk copies of the chunk's node records, shared-node
 // destinations (into shd) and unit records with their beta*dt^2/6 (even unit
-// counts: 16-byte multiples), all on one mbarrier phase.
+// counts: 16-byte multiples), all on one mbarrier phase.  Issued once per
+// block, before any generic access of these buffers (no proxy fence).
 __device__ __forceinline__ void unit_stage(const MeshDev &m, const UnitChunk &cd, const UnitShared &S,
                                            int32_t *shd) {
     const UnitChunk &cu = cd;
@@ -274,7 +275,6 @@ __device__ __forceinline__ void unit_stage(const MeshDev &m, const UnitChunk &cd
     const uint32_t b_shd = (uint32_t)((cd.n_sh + kShPad - 1) / kShPad * kShPad) * 4u;
     const uint32_t b_rec = (uint32_t)cu.n_unit * kURecWords * 4u;
     const uint32_t b_bd = (uint32_t)cu.n_unit * kPatchMax * 8u;
-    fence_proxy_async_smem();      // earlier generic accesses of these buffers before the async writes
     mbar_arrive_expect_tx(S.bar, b_node + b_shd + b_rec + b_bd);
     bulk_g2s(S.node, m.node32 + cd.node_off, b_node, S.bar);
     if (b_shd) bulk_g2s(shd, m.sh_dest + cd.sh_off, b_shd, S.bar);
