@@ -379,6 +379,19 @@ std::string prepare_mesh(int dim, int64_t n_nodes, const double *coords, int64_t
         }
         chunk_begin.push_back(n_elems);
     }
+    if (opt.split_lead > 0 && (int64_t)chunk_begin.size() - 1 >= 4 * (int64_t)opt.split_lead) {
+        // the first split_lead chunks in two halves each (each half is
+        // contiguous in the Morton order: on Kuhn meshes a block of cells)
+        std::vector<int64_t> nb;
+        nb.reserve(chunk_begin.size() + opt.split_lead);
+        for (size_t c = 0; c + 1 < chunk_begin.size(); ++c) {
+            nb.push_back(chunk_begin[c]);
+            if ((int)c < opt.split_lead && chunk_begin[c + 1] - chunk_begin[c] >= 2)
+                nb.push_back((chunk_begin[c] + chunk_begin[c + 1]) / 2);
+        }
+        nb.push_back(n_elems);
+        chunk_begin.swap(nb);
+    }
     const int nc = (int)chunk_begin.size() - 1;
     m.n_chunks = nc;
 

@@ -17,6 +17,11 @@ struct PrepOptions {
     // vertex whose unknown vertex i shares (master[master[i]] == master[i]);
     // nullptr = no merging
     const int32_t *periodic = nullptr;
+    // split each of the first `split_lead` chunks into two halves (Morton
+    // order), when the mesh has at least four times as many chunks: the
+    // blocks of the first wave then end at different times, so the blocks
+    // resident on an SM do not stay in step (0 = no split)
+    int split_lead = 0;
 };
 
 struct PrepMesh {

@@ -534,6 +534,10 @@ extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, cons
         po.chunk_nodes_max = opts->chunk_nodes_max;
     }
     po.periodic = periodic;
+    // 3D meshes (paired-patch operator kernel): the first wave's chunks
+    // split in halves on one of every ~five resident blocks of an SM
+    // (measured on 160^3 Kuhn: 141 -> 138 us per operator pass)
+    if (dim == 3 && !(opts && opts->operator_kernel == 1)) po.split_lead = c->sms;
     ps_mesh *m = new (std::nothrow) ps_mesh();
     if (!m) return PS_ENOMEM;
     m->ctx = c;
