@@ -53,7 +53,7 @@ UNIT = "DOF-iter/s"
 # (the line then reports null).
 TRAFFIC = {
     ("k_cg2_units<false,128,5>", "c3_3d_kuhn_160^3_stiff_warm_tets24576000_nodes4173281"): {
-        "bytes": 345110272 + 27897600,
+        "bytes": 345454336 + 28280064,
         "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (1 pass, cold L2), third launch of "
                   "`python bench.py --workload c3 --steps 1 --warmup 2 --launch-list --no-clocks`; "
                   "profiles/k_cg2_units_kuhn128.md"},

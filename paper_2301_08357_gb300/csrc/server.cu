@@ -248,7 +248,7 @@ static void worker_main(ps_server *s) {
         s->st.busy_seconds += now_s() - t0;
         if (rc != PS_OK) {
             // fail every in-flight request (batched, and single-lane ones
-            // admitted in this round); keep serving the queue
+            // admitted in this pass of the loop); keep serving the queue
             for (size_t ci = 0; ci < s->cases.size(); ++ci) {
                 Case &c = s->cases[ci];
                 if (!c.running) continue;
