@@ -383,7 +383,8 @@ __device__ __forceinline__ bool unit_unset(float v) { return __float_as_uint(v) 
 // a fixed order and sets alpha = rz / p.Ap, and restores the unset pattern
 // for the next launch.  The chunk blocks never wait for it, so they always
 // complete; on timeout the error flag is set, alpha is left unchanged and
-// the shares are reset all the same.
+// the shares are reset all the same (and again, on the stream, at the start
+// of the next CG run, in case a late chunk block wrote its share after).
 template <int NT>
 __device__ __noinline__ void unit_reduce_alpha(const Cg2Args<float> &a, int n_chunks, int *err, int tid) {
     __shared__ float2 s_w[NT / 32];

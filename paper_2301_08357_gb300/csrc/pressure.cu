@@ -895,6 +895,15 @@ static Cg2Args<T> cg2_args(ps_mesh *m) {
     return a;
 }
 
+// The paired-patch kernel's chunk shares of p.Ap back to their "unset"
+// pattern, on stream s: at the start of every CG run and before a diagnostic
+// launch, so that no share written after an interrupted launch can be taken
+// for a later one.
+static cudaError_t reset_unit_shares(ps_mesh *m, cudaStream_t s) {
+    if (!m->ws.pqu) return cudaSuccess;
+    return cudaMemsetAsync(m->ws.pqu, 0xff, ((size_t)m->dev.n_chunks + 8) * sizeof(float2), s);
+}
+
 // FP32 operator kernel of the two-kernel iteration.  (Measured on 64^3..160^3:
 // 512-thread blocks, with or without a register cap for 3 blocks per SM, are
 // 15-55% slower than 256-thread blocks capped at 64 registers.)
@@ -1206,6 +1215,7 @@ int solve_internal(ps_mesh *m, const ps_solve_opts &o, ps_solve_info *info, cuda
                 m->launches += 2;
             } else {
                 Cg2Args<float> a = cg2_args<float>(m);
+                CK(reset_unit_shares(m, s));
                 k_cg2_start<float><<<m->g3c, kBlock, 0, s>>>(m->dev, a, w.r64, scale, w.x32, it_k * it_k, 1,
                                                              max_it - used);
                 m->launches += 1;
@@ -1361,6 +1371,7 @@ extern "C" int ps_debug_cg_apply(ps_mesh *m, const void *x, void *y, double *pap
     hs.rz = 1.0;
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     const Cg2Args<float> ca = cg2_args<float>(m);
+    CK(reset_unit_shares(m, s));
     if (ca.halo)
         k_halo_gather<<<grid_for(m->prep.sh_total, m->ctx->sms), kBlock, 0, s>>>(m->prep.sh_total,
                                                                                 m->dev.sh_ids, ca, 0);
@@ -1460,6 +1471,7 @@ extern "C" int ps_profile_kernel(ps_mesh *m, int which, int reps, void *stream, 
     hs.first = 1;
     hs.free_run = 1;     // the fused pass never stops
     CK(cudaMemcpyAsync(w.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    CK(reset_unit_shares(m, s));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
