@@ -94,7 +94,13 @@ typedef struct {
                              /* fixed-point node sums)                              */
     int32_t operator_threads; /* threads per block of the paired-patch kernel:     */
                              /* 0 = auto (128), 128 or 256                          */
-    int32_t reserved[2];
+    int32_t split_lead;      /* chunks at the head of the (Morton) chunk order split */
+                             /* in halves when the mesh has at least four times as */
+                             /* many, so the first wave of blocks ends out of step:*/
+                             /* 0 = auto (3D meshes with the paired-patch kernel:  */
+                             /* one per SM; ps_debug_prepare: none), -1 = none,    */
+                             /* n > 0 = n                                           */
+    int32_t reserved[1];
 } ps_mesh_opts;
 
 typedef struct {

@@ -537,7 +537,10 @@ extern "C" int ps_mesh_upload_periodic(ps_ctx *c, int dim, int64_t n_nodes, cons
     // 3D meshes (paired-patch operator kernel): the first wave's chunks
     // split in halves on one of every ~five resident blocks of an SM
     // (measured on 160^3 Kuhn: 141 -> 138 us per operator pass)
-    if (dim == 3 && !(opts && opts->operator_kernel == 1)) po.split_lead = c->sms;
+    const int sl = opts ? opts->split_lead : 0;
+    if (sl < -1) return PS_EINVAL;
+    if (sl > 0) po.split_lead = sl;
+    else if (sl == 0 && dim == 3 && !(opts && opts->operator_kernel == 1)) po.split_lead = c->sms;
     ps_mesh *m = new (std::nothrow) ps_mesh();
     if (!m) return PS_ENOMEM;
     m->ctx = c;
@@ -1418,6 +1421,8 @@ extern "C" int ps_debug_prepare(int dim, int64_t n_nodes, const double *coords, 
     if (opts) {
         po.chunk_elems = opts->chunk_elems;
         po.chunk_nodes_max = opts->chunk_nodes_max;
+        if (opts->split_lead < -1) return PS_EINVAL;
+        po.split_lead = opts->split_lead > 0 ? opts->split_lead : 0;
     }
     po.periodic = periodic;
     PrepMesh pm;

@@ -46,7 +46,7 @@ class PressureError(RuntimeError):
 class ps_mesh_opts(C.Structure):
     _fields_ = [("chunk_elems", C.c_int32), ("chunk_nodes_max", C.c_int32), ("pipeline", C.c_int32),
                 ("update_blocks_per_sm", C.c_int32), ("operator_kernel", C.c_int32),
-                ("operator_threads", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("operator_threads", C.c_int32), ("split_lead", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class ps_solve_opts(C.Structure):
@@ -219,7 +219,7 @@ def ps_ctx_bytes_in_use(ctx):
 
 
 def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, pipeline=0,
-                   update_blocks_per_sm=0, periodic=None, operator_kernel=0, operator_threads=0):
+                   update_blocks_per_sm=0, periodic=None, operator_kernel=0, operator_threads=0, split_lead=0):
     """periodic: optional [n_nodes] master map (ps_mesh_upload_periodic)."""
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
@@ -228,7 +228,7 @@ def ps_mesh_upload(ctx, dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_
     if dirichlet is not None:
         dirichlet, pd = _host(dirichlet, np.uint8)
     o = ps_mesh_opts(chunk_elems, chunk_nodes_max, pipeline, update_blocks_per_sm, operator_kernel,
-                     operator_threads)
+                     operator_threads, split_lead)
     h = _vp()
     if periodic is None:
         _check(_lib.ps_mesh_upload(ctx, int(dim), n, pc, conn.shape[0], pe, pd, C.byref(o), C.byref(h)),
@@ -453,7 +453,8 @@ def ps_debug_cg_apply(mesh, x_dev, y_dev, stream=None):
     return float(pap.value)
 
 
-def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, periodic=None):
+def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nodes_max=0, periodic=None,
+                     split_lead=0):
     """Host-only: run the mesh preprocessing and its invariant checks."""
     coords, pc = _host(coords, np.float64)
     conn, pe = _host(conn, np.int32)
@@ -464,6 +465,7 @@ def ps_debug_prepare(dim, coords, conn, dirichlet=None, chunk_elems=0, chunk_nod
     if periodic is not None:
         periodic, pp = _host(periodic, np.int32)
     o = ps_mesh_opts(chunk_elems, chunk_nodes_max)
+    o.split_lead = split_lead
     s = ps_mesh_stats()
     _check(_lib.ps_debug_prepare(int(dim), coords.shape[0], pc, conn.shape[0], pe, pd, pp, C.byref(o),
                                  C.byref(s)), "ps_debug_prepare")

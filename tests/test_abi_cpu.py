@@ -98,6 +98,28 @@ def test_prepare_invariants(P, dim, n, chunk):
     assert s2.n_free == s.n_free
 
 
+def test_prepare_split_lead(P):
+    """The first split_lead chunks of the Morton chunk order are split in
+    halves when there are at least four times as many chunks (the layout's
+    invariants hold either way); fewer chunks are left alone; -1 = none."""
+    from paper_2301_08357_gb300 import synthetic as S
+    case = S.make_c2(n=16)                                   # 24,576 tets
+    base = P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=96)
+    assert base.n_chunks == 256
+    for k in (1, 7, 64):
+        s = P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=96, split_lead=k)
+        assert s.n_chunks == base.n_chunks + k
+        assert s.max_chunk_elems == 96 and s.n_free == base.n_free
+        assert s.n_shared >= base.n_shared
+    # 65 * 4 > 256 chunks: no split; -1: none; below -1: rejected
+    assert P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=96,
+                              split_lead=65).n_chunks == 256
+    assert P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=96,
+                              split_lead=-1).n_chunks == 256
+    with pytest.raises(P.PressureError):
+        P.ps_debug_prepare(3, case.coords, case.conn, case.dirichlet, chunk_elems=96, split_lead=-2)
+
+
 def test_prepare_chunk_node_cap(P):
     from paper_2301_08357_gb300 import synthetic as S
     case = S.make_c2(n=8)
