@@ -648,7 +648,7 @@ def bench_batch(args, P, S, autotune, torch):
     clocks = Clocks(0)
     if not args.no_clocks:
         clocks.start()
-    times, dof_iters, launches = [], 0, 0
+    times, dof_iters, launches, alg_bytes = [], 0, 0, 0.0
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         for x in xs:
@@ -664,8 +664,20 @@ def bench_batch(args, P, S, autotune, torch):
             raise RuntimeError("batched solve failed: %s" % P.ps_status_str(st))
         dof_iters += sum(nf * (inf.iters_inner + inf.iters_outer) for nf, inf in zip(n_free, infos))
         launches += max(inf.kernel_launches for inf in infos)
+        # algorithmic bytes of the inner iterations (the fused one-reduction
+        # pass of the persistent kernel: per element d + 1 vertex ids and
+        # beta dt^2, per node coordinates + alpha and the x r s p w reads and
+        # writes, FP32); the outer FP64 passes are not counted
+        alg_bytes += sum(inf.iters_inner * ((4 * (c.dim + 1) + 4) * c.n_elems + (4 * (c.dim + 1) + 44) * c.n_nodes)
+                         for c, inf in zip(cases, infos))
     clk = clocks.stop() if not args.no_clocks else None
     tot = float(np.sum(times))
+    peak, peak_kind = peaks()
+    ach = alg_bytes / (tot / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_kind": peak_kind, "alg_bytes_per_batch": alg_bytes / args.steps,
+            "basis": "whole batch solve time (every kernel of the solve, FP64 passes and launch gaps "
+                     "included): a lower bound on the persistent inner kernel's own fraction"}
     # the oracle's residual of every 32nd mesh's solution (assembled on the host)
     check = None
     if not args.no_cpu_baseline:
@@ -684,7 +696,7 @@ def bench_batch(args, P, S, autotune, torch):
            "iters_inner_mean": float(np.mean([inf.iters_inner for inf in infos])),
            "iters_inner_max": int(max(inf.iters_inner for inf in infos)),
            "chunk_elems": chunk, **knobs, "tuning": tune, "setup_s": setup_s, "gpu_launches": launches,
-           "l2": "flushed between steps (256 MB write)", "clocks": clk}
+           "roofline": roof, "l2": "flushed between steps (256 MB write)", "clocks": clk}
     for m in meshes:
         P.ps_mesh_free(m)
     P.ps_ctx_destroy(ctx)
