@@ -20,8 +20,11 @@
 //     the chunk's scale comes from a bound on every partial sum (below), and
 //     each node sum is rounded to FP32 once;
 //   * shared nodes' inputs come from a chunk-major halo, contiguous per chunk;
-//   * the p.Ap share is summed by one warp after the node phase (no block
-//     reduction tree).
+//     a thread has all its nodes' loads in flight before any store;
+//   * the chunk's p.Ap share is merged per warp and then across the four
+//     warps by one thread; the chunk block stores it and exits, and one
+//     extra block of the grid sums the shares in chunk order and sets alpha
+//     (no fence, counter or wait in the chunk blocks).
 // Scale of the fixed-point sums: element matrices are positive semidefinite
 // (mass with alpha >= 0, stiffness with beta > 0), so |A^e_ij| <=
 // sqrt(A^e_ii A^e_jj) <= Dmax, the largest diagonal entry D_jj over the
@@ -33,7 +36,8 @@
 // resolution, 2^-47 B ~ 7e-15 B, is far below the FP32 rounding of a row for
 // any dynamic range below ~1e8 between the chunk's largest and a row's own
 // scale.  Each node sum is rounded to FP32 at the end (2^24 h + l in one
-// FMA).  Dirichlet rows are masked to 0 whatever their sums.  The element
+// FMA).  Interior Dirichlet rows are masked to 0 whatever their sums (shared
+// ones by the update kernel, which sums the partials).  The element
 // arithmetic is that of patch_eval (device.cuh): with e1 = b - a and
 // d_j = r_j - a, element j of a patch has the cofactor vectors
 // c1 = d_j x d_{j+1}, c2 = -(e1 x d_{j+1}), c3 = e1 x d_j and c0 = -(c1+c2+c3),
