@@ -3,11 +3,16 @@
 //
 // One worker thread owns a CUDA stream and a batch plan.  Between epochs it
 // admits queued requests (one in flight per case, at most max_slots in flight,
-// the sum of in-flight workspace bytes within the HBM budget), rebuilds the
-// plan when the set of in-flight requests changed (a request already in flight
-// keeps its device state), runs one epoch of the batched engine for every
-// in-flight request, and completes the requests whose solve finished.  A
-// request warm-starts from the pressure its case left on the device.
+// the sum of in-flight workspace bytes within the HBM budget), stages their
+// inputs on its stream (right-hand side; a drifted beta with the element
+// coefficients and the Jacobi diagonal updated on the device), solves the
+// admitted requests of cases at or above the size threshold (single_nodes)
+// alone to convergence with the single-solve engine, rebuilds the plan when
+// the set of batched in-flight requests changed (a request already in flight
+// keeps its device state; the plan keeps its buffers), runs one epoch of the
+// batched engine for every batched in-flight request, and completes the
+// requests whose solve finished.  A request warm-starts from the pressure its
+// case left on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
