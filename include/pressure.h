@@ -440,7 +440,8 @@ int ps_batch_solve(ps_mesh *const *meshes, int n, const double *const *b_dev,
  * are admitted while their workspace fits the HBM budget and a slot is free;
  * admitted requests share persistent-kernel epochs with requests already in
  * flight, and a request that converges frees its slot at the next epoch
- * boundary. */
+ * boundary; with single_nodes set, requests of cases at least that large run
+ * alone in the single-solve engine between epochs instead. */
 typedef struct {
     int32_t max_slots;        /* requests in flight at once (0 = 64)                */
     int32_t epoch_iters;      /* inner iterations per epoch (0 = 64)                */
