@@ -1,9 +1,11 @@
 """Host-side logic of bench.py that needs no GPU: the whole-job aggregation
 over ranks (world_size 2 over gloo on CPU: max time, summed work), the
-reference arm's rank > 0 behaviour, and the clock-sample parser."""
+reference arm's rank > 0 behaviour, the clock-sample parser, and the served
+bench's request stream prepared ahead in a thread pool."""
 import os
 import socket
 
+import numpy as np
 import pytest
 
 import bench
@@ -95,3 +97,35 @@ def test_fp64_flop_model():
     class St2:
         n_elems, n_nodes, dim = 8192, 4225, 2
     assert bench.fp64_flops(St2, False, False) == pytest.approx(50 * 8192 + (8192 * 3 / 4225 + 3) * 4225)
+
+
+def test_drift_ahead_matches_the_sequential_stream():
+    """The served bench prepares each case's next request in a thread pool
+    while the current one is in flight; every case must still draw its
+    seeded random stream in the order of a plain sequential loop."""
+    from paper_2301_08357_gb300 import synthetic as S
+    steps = 4
+    seq_cases = [S.make_served_case(c, lo=1e3, hi=4e3, median=2e3) for c in range(3)]
+    seq = []
+    for c in seq_cases:
+        st, out = (c.beta.copy(), c.b.copy()), []
+        for _ in range(steps - 1):
+            st = S.served_step_drift(c, *st)
+            out.append(st)
+        seq.append(out)
+    cases = [S.make_served_case(c, lo=1e3, hi=4e3, median=2e3) for c in range(3)]
+    ahead = bench._DriftAhead(S, cases, workers=3)
+    state = [(c.beta.copy(), c.b.copy()) for c in cases]
+    got = [[] for _ in cases]
+    for ci in range(len(cases)):
+        ahead.prime(ci, state[ci])
+    for k in range(1, steps):                # cases finishing in a shuffled order each step
+        for ci in ([2, 0, 1] if k % 2 else [1, 2, 0]):
+            state[ci] = ahead.take(ci)
+            got[ci].append(state[ci])
+            if k + 1 < steps:
+                ahead.prime(ci, state[ci])
+    ahead.close()
+    for a, b in zip(seq, got):
+        for (beta1, b1), (beta2, b2) in zip(a, b):
+            assert np.array_equal(beta1, beta2) and np.array_equal(b1, b2)
