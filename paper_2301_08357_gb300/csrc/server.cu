@@ -194,6 +194,7 @@ static void worker_main(ps_server *s) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->st.single_solves++;
         }
+        const size_t n_single_done = done.size();   // complete, results on the host
         // (re)build the plan over the in-flight batched requests, keeping the
         // device state of requests already running
         if (rc == PS_OK) {
@@ -252,8 +253,15 @@ static void worker_main(ps_server *s) {
         s->st.epochs++;
         s->st.busy_seconds += now_s() - t0;
         if (rc != PS_OK) {
-            // fail every in-flight request (batched, and single-lane ones
-            // admitted in this pass of the loop); keep serving the queue
+            // the single-lane requests solved before the failure keep their
+            // results; every other in-flight request fails; keep serving the
+            // queue
+            for (size_t k = 0; k < n_single_done; ++k) {
+                Case &c = s->cases[done[k].first];
+                s->in_flight_bytes -= c.ws_bytes;
+                s->st.in_flight--;
+                finish_req(s, c, c.running, done[k].second.status, &done[k].second);
+            }
             for (size_t ci = 0; ci < s->cases.size(); ++ci) {
                 Case &c = s->cases[ci];
                 if (!c.running) continue;
